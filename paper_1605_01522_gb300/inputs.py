@@ -1,0 +1,362 @@
+"""Seeded synthetic coupled block systems (input generation only).
+
+This module builds the N x N block linear systems (Sec. 4, the blocked system
+A x = b with blocks A_ij) on which the preconditioned GMRES path is run.  It
+holds no solver or preconditioner arithmetic: it assembles bilinear /
+trilinear (Q1) finite-element matrices on a uniform structured mesh, applies
+Dirichlet conditions by symmetric elimination and draws a seeded N(0,1)
+right-hand side.  Both the CUDA path and the CPU oracle consume its output.
+
+The workloads stand in for the paper's thermo-structure interaction (Sec. 6.1,
+the monolithic TSI system) and fluid-structure-like (Sec. 6.2) applications,
+whose meshes are not available:
+
+* ``thermo_elastic_2d``  - 2 fields on the unit square: plane-strain elasticity
+  (2 dof/node) + transient heat (1 dof/node), coupled through
+  A_12 = alpha * int B^T m N and A_21 = 1e-3 * int N m^T B.
+* ``coupled_box_3d``     - the 3D analogue on the unit cube with 2 or 3 fields:
+  elasticity (3 dof/node), heat (1 dof/node) and an optional scalar diffusion
+  field whose diffusivity is log-uniform in [1e-3, 1e3] per element.  The
+  heat-diffusion pair is coupled by alpha*M and 1e-3*M.
+
+Layout of a block: node-level block-CSR (BSR) with int32 ``rowptr`` / ``colind``
+and float64 ``vals`` of shape (nnzb, br, bc), row-major inside a block.
+Dofs of a field are interleaved per node (dof = node * b + component).  The
+global vector is the field-major concatenation of the field vectors.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import itertools
+
+import numpy as np
+
+__all__ = [
+    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d",
+    "batch_sizes_log_uniform",
+]
+
+
+@dataclass
+class BSR:
+    """Node-level block-CSR matrix: block (I, J) is vals[k] for colind[k] == J."""
+    br: int
+    bc: int
+    nbrows: int
+    nbcols: int
+    rowptr: np.ndarray  # int32, nbrows + 1
+    colind: np.ndarray  # int32, nnzb
+    vals: np.ndarray    # float64, (nnzb, br, bc)
+
+    @property
+    def nnzb(self) -> int:
+        return int(self.colind.shape[0])
+
+    @property
+    def shape(self):
+        return (self.nbrows * self.br, self.nbcols * self.bc)
+
+    def to_scipy(self):
+        """Point CSR copy (scipy), for consumers that work on scalar entries."""
+        import scipy.sparse as sp
+        m = sp.bsr_matrix((self.vals, self.colind, self.rowptr), shape=self.shape)
+        return m.tocsr()
+
+
+@dataclass
+class Field:
+    name: str
+    b: int                 # dofs per node
+    nnodes: int
+    dim: int
+    coords: np.ndarray     # (nnodes, dim) float64
+    nullspace: str         # "const" (per-component constants) or "rbm" (rigid-body modes)
+    theta: float = 0.0     # strength-of-connection threshold used for this field
+    dirichlet_nodes: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+
+    @property
+    def ndofs(self) -> int:
+        return self.nnodes * self.b
+
+
+@dataclass
+class BlockSystem:
+    fields: list
+    blocks: dict           # (i, j) -> BSR; absent pairs are zero blocks
+    rhs: np.ndarray        # float64, sum of field dofs
+    name: str = ""
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def nfields(self) -> int:
+        return len(self.fields)
+
+    @property
+    def offsets(self):
+        off = [0]
+        for f in self.fields:
+            off.append(off[-1] + f.ndofs)
+        return off
+
+    @property
+    def ndofs(self) -> int:
+        return self.offsets[-1]
+
+    def scipy_blocks(self):
+        return {k: v.to_scipy() for k, v in self.blocks.items()}
+
+
+# ----------------------------------------------------------------------------
+# Q1 reference-element matrices on an axis-aligned cell of edge h
+# ----------------------------------------------------------------------------
+
+def _local_offsets(dim):
+    # local node a <-> offset o_a in {0,1}^dim, x fastest
+    return [tuple(reversed(t)) for t in itertools.product((0, 1), repeat=dim)]
+
+
+def _gauss_2pt():
+    g = 0.5 / np.sqrt(3.0)
+    return np.array([0.5 - g, 0.5 + g]), np.array([0.5, 0.5])
+
+
+def _shape_at(dim, xi):
+    """Values N_a(xi) and reference gradients dN_a/dxi on [0,1]^dim."""
+    offs = _local_offsets(dim)
+    n = len(offs)
+    N = np.ones(n)
+    dN = np.ones((n, dim))
+    for a, o in enumerate(offs):
+        for d in range(dim):
+            f = xi[d] if o[d] else 1.0 - xi[d]
+            df = 1.0 if o[d] else -1.0
+            N[a] *= f
+            for e in range(dim):
+                dN[a, e] *= df if e == d else f
+    return N, dN
+
+
+def _strain_matrix(dim, dNdx):
+    n = dNdx.shape[0]
+    if dim == 2:
+        B = np.zeros((3, 2 * n))
+        for a in range(n):
+            dx, dy = dNdx[a]
+            B[0, 2 * a] = dx
+            B[1, 2 * a + 1] = dy
+            B[2, 2 * a] = dy
+            B[2, 2 * a + 1] = dx
+        return B
+    B = np.zeros((6, 3 * n))
+    for a in range(n):
+        dx, dy, dz = dNdx[a]
+        c = 3 * a
+        B[0, c] = dx
+        B[1, c + 1] = dy
+        B[2, c + 2] = dz
+        B[3, c + 1] = dz
+        B[3, c + 2] = dy
+        B[4, c] = dz
+        B[4, c + 2] = dx
+        B[5, c] = dy
+        B[5, c + 1] = dx
+    return B
+
+
+def _elasticity_D(dim, E, nu):
+    lam = E * nu / ((1 + nu) * (1 - 2 * nu))
+    mu = E / (2 * (1 + nu))
+    if dim == 2:  # plane strain
+        return np.array([[lam + 2 * mu, lam, 0], [lam, lam + 2 * mu, 0], [0, 0, mu]])
+    D = np.zeros((6, 6))
+    D[:3, :3] = lam
+    D[np.arange(3), np.arange(3)] = lam + 2 * mu
+    D[3, 3] = D[4, 4] = D[5, 5] = mu
+    return D
+
+
+def q1_element_matrices(dim, h, E=1.0, nu=0.3):
+    """Element stiffness (elasticity, Laplacian), mass and thermo-mechanical
+    coupling int B^T m N on a cell of edge h with 2^dim Gauss points."""
+    pts, wts = _gauss_2pt()
+    nloc = 2 ** dim
+    D = _elasticity_D(dim, E, nu)
+    m = np.array([1.0, 1.0, 0.0]) if dim == 2 else np.array([1.0, 1, 1, 0, 0, 0])
+    Ke = np.zeros((dim * nloc, dim * nloc))
+    Kl = np.zeros((nloc, nloc))
+    Me = np.zeros((nloc, nloc))
+    Ce = np.zeros((dim * nloc, nloc))
+    detJ = h ** dim
+    for idx in itertools.product(range(2), repeat=dim):
+        xi = np.array([pts[i] for i in idx])
+        w = np.prod([wts[i] for i in idx]) * detJ
+        N, dN = _shape_at(dim, xi)
+        dNdx = dN / h
+        B = _strain_matrix(dim, dNdx)
+        Ke += w * B.T @ D @ B
+        Kl += w * dNdx @ dNdx.T
+        Me += w * np.outer(N, N)
+        Ce += w * np.outer(B.T @ m, N)
+    return Ke, Kl, Me, Ce
+
+
+# ----------------------------------------------------------------------------
+# Structured-mesh BSR assembly
+# ----------------------------------------------------------------------------
+
+class _Grid:
+    def __init__(self, ne, dim):
+        self.ne = ne
+        self.dim = dim
+        self.n1 = ne + 1
+        self.nnodes = self.n1 ** dim
+        ijk = np.indices((self.n1,) * dim).reshape(dim, -1)[::-1]  # x fastest
+        self.ijk = ijk.T.copy()                                      # (nnodes, dim): (i, j[, k])
+        self.coords = self.ijk / float(ne)
+        self.stride = np.array([self.n1 ** d for d in range(dim)])
+        # neighbour stencil, in increasing node-index order (z slowest)
+        self.stencil = [tuple(reversed(t)) for t in itertools.product((-1, 0, 1), repeat=dim)]
+        self.sidx = {s: k for k, s in enumerate(self.stencil)}
+        ns = len(self.stencil)
+        valid = np.ones((self.nnodes, ns), bool)
+        for k, s in enumerate(self.stencil):
+            for d in range(dim):
+                c = self.ijk[:, d] + s[d]
+                valid[:, k] &= (c >= 0) & (c <= ne)
+        self.valid = valid
+        counts = valid.sum(1)
+        self.rowptr = np.zeros(self.nnodes + 1, np.int64)
+        np.cumsum(counts, out=self.rowptr[1:])
+        pos = np.full((self.nnodes, ns), -1, np.int64)
+        run = np.cumsum(valid, axis=1) - 1 + self.rowptr[:-1, None]
+        pos[valid] = run[valid]
+        self.pos = pos
+        colind = np.zeros(self.rowptr[-1], np.int64)
+        for k, s in enumerate(self.stencil):
+            off = int(np.dot(s, self.stride))
+            v = valid[:, k]
+            colind[pos[v, k]] = np.nonzero(v)[0] + off
+        self.colind = colind
+        # elements: base node index for every cell
+        eijk = np.indices((ne,) * dim).reshape(dim, -1)[::-1].T
+        self.nelem = eijk.shape[0]
+        self.ebase = eijk @ self.stride
+        self.loc = _local_offsets(dim)
+
+    def assemble(self, Kloc, br, bc, scale=None):
+        """Sum the element matrix Kloc (nloc*br x nloc*bc, dof = a*b + comp)
+        over all cells, optionally scaled per cell; returns BSR vals."""
+        vals = np.zeros((self.rowptr[-1], br, bc))
+        for a, oa in enumerate(self.loc):
+            node_a = self.ebase + int(np.dot(oa, self.stride))
+            for b_, ob in enumerate(self.loc):
+                s = tuple(ob[d] - oa[d] for d in range(self.dim))
+                p = self.pos[node_a, self.sidx[s]]
+                blk = Kloc[a * br:(a + 1) * br, b_ * bc:(b_ + 1) * bc]
+                if scale is None:
+                    vals[p] += blk
+                else:
+                    vals[p] += scale[:, None, None] * blk
+        return vals
+
+    def bsr(self, vals, br, bc):
+        return BSR(br, bc, self.nnodes, self.nnodes, self.rowptr.astype(np.int32),
+                   self.colind.astype(np.int32), vals)
+
+
+def _apply_dirichlet(grid, blocks, nfields, dnodes):
+    """Symmetric elimination: zero Dirichlet rows/cols in every block and put
+    the identity on the diagonal blocks (all fields share the node set)."""
+    isd = np.zeros(grid.nnodes, bool)
+    isd[dnodes] = True
+    rows = np.repeat(np.arange(grid.nnodes), np.diff(grid.rowptr))
+    kill = isd[rows] | isd[grid.colind]
+    diag = isd[rows] & (rows == grid.colind)
+    for (i, j), m in blocks.items():
+        m.vals[kill] = 0.0
+        if i == j:
+            m.vals[diag] = np.eye(m.br)
+
+
+def _seeded_rhs(fields, seed, dnodes):
+    rng = np.random.default_rng(seed)
+    n = sum(f.ndofs for f in fields)
+    b = rng.standard_normal(n)
+    off = 0
+    for f in fields:
+        d = (dnodes[:, None] * f.b + np.arange(f.b)[None, :]).ravel()
+        b[off + d] = 0.0
+        off += f.ndofs
+    return b
+
+
+def thermo_elastic_2d(ne=32, alpha=1e-2, beta=1e-3, E=1.0, nu=0.3, k=1.0, dt=0.1, seed=0):
+    """2-field thermo-elastic system on the unit square (Sec. 6.1 in 2D):
+    field 0 plane-strain elasticity, field 1 transient heat (k*L + M/dt),
+    A_01 = alpha*int B^T m N, A_10 = beta*int N m^T B; left edge clamped and
+    T = 0 there."""
+    g = _Grid(ne, 2)
+    h = 1.0 / ne
+    Ke, Kl, Me, Ce = q1_element_matrices(2, h, E, nu)
+    blocks = {
+        (0, 0): g.bsr(g.assemble(Ke, 2, 2), 2, 2),
+        (1, 1): g.bsr(g.assemble(k * Kl + Me / dt, 1, 1), 1, 1),
+        (0, 1): g.bsr(g.assemble(alpha * Ce, 2, 1), 2, 1),
+        (1, 0): g.bsr(g.assemble(beta * Ce.T, 1, 2), 1, 2),
+    }
+    dnodes = np.nonzero(g.ijk[:, 0] == 0)[0]
+    _apply_dirichlet(g, blocks, 2, dnodes)
+    fields = [
+        Field("elasticity", 2, g.nnodes, 2, g.coords, "rbm", 0.0, dnodes),
+        Field("heat", 1, g.nnodes, 2, g.coords, "const", 0.0, dnodes),
+    ]
+    return BlockSystem(fields, blocks, _seeded_rhs(fields, seed, dnodes),
+                       name=f"thermo_elastic_2d_ne{ne}",
+                       meta=dict(ne=ne, alpha=alpha, seed=seed))
+
+
+def coupled_box_3d(ne=64, nfields=3, alpha=1e-2, beta=1e-3, E=1.0, nu=0.3, k=1.0, dt=0.1,
+                   diff_theta=0.02, seed=1):
+    """3D coupled box on the unit cube: field 0 elasticity (3 dof/node), field 1
+    heat (k*L + M/dt), optional field 2 scalar diffusion with per-cell
+    diffusivity 10^U(-3,3) (no mass).  Elasticity-scalar pairs use the
+    thermo-mechanical coupling (alpha*int B^T m N, beta*int N m^T B); the
+    heat-diffusion pair uses alpha*M and beta*M.  The x = 0 face is Dirichlet
+    for every field."""
+    assert nfields in (2, 3)
+    g = _Grid(ne, 3)
+    h = 1.0 / ne
+    Ke, Kl, Me, Ce = q1_element_matrices(3, h, E, nu)
+    rng = np.random.default_rng(seed)
+    blocks = {
+        (0, 0): g.bsr(g.assemble(Ke, 3, 3), 3, 3),
+        (1, 1): g.bsr(g.assemble(k * Kl + Me / dt, 1, 1), 1, 1),
+        (0, 1): g.bsr(g.assemble(alpha * Ce, 3, 1), 3, 1),
+        (1, 0): g.bsr(g.assemble(beta * Ce.T, 1, 3), 1, 3),
+    }
+    fields_theta = [0.0, 0.0]
+    if nfields == 3:
+        kappa = 10.0 ** rng.uniform(-3.0, 3.0, size=g.nelem)
+        blocks[(2, 2)] = g.bsr(g.assemble(Kl, 1, 1, scale=kappa), 1, 1)
+        blocks[(0, 2)] = g.bsr(g.assemble(alpha * Ce, 3, 1), 3, 1)
+        blocks[(2, 0)] = g.bsr(g.assemble(beta * Ce.T, 1, 3), 1, 3)
+        blocks[(1, 2)] = g.bsr(g.assemble(alpha * Me, 1, 1), 1, 1)
+        blocks[(2, 1)] = g.bsr(g.assemble(beta * Me, 1, 1), 1, 1)
+        fields_theta.append(diff_theta)
+    dnodes = np.nonzero(g.ijk[:, 0] == 0)[0]
+    _apply_dirichlet(g, blocks, nfields, dnodes)
+    names = ["elasticity", "heat", "diffusion"]
+    fields = []
+    for i in range(nfields):
+        b = 3 if i == 0 else 1
+        fields.append(Field(names[i], b, g.nnodes, 3, g.coords, "rbm" if i == 0 else "const",
+                            fields_theta[i], dnodes))
+    return BlockSystem(fields, blocks, _seeded_rhs(fields, seed, dnodes),
+                       name=f"coupled_box_3d_ne{ne}_f{nfields}",
+                       meta=dict(ne=ne, nfields=nfields, alpha=alpha, seed=seed))
+
+
+def batch_sizes_log_uniform(nsys=256, lo=12, hi=48, seed=3):
+    """Per-system mesh edge n_e = round(exp(U(ln lo, ln hi)))."""
+    rng = np.random.default_rng(seed)
+    return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=nsys))).astype(int)
