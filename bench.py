@@ -1,0 +1,317 @@
+"""Benchmark: coupled solves/s to 1e-8 on the 3-field 3D coupled box.
+
+Workload: 64^3 Q1 hex mesh, elasticity (3 dof/node) + heat + log-uniform
+diffusion (1 dof/node each), all pairs coupled, 1,373,125 dofs; FGMRES(50)
+to a 1e-8 true relative residual with the BGS(AMG) preconditioner (backward
+sweep, SA-AMG, Chebyshev degree 2) computed in FP32 while the Krylov loop,
+coarse LU and residuals stay FP64.  One step = one full solve from x0 = 0
+with the hierarchy resident (setup excluded, timed separately).
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+on the same workload (bounded sample of FGMRES iterations, scaled to
+solves/s by the oracle's stored iteration count).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled solves/s to 1e-8 residual"
+UNIT = "solves/s"
+NE = 64
+WORKLOAD = "coupled_box_3d_ne64_f3"
+SOLVER_KW = dict(max_levels=5, coarse_max=1000)
+FALLBACK_HBM_GBS = 6800.0
+CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+                "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+                "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+def workload_config(args, s, extra=None):
+    cfg = {
+        "workload": f"3-field 3D coupled box {NE}^3 Q1 ({s.ndofs} dofs: elasticity+heat+diffusion), "
+                    f"{args.precond.upper()} preconditioner in {args.precision.upper()}, FGMRES(50), rtol 1e-8",
+        "ndofs": s.ndofs,
+        "precond": args.precond,
+        "precision": args.precision,
+        "l2": "inputs larger than L2 (matrices ~2 GB per solve pass)",
+        "parallelism": "replicas" if args.gpus > 1 else "1 GPU",
+    }
+    cfg.update(extra or {})
+    return cfg
+
+
+def measured_hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+
+        def find(o):
+            if isinstance(o, dict):
+                for k, v in o.items():
+                    if k == "hbm_gbs" and isinstance(v, (int, float)):
+                        return float(v)
+                    r = find(v)
+                    if r:
+                        return r
+            return None
+        v = find(d)
+        if v:
+            return v, "measured"
+    except Exception:
+        pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={','.join(CLOCK_FIELDS)}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        sm, smax, reasons = [], [], set()
+        names = CLOCK_FIELDS[5:]
+        try:
+            for line in open(self.path):
+                p = [x.strip() for x in line.split(",")]
+                if len(p) != len(CLOCK_FIELDS):
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, p[5:]):
+                    if v.lower() == "active":
+                        reasons.add(n.split(".")[-1])
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def make_system():
+    from paper_1605_01522_gb300 import inputs
+    return inputs.coupled_box_3d(ne=NE, nfields=3, seed=1)
+
+
+def oracle_counts():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def oracle_sample(s, precond_name, n_iter):
+    """Time n_iter FGMRES iterations of the FP64 oracle (its own hierarchy,
+    built untimed) on the full workload; returns (seconds per iteration, setup s)."""
+    from oracle import amg, krylov, precond
+    A = s.scipy_blocks()
+    D = precond.assemble(A, s.nfields)
+    t0 = time.perf_counter()
+    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], precond.Params(precond_name, **SOLVER_KW))
+    t1 = time.perf_counter()
+    krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=n_iter)
+    t2 = time.perf_counter()
+    return (t2 - t1) / n_iter, t1 - t0
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    s = make_system()
+    counts = oracle_counts()
+    key = f"{WORKLOAD}/{args.precond}"
+    iters = counts[key]["iters"]
+    n_iter = 2
+    times = []
+    setup_s = None
+    from oracle import amg, krylov, precond
+    A = s.scipy_blocks()
+    D = precond.assemble(A, s.nfields)
+    t0 = time.perf_counter()
+    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], precond.Params(args.precond, **SOLVER_KW))
+    setup_s = time.perf_counter() - t0
+    for k in range(args.warmup + args.steps):
+        t1 = time.perf_counter()
+        krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=n_iter)
+        dt = (time.perf_counter() - t1) / n_iter * iters
+        if k >= args.warmup:
+            times.append(dt)
+    per_solve = statistics.mean(times)
+    value = 1.0 / per_solve
+    sample = (f"{n_iter} FGMRES iterations per step of the FP64 oracle (scipy, its own hierarchy, setup "
+              f"{setup_s:.1f} s untimed) on the full workload, scaled by the oracle's {iters} iterations per solve")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, s, {"oracle_iters": iters}),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_mfs(args, rank, world):
+    import torch
+    from paper_1605_01522_gb300 import mfs
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    s = make_system()
+    stream = torch.cuda.Stream(device=dev)
+    prm = mfs.default_params(precond=args.precond, precision=args.precision, profile=1,
+                             cuda_stream=stream.cuda_stream, **SOLVER_KW)
+    t0 = time.perf_counter()
+    lib = mfs.Solver(s, params=prm)
+    setup_s = time.perf_counter() - t0
+    n = s.ndofs
+    with torch.cuda.stream(stream):
+        b = torch.from_numpy(s.rhs).to(dev)
+        x = torch.zeros(n, dtype=torch.float64, device=dev)
+    stream.synchronize()
+    infos = []
+    for _ in range(args.warmup):
+        x.zero_()
+        torch.cuda.synchronize()
+        _, info, rc = lib.solve(b, x, tol=1e-8)
+    lib.kernel_stats(reset=True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                x.zero_()
+            _, info, rc = lib.solve(b, x, tol=1e-8)
+            infos.append(info)
+            if rc != mfs.OK:
+                raise RuntimeError(f"solve failed rc={rc} info={info}")
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        dist.barrier()
+        t = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    stats = lib.kernel_stats(reset=True)
+    # true residual, recomputed through the library's FP64 matvec (device)
+    r = b - lib.matvec(x)
+    relres = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+    # end-to-end: host (pinned) vectors, copies inside the timed region
+    bh = torch.from_numpy(s.rhs.copy()).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for k in range(max(2, args.steps // 2) + 1):
+        xh.zero_()
+        t1 = time.perf_counter()
+        _, info_h, rc = lib.solve(bh.numpy(), xh.numpy(), tol=1e-8)
+        dt = time.perf_counter() - t1
+        if k > 0:
+            e2e_times.append(dt)
+    lib.kernel_stats(reset=True)
+    e2e = {"value": world / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
+           "d2h_bytes_per_step": 8 * n}
+    # roofline of the dominant kernel class (by event time)
+    peak, peak_kind = measured_hbm_peak()
+    cls = max(("spmv", "smooth"), key=lambda c: stats[c][1])
+    launches, ms, nbytes = stats[cls]
+    achieved = nbytes / (ms / 1e3) / 1e9
+    launches_total = sum(v[0] for v in stats.values())
+    value = world * args.steps / elapsed
+    if rank != 0:
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        counts = oracle_counts()
+        iters_o = counts[f"{WORKLOAD}/{args.precond}"]["iters"]
+        n_iter = 3
+        per_iter, osetup = oracle_sample(s, args.precond, n_iter)
+        cpu = {"value": 1.0 / (per_iter * iters_o), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n_iter} FGMRES({args.precond}) iterations of the FP64 oracle on the full workload "
+                         f"(own hierarchy, setup {osetup:.1f} s untimed), scaled by its {iters_o} iterations/solve"}
+    shares = {c: round(v[1] / max(1e-9, sum(u[1] for u in stats.values())), 4) for c, v in stats.items()}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32p" else "f64",
+        "data": "synthetic",
+        "config": workload_config(args, s, {"iters": infos[-1]["iters"], "true_relres": relres,
+                                            "setup_s": round(setup_s, 2), "levels": infos[-1]["levels"],
+                                            "kernel_time_share": shares}),
+        "roofline": {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
+                     "launches": launches, "ms": ms, "algorithmic_bytes": nbytes},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches_total),
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    lib.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mfs", choices=["mfs", "reference"])
+    ap.add_argument("--precond", default="bgs_amg", choices=["bgs_amg", "amg_bgs", "simple"])
+    ap.add_argument("--precision", default="fp32p", choices=["fp32p", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_mfs(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * mfs.h - C ABI of libmfs, a single-GPU (GB300, sm_103a) solver for monolithic
+ * n-field coupled linear systems with block preconditioners.
+ *
+ * Problem (Sec. 4, the blocked system): A x = b with A = [A_ij], i, j = 1..N,
+ * where A_ij couples field i (rows) to field j (columns) and any block may be
+ * zero.  The solver is right-preconditioned flexible GMRES(m) (Sec. 3.1-3.2)
+ * with one of three block preconditioners:
+ *   MFS_BGS_AMG  block Gauss-Seidel with one smoothed-aggregation AMG V-cycle
+ *                per diagonal block (Sec. 4.1);
+ *   MFS_SIMPLE   n-field SIMPLE(AMG): fields merged into a predictor group and a
+ *                Schur group, SIMPLEC / diagonal approximation of the predictor
+ *                block, explicit approximate Schur complement (Sec. 4.2);
+ *   MFS_AMG_BGS  monolithic AMG with block-diagonal transfers, blockwise
+ *                Galerkin coarse blocks and block Gauss-Seidel level smoothing
+ *                (Sec. 4.3).
+ * Every solve-phase step runs in this library's CUDA kernels; there is no CPU
+ * fallback.  The AMG setup (aggregation, prolongators, Galerkin products,
+ * coarse factorisation) runs in this library's host code and is timed apart.
+ *
+ * Conventions
+ *   - All functions return MFS_OK (0) or a negative MFS_ERR_* code;
+ *     mfs_strerror() names it.  A failed call leaves no partial handle.
+ *   - Vectors are float64, field-major: the vector of field 0, then field 1, ...
+ *     Inside a field the dofs of a node are contiguous (dof = node * b + c).
+ *   - Vector arguments may be host or device (CUDA) pointers; the library
+ *     detects which and copies host data through its own device buffers.
+ *   - Input block matrices are HOST pointers and are deep-copied; the caller
+ *     may free them after mfs_setup returns.
+ *   - Work is issued on params.cuda_stream (0 = legacy default stream); every
+ *     call returns after its work on that stream has finished.
+ *   - A handle is not thread-safe: one thread at a time per handle.
+ */
+#ifndef MFS_H
+#define MFS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MFS_MAX_FIELDS 8
+
+enum mfs_status {
+  MFS_OK = 0,
+  MFS_ERR_INVALID = -1,        /* bad argument, shape or parameter */
+  MFS_ERR_CUDA = -2,           /* CUDA runtime error or no usable GPU */
+  MFS_ERR_OOM = -3,            /* device allocation failed */
+  MFS_ERR_SINGULAR = -4,       /* zero pivot / zero diagonal in setup */
+  MFS_ERR_NOT_CONVERGED = -5,  /* max_iters reached; x holds the last iterate */
+  MFS_ERR_BREAKDOWN = -6,      /* non-finite value met inside GMRES */
+  MFS_ERR_SETUP = -7           /* aggregation could not coarsen a field */
+};
+
+enum mfs_precond { MFS_BGS_AMG = 0, MFS_SIMPLE = 1, MFS_AMG_BGS = 2 };
+enum mfs_bgs_order { MFS_BWD = 0, MFS_FWD = 1, MFS_SYM = 2 };
+enum mfs_nullspace { MFS_NS_CONST = 0, MFS_NS_RBM = 1 };
+enum mfs_precision { MFS_FP64 = 0, MFS_FP32P = 1 };
+enum mfs_simple_approx { MFS_ABSROWSUM = 0, MFS_DIAG = 1 };
+enum mfs_smoother { MFS_CHEBYSHEV = 0, MFS_JACOBI = 1 };
+
+/* One nonzero block A_ij as node-level block-CSR (BSR): nbrows x nbcols node
+ * blocks of br x bc scalars (br = dofs per node of field i, bc = of field j),
+ * block k holds vals[k*br*bc .. (k+1)*br*bc) row-major; colind sorted within
+ * each row.  Host pointers. */
+typedef struct {
+  int i, j;
+  int br, bc;
+  int64_t nbrows, nbcols, nnzb;
+  const int32_t *rowptr; /* nbrows + 1 */
+  const int32_t *colind; /* nnzb */
+  const double *vals;    /* nnzb * br * bc */
+} mfs_block;
+
+/* One physical field.  coords (host, nnodes * dim, may be NULL for
+ * MFS_NS_CONST) give the rigid-body modes of an MFS_NS_RBM field
+ * (requires dofs_per_node == dim). */
+typedef struct {
+  int64_t nnodes;
+  int dofs_per_node;
+  int dim;
+  const double *coords;
+  int nullspace;          /* enum mfs_nullspace */
+  double strength_theta;  /* strength-of-connection threshold, >= 0 */
+} mfs_field;
+
+typedef struct {
+  int precond;                       /* enum mfs_precond */
+  int bgs_order;                     /* enum mfs_bgs_order (default MFS_BWD) */
+  int bgs_sweeps;                    /* k_max of BGS / SIMPLE (default 1) */
+  int simple_group[MFS_MAX_FIELDS];  /* per field: 0 = predictor, 1 = Schur */
+  int simple_approx;                 /* enum mfs_simple_approx */
+  int max_levels;                    /* multigrid levels incl. the finest (>= 1) */
+  int64_t coarse_max;                /* stop coarsening at <= this many dofs per group */
+  int smoother;                      /* enum mfs_smoother */
+  int cheb_degree;                   /* Chebyshev degree (default 2) */
+  double cheb_ratio;                 /* lower interval end = lambda / ratio (30) */
+  double cheb_boost;                 /* upper interval end = boost * lambda (1.1) */
+  double jacobi_omega;               /* damped-Jacobi weight (2/3) */
+  int jacobi_sweeps;                 /* damped-Jacobi sweeps (1) */
+  int restart;                       /* GMRES restart length m (default 50) */
+  int max_iters;                     /* total GMRES iterations (default 1000) */
+  int precision;                     /* enum mfs_precision */
+  uint64_t seed;                     /* SplitMix64 seed: priorities, power iteration */
+  void *cuda_stream;                 /* cudaStream_t or NULL */
+  int verbose;                       /* 0 = silent */
+  int setup_only;                    /* 1: build the host hierarchy only (no GPU needed);
+                                        the handle then serves the export calls alone */
+  int profile;                       /* 1: time every kernel launch of mfs_solve with CUDA
+                                        events, by kernel class (see mfs_kernel_stats) */
+} mfs_params;
+
+typedef struct {
+  int iters;             /* preconditioner applications (GMRES iterations) */
+  int restarts;
+  int converged;         /* 1 when true residual <= tol */
+  double true_relres;    /* ||b - A x|| / ||b - A x0||, float64, on the GPU */
+  double est_relres;     /* GMRES (Givens) estimate at exit */
+  double solve_ms;       /* wall time of mfs_solve */
+  double setup_ms;       /* wall time of mfs_setup */
+  int levels[2];         /* level count of hierarchy group 0 and 1 (or 0) */
+} mfs_info;
+
+/* Fill *p with the defaults listed above (BGS(AMG), backward, 1 sweep,
+ * SIMPLE groups all zero = predictor is every field but the last, SIMPLEC, 4 levels, coarse_max 1000,
+ * Chebyshev degree 2, GMRES(50), FP64, seed 7). */
+void mfs_default_params(mfs_params *p);
+
+/* Build the hierarchy for the block system (Sec. 4: blocks A_ij with the
+ * field map; Sec. 3.3 / 4.3: AMG setup and Galerkin coarse operators).
+ * nblocks blocks with distinct (i, j); every diagonal block must be given.
+ * On success *out owns all device data; free it with mfs_free. */
+int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int nfields,
+              const mfs_params *params, struct mfs_handle **out);
+
+/* Solve A x = rhs by FGMRES(m) to ||b - A x|| <= tol * ||b - A x0|| (Sec. 7.1
+ * stopping rule) with x0 taken from x on entry.  rhs, x: n float64 (host or
+ * device).  info may be NULL.  Returns MFS_ERR_NOT_CONVERGED with the last
+ * iterate in x when max_iters is reached. */
+int mfs_solve(struct mfs_handle *h, const double *rhs, double *x, double tol, mfs_info *info);
+
+/* One preconditioner application z = M^-1 v (the Sec. 4 preconditioner with
+ * x^(0) = 0 and k_max sweeps).  v, z: n float64, host or device. */
+int mfs_apply(struct mfs_handle *h, const double *v, double *z);
+
+/* y = A x with the fine coupled operator (all nonzero blocks), float64. */
+int mfs_matvec(struct mfs_handle *h, const double *x, double *y);
+
+/* Total scalar dofs n of the coupled system. */
+int64_t mfs_ndofs(const struct mfs_handle *h);
+
+/* Export one hierarchy matrix as point CSR (float64) for inspection.
+ * what: 0 = A block (i, j) of level, 1 = P of field i (level -> level+1),
+ *       2 = R of field i.  group: 0 (all fields; SIMPLE: predictor group) or
+ *       1 (SIMPLE Schur group, blocks of S~).  Call with NULL arrays to get
+ *       *nrows, *ncols, *nnz; then with arrays of that size. */
+int mfs_export_csr(const struct mfs_handle *h, int what, int group, int level, int i, int j,
+                   int64_t *nrows, int64_t *ncols, int64_t *nnz,
+                   int32_t *rowptr, int32_t *colind, double *vals);
+
+/* Export per-level data.  what: 0 = aggregate id per node (int32, -1 for
+ * unaggregated nodes), 1 = lambda_max estimate (1 double), 2 = SIMPLE
+ * diagonal A~_11 of predictor field i (double, group 0, level 0).
+ * cap = capacity in elements; *count receives the element count. */
+int mfs_export_array(const struct mfs_handle *h, int what, int group, int level, int i,
+                     void *buf, int64_t cap, int64_t *count);
+
+/* Number of levels of hierarchy group g (0 when absent). */
+int mfs_num_levels(const struct mfs_handle *h, int group);
+
+/* Kernel accounting of the mfs_solve calls made since setup or the last
+ * reset (handle built with params.profile = 1).  For class c in 0..4
+ * (0 block SpMV incl. transfers, 1 fused smoothing step, 2 vector kernels,
+ * 3 dense coarse solve, 4 Arnoldi reductions/updates) writes
+ * out[3c] = launches, out[3c+1] = summed event time in ms,
+ * out[3c+2] = summed algorithmic bytes (every matrix/vector entry a launch
+ * touches counted once).  cap = length of out.  Returns the number of
+ * classes written; reset != 0 zeroes the counters afterwards.  The event
+ * hook is process-wide: profile one handle at a time. */
+int mfs_kernel_stats(struct mfs_handle *h, double *out, int cap, int reset);
+
+/* Release every device and host resource of the handle (NULL is a no-op). */
+void mfs_free(struct mfs_handle *h);
+/* Static description of a status code. */
+const char *mfs_strerror(int code);
+/* Detail of the last failure on the calling thread ("" if none). */
+const char *mfs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MFS_H */

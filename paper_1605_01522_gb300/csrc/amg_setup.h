@@ -1,0 +1,69 @@
+// Smoothed-aggregation AMG setup on the host (timed apart from the solve).
+//
+// Single-field objects P^l_i, R^l_i, A^l_ii and smoother data per field and
+// level (Sec. 3.3, Sec. 4.3), blockwise Galerkin coarse blocks for the
+// monolithic hierarchy (Sec. 4.3), the SIMPLE approximation A~_11 and the
+// explicit S~ (Sec. 4.2), and dense LU factors of the coarsest operators.
+// Aggregation and the tentative prolongator follow the steps fixed for this
+// library (the paper cites smoothed aggregation without detail):
+//   strength |A_IJ|_F > theta sqrt(|A_II|_F |A_JJ|_F), symmetrised;
+//   roots = lexicographically-first distance-2 maximal independent set in
+//   decreasing SplitMix64 priority (ties: lower index); neighbours of a root
+//   join it; remaining nodes join the neighbouring aggregate whose root has
+//   the highest priority; nodes without strong neighbours stay unaggregated;
+//   per-aggregate Gram-Schmidt QR (two passes, columns with remaining norm
+//   <= 1e-10 of the original dropped) of the near-nullspace, rotations about
+//   the aggregate centroid; lambda_max(D^-1 A) by 10 power iterations from a
+//   SplitMix64 start vector; P = (I - 4/(3 lambda) D^-1 A) P_tent; R = P^T.
+#pragma once
+#include <map>
+#include <utility>
+#include <vector>
+
+#include "host_sparse.h"
+
+namespace mfs {
+
+struct FieldInfo {
+  int64_t nnodes = 0;
+  int b = 1, dim = 3;
+  int ns = 0;  // 0 constants, 1 rigid-body modes
+  double theta = 0.0;
+  std::vector<double> coords;
+};
+
+struct HLevelField {
+  HBsr A;                      // diagonal block A^l_ii
+  std::vector<double> dinv;    // inverse point diagonal
+  double lam = 0.0;            // lambda_max(D^-1 A) estimate (levels < coarsest)
+  std::vector<int32_t> agg;    // node -> aggregate (-1 unaggregated)
+  int64_t nagg = 0;
+  HBsr P, R;                   // to level l+1
+  std::vector<double> B;       // near-nullspace on coarse levels (n x b)
+};
+
+struct HDenseLU {
+  int n = 0;
+  std::vector<double> lu;      // column-major n x n, unit-lower L below the diagonal
+  std::vector<int32_t> perm;   // y = b[perm]
+};
+
+using BlockMap = std::map<std::pair<int, int>, HBsr>;
+
+struct HGroup {
+  int nf = 0;
+  std::vector<FieldInfo> info;
+  std::vector<std::vector<HLevelField>> lv;  // [level][field]
+  std::vector<BlockMap> off;                 // [level] off-diagonal blocks (monolithic AMG only)
+  std::vector<HDenseLU> coarse_field;        // per-field LU of the coarsest A_ii
+  HDenseLU coarse_coupled;                   // LU of the assembled coarsest coupled matrix
+  int nlevels() const { return (int)lv.size(); }
+};
+
+void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<FieldInfo> &info,
+                 int max_levels, int64_t coarse_max, uint64_t seed, bool want_off,
+                 const BlockMap *fine_off);
+HDenseLU dense_lu(int n, std::vector<double> a_rowmajor);
+std::vector<double> bsr_to_dense(const HBsr &A);
+
+}  // namespace mfs

@@ -1,0 +1,399 @@
+// Solve-phase CUDA kernels for sm_103a: blocked SELL-32 SpMV, the fused
+// residual + polynomial smoothing step, the dense LU coarse solve and the
+// CGS2 Arnoldi reductions.  All sparse work is HBM-bandwidth bound; loads of
+// a warp are contiguous per slot and every reduction has a fixed order.
+#include "kernels.cuh"
+
+#include <cstdio>
+
+namespace mfs {
+namespace dev {
+
+namespace {
+
+constexpr int kThreads = 256;
+LaunchHook *g_hook = nullptr;
+
+struct HookScope {
+  cudaStream_t s;
+  int cls;
+  double bytes;
+  HookScope(cudaStream_t s_, int c, double b) : s(s_), cls(c), bytes(b) {
+    if (g_hook) g_hook->before(s);
+  }
+  ~HookScope() {
+    if (g_hook) g_hook->after(s, cls, bytes);
+  }
+};
+
+// algorithmic bytes of one pass over a block matrix: values + block-column
+// indices + row lengths, each read once
+template <typename T> double matrix_bytes(const Sell &A) {
+  return (double)A.nnzb * (A.br * A.bc * sizeof(T) + sizeof(int32_t)) + (double)A.nbr * sizeof(int32_t);
+}
+
+inline unsigned grid_for(int64_t n, int threads = kThreads) {
+  return (unsigned)((n + threads - 1) / threads);
+}
+
+template <int BR, int BC, typename T>
+__device__ __forceinline__ void sell_row(const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+                                         const int32_t *__restrict__ col, const T *__restrict__ val,
+                                         const T *__restrict__ x, int64_t row, T (&acc)[BR]) {
+  const int lane = (int)(row & 31);
+  const int64_t slice = row >> 5;
+  const int64_t base = sp[slice];
+  const int len = rl[row];
+  const int32_t *cp = col + base * 32 + lane;
+  const T *vp = val + base * (BR * BC * 32) + lane;
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+#pragma unroll 2
+  for (int t = 0; t < len; ++t) {
+    const int64_t c = __ldg(cp + (int64_t)t * 32);
+    T xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = __ldg(x + c * BC + q);
+    const T *v = vp + (int64_t)t * (BR * BC * 32);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[r] += __ldg(v + (r * BC + q) * 32) * xv[q];
+  }
+}
+
+template <int BR, int BC, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+       const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x, T *y,
+       T alpha, T beta, const T *z) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  T acc[BR];
+  sell_row<BR, BC, T>(sp, rl, col, val, x, row, acc);
+  T *yp = y + row * BR;
+  if (z != nullptr) {
+    const T *zp = z + row * BR;
+    T zv[BR];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) zv[r] = zp[r];
+#pragma unroll
+    for (int r = 0; r < BR; ++r) yp[r] = alpha * acc[r] + beta * zv[r];
+  } else {
+#pragma unroll
+    for (int r = 0; r < BR; ++r) yp[r] = alpha * acc[r];
+  }
+}
+
+template <int BR, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+         const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ dinv,
+         const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ xout, T *__restrict__ d,
+         T c1, T c2) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  T acc[BR];
+  sell_row<BR, BR, T>(sp, rl, col, val, x, row, acc);
+#pragma unroll
+  for (int r = 0; r < BR; ++r) {
+    const int64_t i = row * BR + r;
+    const T res = b[i] - acc[r];
+    const T dd = c1 * d[i] + c2 * dinv[i] * res;
+    d[i] = dd;
+    xout[i] = x[i] + dd;
+  }
+}
+
+template <typename T>
+__global__ void k_smooth_first(int64_t n, const T *__restrict__ dinv, const T *__restrict__ b,
+                               T *__restrict__ x, T *__restrict__ d, T c2) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T dd = c2 * dinv[i] * b[i];
+    d[i] = dd;
+    x[i] = dd;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_lu_solve(int n, const double *__restrict__ lu, const int32_t *__restrict__ perm,
+           const T *__restrict__ b, T *__restrict__ x) {
+  extern __shared__ double y[];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) y[i] = (double)b[perm[i]];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    const double yk = y[k];
+    const double *lk = lu + (int64_t)k * n;
+    for (int i = k + 1 + tid; i < n; i += nt) y[i] -= lk[i] * yk;
+    __syncthreads();
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const double *uk = lu + (int64_t)k * n;
+    if (tid == 0) y[k] /= uk[k];
+    __syncthreads();
+    const double yk = y[k];
+    for (int i = tid; i < k; i += nt) y[i] -= uk[i] * yk;
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += nt) x[i] = (T)y[i];
+}
+
+template <typename T>
+__global__ void k_fill(T *x, int64_t n, T v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] = v;
+}
+
+template <typename T>
+__global__ void k_axpy_diag(T *__restrict__ x, const T *__restrict__ dinv, const T *__restrict__ t, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] -= dinv[i] * t[i];
+}
+
+template <typename T>
+__global__ void k_axpy(T *__restrict__ y, const T *__restrict__ x, T a, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] += a * x[i];
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (TO)in[i];
+}
+
+__global__ void k_scale(const double *x, double a, double *y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  }
+  return s;  // valid in thread 0
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_mdot(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ w, int64_t n,
+       double *__restrict__ partial, int nblk) {
+  __shared__ double sh[32];
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  for (int q = 0; q < k; ++q) {
+    const double *vq = V + (int64_t)q * ldv;
+    double acc = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += vq[i] * w[i];
+    const double s = block_sum(acc, sh);
+    if (threadIdx.x == 0) partial[(int64_t)q * nblk + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, double *__restrict__ out) {
+  __shared__ double sh[32];
+  const double *p = partial + (int64_t)blockIdx.x * nblk;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += p[i];
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_cgs_update(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ h,
+             double *__restrict__ w, int64_t n, double *__restrict__ partial, int nblk) {
+  __shared__ double hs[64];
+  __shared__ double sh[32];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
+  __syncthreads();
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  double nrm = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < k; ++q) s += V[(int64_t)q * ldv + i] * hs[q];
+    const double wn = w[i] - s;
+    w[i] = wn;
+    nrm += wn * wn;
+  }
+  if (partial != nullptr) {
+    const double t = block_sum(nrm, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_gemv_add(const double *__restrict__ Z, int64_t ldz, int k, const double *__restrict__ y,
+                           double *__restrict__ x, int64_t n) {
+  __shared__ double ys[64];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[q];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < k; ++q) s += Z[(int64_t)q * ldz + i] * ys[q];
+    x[i] += s;
+  }
+}
+
+inline unsigned ew_grid(int64_t n) {
+  int64_t g = (n + kThreads - 1) / kThreads;
+  if (g > 152 * 16) g = 152 * 16;
+  return (unsigned)(g > 0 ? g : 1);
+}
+
+}  // namespace
+
+#define MFS_BLOCK_DISPATCH(BRV, BCV, CALL)                                      \
+  switch (BRV * 16 + BCV) {                                                     \
+    case 1 * 16 + 1: { constexpr int BR_ = 1, BC_ = 1; CALL; } break;           \
+    case 1 * 16 + 2: { constexpr int BR_ = 1, BC_ = 2; CALL; } break;           \
+    case 1 * 16 + 3: { constexpr int BR_ = 1, BC_ = 3; CALL; } break;           \
+    case 1 * 16 + 6: { constexpr int BR_ = 1, BC_ = 6; CALL; } break;           \
+    case 2 * 16 + 1: { constexpr int BR_ = 2, BC_ = 1; CALL; } break;           \
+    case 2 * 16 + 2: { constexpr int BR_ = 2, BC_ = 2; CALL; } break;           \
+    case 2 * 16 + 3: { constexpr int BR_ = 2, BC_ = 3; CALL; } break;           \
+    case 2 * 16 + 6: { constexpr int BR_ = 2, BC_ = 6; CALL; } break;           \
+    case 3 * 16 + 1: { constexpr int BR_ = 3, BC_ = 1; CALL; } break;           \
+    case 3 * 16 + 2: { constexpr int BR_ = 3, BC_ = 2; CALL; } break;           \
+    case 3 * 16 + 3: { constexpr int BR_ = 3, BC_ = 3; CALL; } break;           \
+    case 3 * 16 + 6: { constexpr int BR_ = 3, BC_ = 6; CALL; } break;           \
+    case 6 * 16 + 1: { constexpr int BR_ = 6, BC_ = 1; CALL; } break;           \
+    case 6 * 16 + 2: { constexpr int BR_ = 6, BC_ = 2; CALL; } break;           \
+    case 6 * 16 + 3: { constexpr int BR_ = 6, BC_ = 3; CALL; } break;           \
+    case 6 * 16 + 6: { constexpr int BR_ = 6, BC_ = 6; CALL; } break;           \
+    default: fprintf(stderr, "mfs: unsupported block shape %dx%d\n", BRV, BCV); \
+  }
+
+void set_launch_hook(LaunchHook *h) { g_hook = h; }
+
+template <typename T>
+void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStream_t s) {
+  if (A.nbr == 0) return;
+  const T *v = vals<T>(A);
+  HookScope hs(s, K_SPMV, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + A.nrows() * (z ? 2 : 1)));
+  MFS_BLOCK_DISPATCH(A.br, A.bc,
+                     (k_spmv<BR_, BC_, T><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                         A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+}
+
+#define MFS_SQUARE_DISPATCH(BRV, CALL)                                  \
+  switch (BRV) {                                                        \
+    case 1: { constexpr int BR_ = 1; CALL; } break;                     \
+    case 2: { constexpr int BR_ = 2; CALL; } break;                     \
+    case 3: { constexpr int BR_ = 3; CALL; } break;                     \
+    case 6: { constexpr int BR_ = 6; CALL; } break;                     \
+    default: fprintf(stderr, "mfs: unsupported block size %d\n", BRV); \
+  }
+
+template <typename T>
+void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, T *d, T c1, T c2,
+                 cudaStream_t s) {
+  if (A.nbr == 0) return;
+  const T *v = vals<T>(A);
+  HookScope hs(s, K_SMOOTH, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + 5.0 * A.nrows()));
+  MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                                A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+}
+
+template <typename T>
+void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s) {
+  if (n == 0) return;
+  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T));
+  k_smooth_first<T><<<ew_grid(n), kThreads, 0, s>>>(n, dinv, b, x, d, c2);
+}
+
+template <typename T>
+void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
+  if (lu.n == 0) return;
+  HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n);
+  const size_t smem = (size_t)lu.n * sizeof(double);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaFuncSetAttribute(k_lu_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr_set = true;
+  }
+  k_lu_solve<T><<<1, 1024, smem, s>>>(lu.n, lu.lu, lu.perm, b, x);
+}
+
+template <typename T>
+void fill(T *x, int64_t n, T v, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, (double)n * sizeof(T));
+  if (n) k_fill<T><<<ew_grid(n), kThreads, 0, s>>>(x, n, v);
+}
+template <typename T>
+void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T));
+  if (n) k_axpy_diag<T><<<ew_grid(n), kThreads, 0, s>>>(x, dinv, t, n);
+}
+template <typename T>
+void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T));
+  if (n) k_axpy<T><<<ew_grid(n), kThreads, 0, s>>>(y, x, a, n);
+}
+template <typename TI, typename TO>
+void convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)));
+  if (n) k_convert<TI, TO><<<ew_grid(n), kThreads, 0, s>>>(in, out, n);
+}
+void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, 16.0 * n);
+  if (n) k_scale<<<ew_grid(n), kThreads, 0, s>>>(x, a, y, n);
+}
+
+int mdot_blocks(int64_t n) {
+  int64_t b = n / 2048;
+  if (b < 1) b = 1;
+  if (b > 152 * 4) b = 152 * 4;
+  return (int)b;
+}
+
+void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, double *partial, int nblk,
+          cudaStream_t s) {
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 1));
+  k_mdot<<<nblk, kThreads, 0, s>>>(V, ldv, k, w, n, partial, nblk);
+}
+
+void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s) {
+  HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk);
+  k_reduce_partials<<<k, kThreads, 0, s>>>(partial, nblk, out);
+}
+
+void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,
+                double *partial, int nblk, cudaStream_t s) {
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2));
+  k_cgs_update<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
+}
+
+void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2));
+  k_gemv_add<<<ew_grid(n), kThreads, 0, s>>>(Z, ldz, k, y, x, n);
+}
+
+#define MFS_INST(T)                                                                                   \
+  template void spmv<T>(const Sell &, const T *, T *, T, T, const T *, cudaStream_t);                 \
+  template void smooth_step<T>(const Sell &, const T *, const T *, const T *, T *, T *, T, T,         \
+                               cudaStream_t);                                                         \
+  template void smooth_first<T>(int64_t, const T *, const T *, T *, T *, T, cudaStream_t);            \
+  template void lu_solve<T>(const DenseLU &, const T *, T *, cudaStream_t);                           \
+  template void fill<T>(T *, int64_t, T, cudaStream_t);                                               \
+  template void axpy_diag<T>(T *, const T *, const T *, int64_t, cudaStream_t);                       \
+  template void axpy<T>(T *, const T *, T, int64_t, cudaStream_t);
+MFS_INST(double)
+MFS_INST(float)
+template void convert<double, float>(const double *, float *, int64_t, cudaStream_t);
+template void convert<float, double>(const float *, double *, int64_t, cudaStream_t);
+template void convert<double, double>(const double *, double *, int64_t, cudaStream_t);
+
+}  // namespace dev
+}  // namespace mfs

@@ -1,0 +1,88 @@
+// Device data layouts and kernel launchers of the solve phase.
+//
+// Block matrices are stored in a blocked SELL-32 layout: block rows are cut
+// into slices of 32 consecutive rows, one thread per block row; slot t of a
+// slice holds the t-th nonzero block of each of its 32 rows, with the 32
+// lanes' copies of block entry e next to each other, so every load of a warp
+// is one contiguous 128/256-byte segment.  Rows shorter than the slice width
+// are padded but the padding is never read (per-row lengths).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mfs {
+namespace dev {
+
+struct Sell {
+  int br = 0, bc = 0;
+  int64_t nbr = 0, nbc = 0;
+  int64_t nslices = 0, nslots = 0;
+  int64_t nnzb = 0;            // true nonzero blocks (algorithmic size)
+  const int32_t *sp = nullptr; // nslices + 1 slot offsets
+  const int32_t *rl = nullptr; // nbr row lengths
+  const int32_t *col = nullptr;// nslots * 32 block-column indices
+  const double *v64 = nullptr; // nslots * br*bc * 32
+  const float *v32 = nullptr;
+  bool valid() const { return nbr > 0 || nbc > 0; }
+  int64_t nrows() const { return nbr * br; }
+  int64_t ncols() const { return nbc * bc; }
+};
+
+// Optional per-launch accounting (CUDA events around every launch, with the
+// launch's algorithmic byte count); installed by the solver when profiling.
+enum KernelClass { K_SPMV = 0, K_SMOOTH = 1, K_VECTOR = 2, K_COARSE = 3, K_ARNOLDI = 4, K_NCLASS = 5 };
+struct LaunchHook {
+  virtual void before(cudaStream_t s) = 0;
+  virtual void after(cudaStream_t s, int cls, double bytes) = 0;
+  virtual ~LaunchHook() {}
+};
+void set_launch_hook(LaunchHook *h);
+
+template <typename T> inline const T *vals(const Sell &A);
+template <> inline const double *vals<double>(const Sell &A) { return A.v64; }
+template <> inline const float *vals<float>(const Sell &A) { return A.v32; }
+
+struct DenseLU {
+  int n = 0;
+  const double *lu = nullptr;   // column-major, unit-lower L and U
+  const int32_t *perm = nullptr;
+};
+
+// y = alpha * A x + beta * z   (z may alias y or be null when beta == 0)
+template <typename T>
+void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStream_t s);
+
+// One smoothing step on A with point-diagonal inverse dinv:
+//   r = b - A x;  d = c1 * d + c2 * dinv * r;  xout = x + d
+template <typename T>
+void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, T *d, T c1, T c2,
+                 cudaStream_t s);
+// First step from x = 0:  d = c2 * dinv * b;  x = d
+template <typename T>
+void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s);
+
+// x = LU^-1 b  (dense, one CTA; b, x of type T, arithmetic in float64)
+template <typename T>
+void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s);
+
+// elementwise helpers
+template <typename T> void fill(T *x, int64_t n, T v, cudaStream_t s);
+template <typename T> void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s);  // x -= dinv*t
+template <typename T> void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s);                 // y += a x
+template <typename TI, typename TO> void convert(const TI *in, TO *out, int64_t n, cudaStream_t s);
+void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s);                      // y = a x
+
+// Arnoldi (float64).  V holds k row vectors of length n, row q at V + q*ldv.
+int mdot_blocks(int64_t n);
+void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, double *partial,
+          int nblk, cudaStream_t s);                                   // partial[q*nblk+b]
+void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s);
+// w -= sum_q V_q h_q; if partial != null also partial[b] = sum w_new^2 over block b
+void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,
+                double *partial, int nblk, cudaStream_t s);
+// x += sum_q Z_q y_q
+void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, int64_t n,
+              cudaStream_t s);
+
+}  // namespace dev
+}  // namespace mfs

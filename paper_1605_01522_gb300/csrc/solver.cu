@@ -1,0 +1,1132 @@
+// libmfs: device hierarchy, block preconditioners, FGMRES and the C ABI.
+//
+//  * BGS(AMG)  (Sec. 4.1): k_max sweeps of block Gauss-Seidel from x = 0, one
+//    single-field V-cycle (Algorithm 1) per diagonal block;
+//  * SIMPLE    (Sec. 4.2): predictor / Schur / update steps on a 2 x 2 merging
+//    of the fields, SIMPLEC or diagonal A~_11, explicit S~;
+//  * AMG(BGS)  (Sec. 4.3): coupled V-cycle with block-diagonal transfers,
+//    blockwise Galerkin coarse blocks, BGS level smoothing and a dense LU of
+//    the assembled coarsest coupled matrix;
+//  * FGMRES(m) (Sec. 3.1-3.2, right preconditioning) with CGS2 Arnoldi and
+//    the Sec. 7.1 stopping rule.
+// Every step of a solve runs as a kernel of kernels.cu; the host only
+// sequences launches and runs the (m+1) x m Givens least-squares update.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "amg_setup.h"
+#include "kernels.cuh"
+#include "mfs.h"
+
+namespace mfs {
+
+struct CudaError : std::runtime_error {
+  int code;
+  CudaError(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+static thread_local std::string g_last_error;
+
+#define MFS_CUDA(call)                                                                      \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess)                                                                  \
+      throw CudaError(e_ == cudaErrorMemoryAllocation ? MFS_ERR_OOM : MFS_ERR_CUDA,         \
+                      std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+  } while (0)
+
+struct Arena {
+  std::vector<void *> ptrs;
+  template <typename T> T *alloc(int64_t count) {
+    if (count <= 0) return nullptr;
+    void *p = nullptr;
+    MFS_CUDA(cudaMalloc(&p, (size_t)count * sizeof(T)));
+    ptrs.push_back(p);
+    return (T *)p;
+  }
+  template <typename T> T *upload(const std::vector<T> &h) {
+    T *p = alloc<T>((int64_t)h.size());
+    if (p) MFS_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+  }
+  template <typename T> T *zeros(int64_t count) {
+    T *p = alloc<T>(count);
+    if (p) MFS_CUDA(cudaMemset(p, 0, (size_t)count * sizeof(T)));
+    return p;
+  }
+  ~Arena() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+};
+
+static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32) {
+  dev::Sell S;
+  S.br = A.br;
+  S.bc = A.bc;
+  S.nbr = A.nbr;
+  S.nbc = A.nbc;
+  S.nnzb = A.nnzb();
+  if (A.nbr == 0) return S;
+  const int bs = A.br * A.bc;
+  S.nslices = (A.nbr + 31) / 32;
+  std::vector<int32_t> sp(S.nslices + 1, 0), rl(A.nbr);
+  for (int64_t s = 0; s < S.nslices; ++s) {
+    int w = 0;
+    for (int64_t I = s * 32; I < std::min<int64_t>(A.nbr, s * 32 + 32); ++I) {
+      rl[I] = (int32_t)(A.rp[I + 1] - A.rp[I]);
+      w = std::max(w, rl[I]);
+    }
+    if ((int64_t)sp[s] + w > INT32_MAX / 32) throw SetupError(MFS_ERR_INVALID, "matrix too large for 32-bit slot offsets");
+    sp[s + 1] = sp[s] + w;
+  }
+  S.nslots = sp[S.nslices];
+  std::vector<int32_t> col((size_t)S.nslots * 32, 0);
+  std::vector<double> v64;
+  std::vector<float> v32;
+  if (want64) v64.assign((size_t)S.nslots * bs * 32, 0.0);
+  if (want32) v32.assign((size_t)S.nslots * bs * 32, 0.0f);
+  for (int64_t I = 0; I < A.nbr; ++I) {
+    const int64_t s = I >> 5, lane = I & 31;
+    for (int64_t t = 0; t < A.rp[I + 1] - A.rp[I]; ++t) {
+      const int64_t a = A.rp[I] + t, slot = sp[s] + t;
+      col[slot * 32 + lane] = A.ci[a];
+      for (int e = 0; e < bs; ++e) {
+        const size_t o = (size_t)(slot * bs + e) * 32 + lane;
+        if (want64) v64[o] = A.v[a * bs + e];
+        if (want32) v32[o] = (float)A.v[a * bs + e];
+      }
+    }
+  }
+  S.sp = ar.upload(sp);
+  S.rl = ar.upload(rl);
+  S.col = ar.upload(col);
+  if (want64) S.v64 = ar.upload(v64);
+  if (want32) S.v32 = ar.upload(v32);
+  return S;
+}
+
+static dev::DenseLU upload_lu(Arena &ar, const HDenseLU &lu) {
+  dev::DenseLU d;
+  d.n = lu.n;
+  if (lu.n > 16384) throw SetupError(MFS_ERR_INVALID, "coarsest level too large for the dense LU (raise max_levels or lower coarse_max)");
+  d.lu = ar.upload(lu.lu);
+  d.perm = ar.upload(lu.perm);
+  return d;
+}
+
+template <typename T> static T *upload_as(Arena &ar, const std::vector<double> &h) {
+  std::vector<T> t(h.begin(), h.end());
+  return ar.upload(t);
+}
+
+template <typename T> struct FL {
+  int64_t n = 0;
+  dev::Sell A, P, R;
+  T *dinv = nullptr;
+  std::vector<T> c1, c2;  // smoother step coefficients
+  T *bv = nullptr, *xv = nullptr, *t = nullptr, *d = nullptr, *r = nullptr, *c = nullptr, *e = nullptr;
+};
+
+template <typename T> struct DGroup {
+  int nf = 0, L = 0;
+  bool mono = false;
+  std::vector<std::vector<FL<T>>> lv;
+  std::vector<std::map<std::pair<int, int>, dev::Sell>> off;
+  std::vector<dev::DenseLU> cf;
+  dev::DenseLU cc;
+  T *cb = nullptr, *cx = nullptr;
+  const dev::Sell *block(int l, int i, int j) const {
+    if (i == j) return &lv[l][i].A;
+    auto it = off[l].find({i, j});
+    return it == off[l].end() ? nullptr : &it->second;
+  }
+};
+
+static void smoother_coeffs(const mfs_params &p, double lam, std::vector<double> &c1, std::vector<double> &c2) {
+  c1.clear();
+  c2.clear();
+  if (p.smoother == MFS_JACOBI) {
+    for (int k = 0; k < p.jacobi_sweeps; ++k) {
+      c1.push_back(0.0);
+      c2.push_back(p.jacobi_omega);
+    }
+    return;
+  }
+  const double hi = p.cheb_boost * lam, lo = lam / p.cheb_ratio;
+  const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  c1.push_back(0.0);
+  c2.push_back(1.0 / theta);
+  for (int k = 1; k < p.cheb_degree; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    c1.push_back(rn * rho);
+    c2.push_back(2.0 * rn / delta);
+    rho = rn;
+  }
+}
+
+// Build the device copy of a host group.  level0 gives the Sell objects of
+// the level-0 diagonal / off-diagonal blocks (shared with the fine operator).
+template <typename T>
+static void upload_group(Arena &ar, DGroup<T> &g, const HGroup &h, const mfs_params &p,
+                         const std::vector<dev::Sell> &level0_diag,
+                         const std::map<std::pair<int, int>, dev::Sell> &level0_off, bool mono) {
+  const bool f32 = std::is_same<T, float>::value;
+  g.nf = h.nf;
+  g.L = h.nlevels();
+  g.mono = mono;
+  g.lv.assign(g.L, std::vector<FL<T>>(g.nf));
+  g.off.assign(g.L, {});
+  g.off[0] = level0_off;
+  for (int l = 0; l < g.L; ++l) {
+    for (int i = 0; i < g.nf; ++i) {
+      const HLevelField &hf = h.lv[l][i];
+      FL<T> &f = g.lv[l][i];
+      f.n = hf.A.nrows();
+      f.A = l == 0 ? level0_diag[i] : upload_sell(ar, hf.A, !f32, f32);
+      if (l + 1 < g.L) {
+        f.P = upload_sell(ar, hf.P, !f32, f32);
+        f.R = upload_sell(ar, hf.R, !f32, f32);
+        std::vector<double> c1, c2;
+        smoother_coeffs(p, hf.lam, c1, c2);
+        f.c1.assign(c1.begin(), c1.end());
+        f.c2.assign(c2.begin(), c2.end());
+        f.dinv = upload_as<T>(ar, hf.dinv);
+        f.t = ar.zeros<T>(f.n);
+        f.d = ar.zeros<T>(f.n);
+        f.r = ar.zeros<T>(f.n);
+      }
+      f.c = ar.zeros<T>(f.n);
+      f.e = ar.zeros<T>(f.n);
+    }
+    if (l > 0 && mono)
+      for (auto &kv : h.off[l]) g.off[l][kv.first] = upload_sell(ar, kv.second, !f32, f32);
+  }
+  // level vectors of coarse levels; the coarsest ones contiguous for the coupled LU
+  int64_t ctot = 0;
+  for (int i = 0; i < g.nf; ++i) ctot += g.lv[g.L - 1][i].n;
+  if (g.L > 1 || mono) {
+    g.cb = ar.zeros<T>(ctot);
+    g.cx = ar.zeros<T>(ctot);
+  }
+  int64_t o = 0;
+  for (int i = 0; i < g.nf; ++i) {
+    for (int l = 1; l < g.L - 1; ++l) {
+      g.lv[l][i].bv = ar.zeros<T>(g.lv[l][i].n);
+      g.lv[l][i].xv = ar.zeros<T>(g.lv[l][i].n);
+    }
+    if (g.L > 1 || mono) {
+      g.lv[g.L - 1][i].bv = g.cb + o;
+      g.lv[g.L - 1][i].xv = g.cx + o;
+    }
+    o += g.lv[g.L - 1][i].n;
+  }
+  g.cf.resize(g.nf);
+  for (int i = 0; i < g.nf; ++i) g.cf[i] = upload_lu(ar, h.coarse_field[i]);
+  if (mono) g.cc = upload_lu(ar, h.coarse_coupled);
+}
+
+template <typename T> struct Precond {
+  int kind = 0, nf = 0, order = 0, sweeps = 1;
+  std::vector<int64_t> fsize, foff;
+  DGroup<T> g0, g1;
+  std::vector<int> G1, G2;
+  std::map<std::pair<int, int>, dev::Sell> cross;
+  std::vector<T *> dtinv, sr2, st;
+  cudaStream_t s = nullptr;
+
+  // single-field polynomial smoother S^l_i; zero: x enters as 0
+  void smooth(FL<T> &f, const T *rhs, T *x, bool zero) {
+    const int ns = (int)f.c1.size();
+    T *cur = x, *oth = f.t;
+    int k0 = 0;
+    if (zero) {
+      T *tgt = ((ns - 1) % 2 == 0) ? x : f.t;
+      dev::smooth_first<T>(f.n, f.dinv, rhs, tgt, f.d, f.c2[0], s);
+      cur = tgt;
+      oth = tgt == x ? f.t : x;
+      k0 = 1;
+    }
+    for (int k = k0; k < ns; ++k) {
+      dev::smooth_step<T>(f.A, f.dinv, rhs, cur, oth, f.d, f.c1[k], f.c2[k], s);
+      std::swap(cur, oth);
+    }
+    if (cur != x) MFS_CUDA(cudaMemcpyAsync(x, cur, f.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  }
+
+  // Algorithm 1 for field i of group g from level l, zero initial guess
+  void vcycle(DGroup<T> &g, int i, int l, const T *rhs, T *x) {
+    FL<T> &f = g.lv[l][i];
+    if (l == g.L - 1) {
+      dev::lu_solve<T>(g.cf[i], rhs, x, s);
+      return;
+    }
+    FL<T> &c = g.lv[l + 1][i];
+    smooth(f, rhs, x, true);
+    dev::spmv<T>(f.A, x, f.r, T(-1), T(1), rhs, s);
+    dev::spmv<T>(f.R, f.r, c.bv, T(1), T(0), nullptr, s);
+    vcycle(g, i, l + 1, c.bv, c.xv);
+    dev::spmv<T>(f.P, c.xv, x, T(1), T(1), x, s);
+    smooth(f, rhs, x, false);
+  }
+
+  static std::vector<std::vector<int>> orders(int order, int nf) {
+    std::vector<int> fwd(nf), bwd(nf);
+    for (int i = 0; i < nf; ++i) {
+      fwd[i] = i;
+      bwd[i] = nf - 1 - i;
+    }
+    if (order == MFS_FWD) return {fwd};
+    if (order == MFS_BWD) return {bwd};
+    return {fwd, bwd};
+  }
+
+  // block Gauss-Seidel on level 0 of group g with V-cycle block solves
+  void bgs(DGroup<T> &g, const std::vector<const T *> &b, const std::vector<T *> &x) {
+    std::vector<char> nz(g.nf, 0);
+    for (int sw = 0; sw < sweeps; ++sw)
+      for (auto &seq : orders(order, g.nf))
+        for (int i : seq) {
+          FL<T> &f = g.lv[0][i];
+          const T *rhs = b[i];
+          for (int j = 0; j < g.nf; ++j) {
+            if (!nz[j]) continue;
+            const dev::Sell *M = g.block(0, i, j);
+            if (!M) continue;
+            dev::spmv<T>(*M, x[j], f.c, T(-1), T(1), rhs, s);
+            rhs = f.c;
+          }
+          if (!nz[i]) {
+            vcycle(g, i, 0, rhs, x[i]);
+            nz[i] = 1;
+          } else {
+            vcycle(g, i, 0, rhs, f.e);
+            dev::axpy<T>(x[i], f.e, T(1), f.n, s);
+          }
+        }
+  }
+
+  void mono_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero) {
+    std::vector<char> nz(g.nf, zero ? 0 : 1);
+    for (int sw = 0; sw < sweeps; ++sw)
+      for (auto &seq : orders(order, g.nf))
+        for (int i : seq) {
+          FL<T> &f = g.lv[l][i];
+          const T *rhs = b[i];
+          for (int j = 0; j < g.nf; ++j) {
+            if (j == i || !nz[j]) continue;
+            const dev::Sell *M = g.block(l, i, j);
+            if (!M) continue;
+            dev::spmv<T>(*M, x[j], f.c, T(-1), T(1), rhs, s);
+            rhs = f.c;
+          }
+          smooth(f, rhs, x[i], !nz[i]);
+          nz[i] = 1;
+        }
+  }
+
+  void mono_cycle(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x) {
+    if (l == g.L - 1) {
+      for (int i = 0; i < g.nf; ++i)
+        if (b[i] != g.lv[l][i].bv)
+          MFS_CUDA(cudaMemcpyAsync(g.lv[l][i].bv, b[i], g.lv[l][i].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      dev::lu_solve<T>(g.cc, g.cb, g.cx, s);
+      for (int i = 0; i < g.nf; ++i)
+        if (x[i] != g.lv[l][i].xv)
+          MFS_CUDA(cudaMemcpyAsync(x[i], g.lv[l][i].xv, g.lv[l][i].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      return;
+    }
+    mono_smooth(g, l, b, x, true);
+    std::vector<const T *> bc(g.nf);
+    std::vector<T *> xc(g.nf);
+    for (int i = 0; i < g.nf; ++i) {
+      FL<T> &f = g.lv[l][i];
+      dev::spmv<T>(f.A, x[i], f.r, T(-1), T(1), b[i], s);
+      for (int j = 0; j < g.nf; ++j) {
+        if (j == i) continue;
+        const dev::Sell *M = g.block(l, i, j);
+        if (M) dev::spmv<T>(*M, x[j], f.r, T(-1), T(1), f.r, s);
+      }
+      dev::spmv<T>(f.R, f.r, g.lv[l + 1][i].bv, T(1), T(0), nullptr, s);
+      bc[i] = g.lv[l + 1][i].bv;
+      xc[i] = g.lv[l + 1][i].xv;
+    }
+    mono_cycle(g, l + 1, bc, xc);
+    for (int i = 0; i < g.nf; ++i) dev::spmv<T>(g.lv[l][i].P, xc[i], x[i], T(1), T(1), x[i], s);
+    mono_smooth(g, l, b, x, false);
+  }
+
+  void apply(const T *in, T *out) {
+    std::vector<const T *> b(nf);
+    std::vector<T *> x(nf);
+    for (int i = 0; i < nf; ++i) {
+      b[i] = in + foff[i];
+      x[i] = out + foff[i];
+    }
+    if (kind == MFS_BGS_AMG) {
+      bgs(g0, b, x);
+    } else if (kind == MFS_AMG_BGS) {
+      mono_cycle(g0, 0, b, x);
+    } else {
+      std::vector<const T *> b1, b2;
+      std::vector<T *> x1, x2;
+      for (int j : G1) {
+        b1.push_back(b[j]);
+        x1.push_back(x[j]);
+      }
+      for (int k : G2) x2.push_back(x[k]);
+      // predictor
+      if (G1.size() == 1) vcycle(g0, 0, 0, b1[0], x1[0]);
+      else bgs(g0, b1, x1);
+      // Schur right-hand side b_2 - A_21 dx_1
+      for (size_t kk = 0; kk < G2.size(); ++kk) {
+        const T *rhs = b[G2[kk]];
+        for (size_t jj = 0; jj < G1.size(); ++jj) {
+          auto it = cross.find({G2[kk], G1[jj]});
+          if (it == cross.end()) continue;
+          dev::spmv<T>(it->second, x1[jj], sr2[kk], T(-1), T(1), rhs, s);
+          rhs = sr2[kk];
+        }
+        b2.push_back(rhs);
+      }
+      if (G2.size() == 1) vcycle(g1, 0, 0, b2[0], x2[0]);
+      else bgs(g1, b2, x2);
+      // update x_1 = dx_1 - A~11^-1 A_12 dx_2
+      for (size_t jj = 0; jj < G1.size(); ++jj) {
+        bool any = false;
+        for (size_t kk = 0; kk < G2.size(); ++kk) {
+          auto it = cross.find({G1[jj], G2[kk]});
+          if (it == cross.end()) continue;
+          dev::spmv<T>(it->second, x2[kk], st[jj], T(1), any ? T(1) : T(0), any ? st[jj] : nullptr, s);
+          any = true;
+        }
+        if (any) dev::axpy_diag<T>(x1[jj], dtinv[jj], st[jj], fsize[G1[jj]], s);
+      }
+    }
+  }
+};
+
+// Per-launch CUDA-event accounting by kernel class (enabled by params.profile).
+struct EventProf : dev::LaunchHook {
+  std::vector<cudaEvent_t> ev;
+  size_t used = 0;
+  std::vector<std::pair<int, double>> meta;
+  double ms[dev::K_NCLASS] = {0}, bytes[dev::K_NCLASS] = {0}, launches[dev::K_NCLASS] = {0};
+  cudaEvent_t next() {
+    if (used == ev.size()) {
+      cudaEvent_t e;
+      MFS_CUDA(cudaEventCreate(&e));
+      ev.push_back(e);
+    }
+    return ev[used++];
+  }
+  void before(cudaStream_t s) override { MFS_CUDA(cudaEventRecord(next(), s)); }
+  void after(cudaStream_t s, int cls, double b) override {
+    MFS_CUDA(cudaEventRecord(next(), s));
+    meta.push_back({cls, b});
+  }
+  void collect() {
+    if (used) MFS_CUDA(cudaEventSynchronize(ev[used - 1]));
+    for (size_t k = 0; k < meta.size(); ++k) {
+      float t = 0.f;
+      MFS_CUDA(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
+      ms[meta[k].first] += t;
+      bytes[meta[k].first] += meta[k].second;
+      launches[meta[k].first] += 1;
+    }
+    used = 0;
+    meta.clear();
+  }
+  void reset() {
+    for (int c = 0; c < dev::K_NCLASS; ++c) ms[c] = bytes[c] = launches[c] = 0;
+  }
+  ~EventProf() override {
+    for (auto e : ev) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace mfs
+
+using namespace mfs;
+
+struct mfs_handle {
+  mfs_params prm{};
+  int nf = 0;
+  std::vector<int64_t> fsize, foff;
+  int64_t n = 0;
+  cudaStream_t s = nullptr;
+  Arena ar;
+  std::map<std::pair<int, int>, dev::Sell> A64;
+  std::unique_ptr<Precond<double>> p64;
+  std::unique_ptr<Precond<float>> p32;
+  HGroup hg0, hg1;
+  std::vector<std::vector<double>> dtilde;
+  BlockMap schur_off;
+  std::vector<HBsr> schur_diag;
+  std::vector<int> G1, G2;
+  bool host_only = false;
+  // solve workspace
+  int m = 0, nblk = 1;
+  double *V = nullptr, *Z = nullptr, *xd = nullptr, *bd = nullptr, *rd = nullptr, *partial = nullptr;
+  double *hdev = nullptr, *ydev = nullptr;
+  float *in32 = nullptr, *out32 = nullptr;
+  double *hpin = nullptr;
+  double setup_ms = 0.0;
+  std::unique_ptr<EventProf> prof;
+  ~mfs_handle() {
+    if (hpin) cudaFreeHost(hpin);
+  }
+};
+
+namespace {
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void matvec(mfs_handle *h, const double *x, double *y) {
+  for (int i = 0; i < h->nf; ++i) {
+    bool first = true;
+    for (int j = 0; j < h->nf; ++j) {
+      auto it = h->A64.find({i, j});
+      if (it == h->A64.end()) continue;
+      dev::spmv<double>(it->second, x + h->foff[j], y + h->foff[i], 1.0, first ? 0.0 : 1.0,
+                        first ? nullptr : y + h->foff[i], h->s);
+      first = false;
+    }
+    if (first) dev::fill<double>(y + h->foff[i], h->fsize[i], 0.0, h->s);
+  }
+}
+
+void precond_apply(mfs_handle *h, const double *v, double *z) {
+  if (h->p64) {
+    h->p64->apply(v, z);
+  } else {
+    dev::convert<double, float>(v, h->in32, h->n, h->s);
+    h->p32->apply(h->in32, h->out32);
+    dev::convert<float, double>(h->out32, z, h->n, h->s);
+  }
+}
+
+// ||x||^2 of n doubles, deterministic, result in host memory
+double dot_host(mfs_handle *h, const double *x, const double *y) {
+  dev::mdot(x, 0, 1, y, h->n, h->partial, h->nblk, h->s);
+  dev::reduce_partials(h->partial, 1, h->nblk, h->hdev, h->s);
+  MFS_CUDA(cudaMemcpyAsync(h->hpin, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  MFS_CUDA(cudaStreamSynchronize(h->s));
+  return h->hpin[0];
+}
+
+int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info) {
+  const int64_t n = h->n;
+  const int m = h->m;
+  cudaStream_t s = h->s;
+  double *r = h->rd;
+  // r = b - A x
+  matvec(h, x, r);
+  dev::axpy<double>(r, b, -1.0, n, s);
+  dev::scale(r, -1.0, r, n, s);
+  const double r0 = std::sqrt(dot_host(h, r, r));
+  int iters = 0, restarts = 0;
+  double est = 1.0, relres = 0.0;
+  if (r0 == 0.0) {
+    info->iters = 0;
+    info->converged = 1;
+    info->true_relres = 0.0;
+    info->est_relres = 0.0;
+    return MFS_OK;
+  }
+  if (!std::isfinite(r0)) return MFS_ERR_BREAKDOWN;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  double *hp = h->hpin;
+  while (true) {
+    const double beta = std::sqrt(dot_host(h, r, r));
+    dev::scale(r, 1.0 / beta, h->V, n, s);
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jend = 0;
+    bool stop = false;
+    for (int j = 0; j < m; ++j) {
+      double *vj = h->V + (int64_t)j * n;
+      double *zj = h->Z + (int64_t)j * n;
+      double *w = h->V + (int64_t)(j + 1) * n;
+      precond_apply(h, vj, zj);
+      matvec(h, zj, w);
+      // CGS2: h1 = V^T w (and |w|^2), w -= V h1, h2 = V^T w, w -= V h2 (and |w|^2)
+      dev::mdot(h->V, n, j + 2, w, n, h->partial, h->nblk, s);
+      dev::reduce_partials(h->partial, j + 2, h->nblk, h->hdev, s);
+      dev::cgs_update(h->V, n, j + 1, h->hdev, w, n, nullptr, h->nblk, s);
+      dev::mdot(h->V, n, j + 1, w, n, h->partial, h->nblk, s);
+      dev::reduce_partials(h->partial, j + 1, h->nblk, h->hdev + 64, s);
+      dev::cgs_update(h->V, n, j + 1, h->hdev + 64, w, n, h->partial, h->nblk, s);
+      dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + 128, s);
+      MFS_CUDA(cudaMemcpyAsync(hp, h->hdev, 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      MFS_CUDA(cudaStreamSynchronize(s));
+      const double nw0 = std::sqrt(hp[j + 1]);
+      const double hn = std::sqrt(hp[128]);
+      if (!std::isfinite(hn) || !std::isfinite(nw0)) return MFS_ERR_BREAKDOWN;
+      double *Hj = H.data() + (size_t)j * (m + 1);  // column j
+      for (int k = 0; k <= j; ++k) Hj[k] = hp[k] + hp[64 + k];
+      Hj[j + 1] = hn;
+      for (int k = 0; k < j; ++k) {
+        const double a = Hj[k], c = Hj[k + 1];
+        Hj[k] = cs[k] * a + sn[k] * c;
+        Hj[k + 1] = -sn[k] * a + cs[k] * c;
+      }
+      if (Hj[j + 1] == 0.0) {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+      } else {
+        const double rr = std::hypot(Hj[j], Hj[j + 1]);
+        cs[j] = Hj[j] / rr;
+        sn[j] = Hj[j + 1] / rr;
+      }
+      Hj[j] = cs[j] * Hj[j] + sn[j] * Hj[j + 1];
+      Hj[j + 1] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++iters;
+      jend = j + 1;
+      est = std::fabs(g[j + 1]) / r0;
+      const bool happy = hn <= 1e-14 * nw0;
+      if (est <= tol || happy || iters >= h->prm.max_iters) {
+        stop = true;
+        break;
+      }
+      dev::scale(w, 1.0 / hn, w, n, s);
+    }
+    (void)stop;
+    for (int k = jend - 1; k >= 0; --k) {
+      double sum = g[k];
+      for (int q = k + 1; q < jend; ++q) sum -= H[(size_t)q * (m + 1) + k] * y[q];
+      y[k] = sum / H[(size_t)k * (m + 1) + k];
+    }
+    MFS_CUDA(cudaMemcpyAsync(h->ydev, y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, s));
+    dev::gemv_add(h->Z, n, jend, h->ydev, x, n, s);
+    matvec(h, x, r);
+    dev::axpy<double>(r, b, -1.0, n, s);
+    dev::scale(r, -1.0, r, n, s);
+    relres = std::sqrt(dot_host(h, r, r)) / r0;
+    if (!std::isfinite(relres)) return MFS_ERR_BREAKDOWN;
+    if (relres <= tol || iters >= h->prm.max_iters) break;
+    ++restarts;
+  }
+  info->iters = iters;
+  info->restarts = restarts;
+  info->true_relres = relres;
+  info->est_relres = est;
+  info->converged = relres <= tol ? 1 : 0;
+  return info->converged ? MFS_OK : MFS_ERR_NOT_CONVERGED;
+}
+
+HBsr to_hbsr(const mfs_block &b) {
+  HBsr A;
+  A.br = b.br;
+  A.bc = b.bc;
+  A.nbr = b.nbrows;
+  A.nbc = b.nbcols;
+  A.rp.assign(b.rowptr, b.rowptr + b.nbrows + 1);
+  A.ci.assign(b.colind, b.colind + b.nnzb);
+  A.v.assign(b.vals, b.vals + b.nnzb * b.br * b.bc);
+  if (A.rp[0] != 0 || A.rp[A.nbr] != b.nnzb) throw SetupError(MFS_ERR_INVALID, "block rowptr inconsistent with nnzb");
+  for (int64_t I = 0; I < A.nbr; ++I) {
+    if (A.rp[I + 1] < A.rp[I]) throw SetupError(MFS_ERR_INVALID, "block rowptr not monotone");
+    for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a) {
+      if (A.ci[a] < 0 || A.ci[a] >= A.nbc) throw SetupError(MFS_ERR_INVALID, "block column index out of range");
+      if (a > A.rp[I] && A.ci[a] <= A.ci[a - 1]) throw SetupError(MFS_ERR_INVALID, "block columns not sorted/unique");
+    }
+  }
+  return A;
+}
+
+// Host half of the setup: hierarchies, SIMPLE diagonal and explicit S~.
+void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks,
+                const std::vector<FieldInfo> &info) {
+  const mfs_params &p = h->prm;
+  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS) {
+    std::vector<HBsr> diag;
+    BlockMap off;
+    for (auto &kv : blocks)
+      if (kv.first.first == kv.first.second) diag.push_back(kv.second);
+      else off[kv.first] = kv.second;
+    build_group(h->hg0, diag, info, p.max_levels, p.coarse_max, p.seed, p.precond == MFS_AMG_BGS, &off);
+    return;
+  }
+  h->G1.clear();
+  h->G2.clear();
+  bool any = false;
+  for (int i = 0; i < h->nf; ++i) any |= p.simple_group[i] != 0;
+  for (int i = 0; i < h->nf; ++i) {
+    const bool schur = any ? p.simple_group[i] != 0 : i == h->nf - 1;
+    (schur ? h->G2 : h->G1).push_back(i);
+  }
+  if (h->G1.empty() || h->G2.empty()) throw SetupError(MFS_ERR_INVALID, "SIMPLE needs a non-empty predictor and Schur group");
+  std::map<int, int> l2;
+  for (size_t a = 0; a < h->G2.size(); ++a) l2[h->G2[a]] = (int)a;
+  std::vector<HBsr> diag1;
+  std::vector<FieldInfo> info1;
+  for (int j : h->G1) {
+    diag1.push_back(blocks.at({j, j}));
+    info1.push_back(info[j]);
+  }
+  build_group(h->hg0, diag1, info1, p.max_levels, p.coarse_max, p.seed, false, nullptr);
+  // A~_11: SIMPLEC sums of absolute entries over the merged predictor rows, or the diagonal
+  h->dtilde.clear();
+  for (int j : h->G1) {
+    std::vector<double> d(h->fsize[j], 0.0);
+    if (p.simple_approx == MFS_DIAG) {
+      d = bsr_point_diagonal(blocks.at({j, j}));
+    } else {
+      for (int l : h->G1) {
+        auto it = blocks.find({j, l});
+        if (it == blocks.end()) continue;
+        std::vector<double> sr = bsr_abs_row_sums(it->second);
+        for (int64_t r = 0; r < (int64_t)d.size(); ++r) d[r] += sr[r];
+      }
+    }
+    for (double v : d)
+      if (v == 0.0) throw SetupError(MFS_ERR_SINGULAR, "zero entry in the SIMPLE diagonal approximation");
+    h->dtilde.push_back(d);
+  }
+  // S~_kl = A_kl - sum_j A_kj diag(1/d~_j) A_jl
+  std::vector<FieldInfo> sinfo;
+  h->schur_off.clear();
+  h->schur_diag.clear();
+  for (int k : h->G2)
+    for (int l : h->G2) {
+      HBsr M;
+      bool have = false;
+      auto it = blocks.find({k, l});
+      if (it != blocks.end()) {
+        M = it->second;
+        have = true;
+      }
+      for (size_t jj = 0; jj < h->G1.size(); ++jj) {
+        const int j = h->G1[jj];
+        auto a = blocks.find({k, j});
+        auto c = blocks.find({j, l});
+        if (a == blocks.end() || c == blocks.end()) continue;
+        HBsr Cs = c->second;
+        std::vector<double> inv(h->dtilde[jj].size());
+        for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / h->dtilde[jj][r];
+        bsr_scale_rows(Cs, inv);
+        HBsr Tm = bsr_spgemm(a->second, Cs);
+        if (have) {
+          M = bsr_axpby(1.0, M, -1.0, Tm);
+        } else {
+          M = bsr_axpby(0.0, Tm, -1.0, Tm);
+          have = true;
+        }
+      }
+      if (!have) continue;
+      if (k == l) {
+        h->schur_diag.push_back(M);
+        FieldInfo fi = info[k];
+        fi.ns = 0;
+        sinfo.push_back(fi);
+      } else {
+        h->schur_off[{l2[k], l2[l]}] = M;
+      }
+    }
+  if (h->schur_diag.size() != h->G2.size()) throw SetupError(MFS_ERR_INVALID, "missing Schur diagonal block");
+  build_group(h->hg1, h->schur_diag, sinfo, p.max_levels, p.coarse_max, p.seed, false, nullptr);
+}
+
+// Device half of the setup: upload the host hierarchy in precision T.
+template <typename T>
+void upload_precond(mfs_handle *h, Precond<T> &P, const std::map<std::pair<int, int>, HBsr> &blocks, bool f32) {
+  const mfs_params &p = h->prm;
+  P.kind = p.precond;
+  P.nf = h->nf;
+  P.order = p.bgs_order;
+  P.sweeps = p.bgs_sweeps;
+  P.fsize = h->fsize;
+  P.foff = h->foff;
+  P.s = h->s;
+  auto fine_sell = [&](int i, int j) { return h->A64.at({i, j}); };
+  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS) {
+    std::vector<dev::Sell> d0;
+    std::map<std::pair<int, int>, dev::Sell> o0;
+    for (int i = 0; i < h->nf; ++i) d0.push_back(fine_sell(i, i));
+    for (auto &kv : blocks)
+      if (kv.first.first != kv.first.second) o0[kv.first] = fine_sell(kv.first.first, kv.first.second);
+    upload_group(h->ar, P.g0, h->hg0, p, d0, o0, p.precond == MFS_AMG_BGS);
+    return;
+  }
+  P.G1 = h->G1;
+  P.G2 = h->G2;
+  std::map<int, int> l1, l2;
+  for (size_t a = 0; a < h->G1.size(); ++a) l1[h->G1[a]] = (int)a;
+  for (size_t a = 0; a < h->G2.size(); ++a) l2[h->G2[a]] = (int)a;
+  std::vector<dev::Sell> d0;
+  std::map<std::pair<int, int>, dev::Sell> o0;
+  for (int j : h->G1) d0.push_back(fine_sell(j, j));
+  for (auto &kv : blocks) {
+    const int i = kv.first.first, j = kv.first.second;
+    if (i != j && l1.count(i) && l1.count(j)) o0[{l1[i], l1[j]}] = fine_sell(i, j);
+    if ((l1.count(i) && l2.count(j)) || (l2.count(i) && l1.count(j))) P.cross[kv.first] = fine_sell(i, j);
+  }
+  upload_group(h->ar, P.g0, h->hg0, p, d0, o0, false);
+  std::vector<dev::Sell> sd0;
+  std::map<std::pair<int, int>, dev::Sell> so0;
+  for (auto &M : h->schur_diag) sd0.push_back(upload_sell(h->ar, M, !f32, f32));
+  for (auto &kv : h->schur_off) so0[kv.first] = upload_sell(h->ar, kv.second, !f32, f32);
+  upload_group(h->ar, P.g1, h->hg1, p, sd0, so0, false);
+  for (size_t jj = 0; jj < h->G1.size(); ++jj) {
+    std::vector<double> inv(h->dtilde[jj].size());
+    for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / h->dtilde[jj][r];
+    P.dtinv.push_back(upload_as<T>(h->ar, inv));
+    P.st.push_back(h->ar.zeros<T>(h->fsize[h->G1[jj]]));
+  }
+  for (int k : h->G2) P.sr2.push_back(h->ar.zeros<T>(h->fsize[k]));
+}
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mfs_default_params(mfs_params *p) {
+  std::memset(p, 0, sizeof(*p));
+  p->precond = MFS_BGS_AMG;
+  p->bgs_order = MFS_BWD;
+  p->bgs_sweeps = 1;
+  for (int i = 0; i < MFS_MAX_FIELDS; ++i) p->simple_group[i] = 0;
+  p->simple_approx = MFS_ABSROWSUM;
+  p->max_levels = 4;
+  p->coarse_max = 1000;
+  p->smoother = MFS_CHEBYSHEV;
+  p->cheb_degree = 2;
+  p->cheb_ratio = 30.0;
+  p->cheb_boost = 1.1;
+  p->jacobi_omega = 2.0 / 3.0;
+  p->jacobi_sweeps = 1;
+  p->restart = 50;
+  p->max_iters = 1000;
+  p->precision = MFS_FP64;
+  p->seed = 7;
+  p->cuda_stream = nullptr;
+  p->verbose = 0;
+}
+
+int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int nfields,
+              const mfs_params *params, mfs_handle **out) {
+  if (!out) return fail(MFS_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!blocks || !fields || !params || nfields < 1 || nfields > MFS_MAX_FIELDS || nblocks < nfields)
+    return fail(MFS_ERR_INVALID, "bad block/field arguments");
+  const mfs_params &p = *params;
+  if (p.precond < 0 || p.precond > 2 || p.bgs_order < 0 || p.bgs_order > 2 || p.bgs_sweeps < 1 ||
+      p.max_levels < 1 || p.coarse_max < 0 || p.restart < 1 || p.restart > 60 || p.max_iters < 1 ||
+      (p.smoother == MFS_CHEBYSHEV && (p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0))) ||
+      (p.smoother == MFS_JACOBI && p.jacobi_sweeps < 1) || (p.smoother != MFS_CHEBYSHEV && p.smoother != MFS_JACOBI) ||
+      (p.precision != MFS_FP64 && p.precision != MFS_FP32P))
+    return fail(MFS_ERR_INVALID, "bad parameters");
+  const bool host_only = p.setup_only != 0;
+  int ndev = 0;
+  if (!host_only && (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)) {
+    cudaGetLastError();
+    return fail(MFS_ERR_CUDA, "no CUDA device");
+  }
+  const double t0 = now_ms();
+  std::unique_ptr<mfs_handle> h(new mfs_handle());
+  try {
+    h->prm = p;
+    h->nf = nfields;
+    h->s = (cudaStream_t)p.cuda_stream;
+    std::vector<FieldInfo> info(nfields);
+    h->foff.assign(nfields + 1, 0);
+    for (int i = 0; i < nfields; ++i) {
+      const mfs_field &f = fields[i];
+      if (f.nnodes < 1 || f.dofs_per_node < 1 || f.dofs_per_node > 6 || f.strength_theta < 0)
+        throw SetupError(MFS_ERR_INVALID, "bad field");
+      info[i].nnodes = f.nnodes;
+      info[i].b = f.dofs_per_node;
+      info[i].dim = f.dim;
+      info[i].ns = f.nullspace;
+      info[i].theta = f.strength_theta;
+      if (f.nullspace == MFS_NS_RBM) {
+        if (!f.coords || f.dim != f.dofs_per_node || (f.dim != 2 && f.dim != 3))
+          throw SetupError(MFS_ERR_INVALID, "rigid-body modes need coords and dofs_per_node == dim in {2,3}");
+        info[i].coords.assign(f.coords, f.coords + f.nnodes * f.dim);
+      } else if (f.nullspace != MFS_NS_CONST) {
+        throw SetupError(MFS_ERR_INVALID, "bad nullspace kind");
+      }
+      h->fsize.push_back(f.nnodes * f.dofs_per_node);
+      h->foff[i + 1] = h->foff[i] + h->fsize[i];
+    }
+    h->n = h->foff[nfields];
+    std::map<std::pair<int, int>, HBsr> hb;
+    for (int k = 0; k < nblocks; ++k) {
+      const mfs_block &b = blocks[k];
+      if (b.i < 0 || b.j < 0 || b.i >= nfields || b.j >= nfields || hb.count({b.i, b.j}))
+        throw SetupError(MFS_ERR_INVALID, "bad or repeated block index");
+      if (b.br != fields[b.i].dofs_per_node || b.bc != fields[b.j].dofs_per_node ||
+          b.nbrows != fields[b.i].nnodes || b.nbcols != fields[b.j].nnodes || !b.rowptr || (b.nnzb && (!b.colind || !b.vals)))
+        throw SetupError(MFS_ERR_INVALID, "block shape does not match the field map");
+      hb[{b.i, b.j}] = to_hbsr(b);
+    }
+    for (int i = 0; i < nfields; ++i)
+      if (!hb.count({i, i})) throw SetupError(MFS_ERR_INVALID, "missing diagonal block");
+    build_host(h.get(), hb, info);
+    h->host_only = host_only;
+    if (host_only) {
+      h->setup_ms = now_ms() - t0;
+      *out = h.release();
+      return MFS_OK;
+    }
+    const bool f32 = p.precision == MFS_FP32P;
+    for (auto &kv : hb) h->A64[kv.first] = upload_sell(h->ar, kv.second, true, f32);
+    if (f32) {
+      h->p32.reset(new Precond<float>());
+      upload_precond<float>(h.get(), *h->p32, hb, true);
+      h->in32 = h->ar.zeros<float>(h->n);
+      h->out32 = h->ar.zeros<float>(h->n);
+    } else {
+      h->p64.reset(new Precond<double>());
+      upload_precond<double>(h.get(), *h->p64, hb, false);
+    }
+    h->m = p.restart;
+    h->nblk = dev::mdot_blocks(h->n);
+    h->V = h->ar.zeros<double>((int64_t)(h->m + 1) * h->n);
+    h->Z = h->ar.zeros<double>((int64_t)h->m * h->n);
+    h->rd = h->ar.zeros<double>(h->n);
+    h->xd = h->ar.zeros<double>(h->n);
+    h->bd = h->ar.zeros<double>(h->n);
+    h->partial = h->ar.zeros<double>((int64_t)64 * h->nblk);
+    h->hdev = h->ar.zeros<double>(256);
+    h->ydev = h->ar.zeros<double>(64);
+    MFS_CUDA(cudaMallocHost(&h->hpin, 256 * sizeof(double)));
+    if (p.profile) h->prof.reset(new EventProf());
+    MFS_CUDA(cudaDeviceSynchronize());
+  } catch (const SetupError &e) {
+    return fail(e.code, e.what());
+  } catch (const CudaError &e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(MFS_ERR_OOM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(MFS_ERR_INVALID, e.what());
+  }
+  h->setup_ms = now_ms() - t0;
+  *out = h.release();
+  return MFS_OK;
+}
+
+int64_t mfs_ndofs(const mfs_handle *h) { return h ? h->n : 0; }
+
+int mfs_num_levels(const mfs_handle *h, int group) {
+  if (!h) return 0;
+  if (group == 0) return h->hg0.nlevels();
+  if (group == 1) return h->hg1.nlevels();
+  return 0;
+}
+
+int mfs_solve(mfs_handle *h, const double *rhs, double *x, double tol, mfs_info *info) {
+  if (!h || !rhs || !x || !(tol > 0.0)) return fail(MFS_ERR_INVALID, "bad solve arguments");
+  if (h->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
+  mfs_info local{};
+  if (!info) info = &local;
+  std::memset(info, 0, sizeof(*info));
+  const double t0 = now_ms();
+  int rc = MFS_OK;
+  try {
+    const bool drhs = is_device_ptr(rhs), dx = is_device_ptr(x);
+    const double *b = rhs;
+    double *xx = x;
+    if (!drhs) {
+      MFS_CUDA(cudaMemcpyAsync(h->bd, rhs, h->n * sizeof(double), cudaMemcpyHostToDevice, h->s));
+      b = h->bd;
+    }
+    if (!dx) {
+      MFS_CUDA(cudaMemcpyAsync(h->xd, x, h->n * sizeof(double), cudaMemcpyHostToDevice, h->s));
+      xx = h->xd;
+    }
+    if (h->prof) dev::set_launch_hook(h->prof.get());
+    try {
+      rc = fgmres(h, b, xx, tol, info);
+    } catch (...) {
+      dev::set_launch_hook(nullptr);
+      throw;
+    }
+    dev::set_launch_hook(nullptr);
+    if (h->prof) h->prof->collect();
+    if (!dx) MFS_CUDA(cudaMemcpyAsync(x, h->xd, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    MFS_CUDA(cudaStreamSynchronize(h->s));
+    MFS_CUDA(cudaGetLastError());
+  } catch (const CudaError &e) {
+    return fail(e.code, e.what());
+  }
+  info->solve_ms = now_ms() - t0;
+  info->setup_ms = h->setup_ms;
+  info->levels[0] = h->hg0.nlevels();
+  info->levels[1] = h->hg1.nlevels();
+  if (rc == MFS_ERR_NOT_CONVERGED) g_last_error = "GMRES reached max_iters";
+  return rc;
+}
+
+static int with_io(mfs_handle *h, const double *in, double *out, void (*fn)(mfs_handle *, const double *, double *)) {
+  if (h->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
+  try {
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    const double *a = in;
+    double *b = out;
+    if (!din) {
+      MFS_CUDA(cudaMemcpyAsync(h->bd, in, h->n * sizeof(double), cudaMemcpyHostToDevice, h->s));
+      a = h->bd;
+    }
+    if (!dout) b = h->xd;
+    fn(h, a, b);
+    if (!dout) MFS_CUDA(cudaMemcpyAsync(out, h->xd, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->s));
+    MFS_CUDA(cudaStreamSynchronize(h->s));
+    MFS_CUDA(cudaGetLastError());
+  } catch (const CudaError &e) {
+    return fail(e.code, e.what());
+  }
+  return MFS_OK;
+}
+
+int mfs_apply(mfs_handle *h, const double *v, double *z) {
+  if (!h || !v || !z || v == z) return fail(MFS_ERR_INVALID, "bad apply arguments");
+  return with_io(h, v, z, precond_apply);
+}
+
+int mfs_matvec(mfs_handle *h, const double *x, double *y) {
+  if (!h || !x || !y || x == y) return fail(MFS_ERR_INVALID, "bad matvec arguments");
+  return with_io(h, x, y, matvec);
+}
+
+static const HBsr *export_matrix(const mfs_handle *h, int what, int group, int level, int i, int j) {
+  const HGroup &g = group == 0 ? h->hg0 : h->hg1;
+  if (group < 0 || group > 1 || level < 0 || level >= g.nlevels() || i < 0 || i >= g.nf) return nullptr;
+  if (what == 0) {
+    if (j < 0 || j >= g.nf) return nullptr;
+    if (i == j) return &g.lv[level][i].A;
+    if (level < (int)g.off.size()) {
+      auto it = g.off[level].find({i, j});
+      if (it != g.off[level].end()) return &it->second;
+    }
+    if (group == 1 && level == 0) {
+      auto it = h->schur_off.find({i, j});
+      if (it != h->schur_off.end()) return &it->second;
+    }
+    return nullptr;
+  }
+  if (level >= g.nlevels() - 1) return nullptr;
+  if (what == 1) return &g.lv[level][i].P;
+  if (what == 2) return &g.lv[level][i].R;
+  return nullptr;
+}
+
+int mfs_export_csr(const mfs_handle *h, int what, int group, int level, int i, int j, int64_t *nrows,
+                   int64_t *ncols, int64_t *nnz, int32_t *rowptr, int32_t *colind, double *vals) {
+  if (!h || !nrows || !ncols || !nnz) return fail(MFS_ERR_INVALID, "bad export arguments");
+  const HBsr *A = export_matrix(h, what, group, level, i, j);
+  if (!A) return fail(MFS_ERR_INVALID, "no such matrix");
+  const int64_t nr = A->nrows();
+  *nrows = nr;
+  *ncols = A->ncols();
+  *nnz = A->nnzb() * A->br * A->bc;
+  if (!rowptr || !colind || !vals) return MFS_OK;
+  const int bs = A->br * A->bc;
+  int64_t k = 0;
+  rowptr[0] = 0;
+  for (int64_t I = 0; I < A->nbr; ++I)
+    for (int r = 0; r < A->br; ++r) {
+      for (int64_t a = A->rp[I]; a < A->rp[I + 1]; ++a)
+        for (int c = 0; c < A->bc; ++c) {
+          colind[k] = (int32_t)(A->ci[a] * A->bc + c);
+          vals[k] = A->v[a * bs + r * A->bc + c];
+          ++k;
+        }
+      rowptr[I * A->br + r + 1] = (int32_t)k;
+    }
+  return MFS_OK;
+}
+
+int mfs_export_array(const mfs_handle *h, int what, int group, int level, int i, void *buf, int64_t cap,
+                     int64_t *count) {
+  if (!h || !count) return fail(MFS_ERR_INVALID, "bad export arguments");
+  const HGroup &g = group == 0 ? h->hg0 : h->hg1;
+  if (group < 0 || group > 1 || level < 0 || level >= g.nlevels() || i < 0 || i >= g.nf)
+    return fail(MFS_ERR_INVALID, "no such level/field");
+  const HLevelField &f = g.lv[level][i];
+  if (what == 0) {
+    *count = (int64_t)f.agg.size();
+    if (buf && cap >= *count) std::memcpy(buf, f.agg.data(), f.agg.size() * sizeof(int32_t));
+  } else if (what == 1) {
+    *count = 1;
+    if (buf && cap >= 1) *(double *)buf = f.lam;
+  } else if (what == 2) {
+    if (group != 0 || i >= (int)h->dtilde.size()) return fail(MFS_ERR_INVALID, "no SIMPLE diagonal");
+    *count = (int64_t)h->dtilde[i].size();
+    if (buf && cap >= *count) std::memcpy(buf, h->dtilde[i].data(), h->dtilde[i].size() * sizeof(double));
+  } else {
+    return fail(MFS_ERR_INVALID, "bad export kind");
+  }
+  return MFS_OK;
+}
+
+int mfs_kernel_stats(mfs_handle *h, double *out, int cap, int reset) {
+  if (!h || !out) return fail(MFS_ERR_INVALID, "bad stats arguments");
+  if (!h->prof) return fail(MFS_ERR_INVALID, "handle was built without profile");
+  int k = 0;
+  for (int c = 0; c < dev::K_NCLASS && 3 * c + 2 < cap; ++c, ++k) {
+    out[3 * c] = h->prof->launches[c];
+    out[3 * c + 1] = h->prof->ms[c];
+    out[3 * c + 2] = h->prof->bytes[c];
+  }
+  if (reset) h->prof->reset();
+  return k;
+}
+
+void mfs_free(mfs_handle *h) {
+  if (!h) return;
+  if (!h->host_only) {
+    if (h->s) cudaStreamSynchronize(h->s);
+    else cudaDeviceSynchronize();
+  }
+  delete h;
+}
+
+const char *mfs_strerror(int code) {
+  switch (code) {
+    case MFS_OK: return "ok";
+    case MFS_ERR_INVALID: return "invalid argument";
+    case MFS_ERR_CUDA: return "CUDA error";
+    case MFS_ERR_OOM: return "out of device memory";
+    case MFS_ERR_SINGULAR: return "singular matrix in setup";
+    case MFS_ERR_NOT_CONVERGED: return "GMRES did not converge within max_iters";
+    case MFS_ERR_BREAKDOWN: return "non-finite value in GMRES";
+    case MFS_ERR_SETUP: return "aggregation failed";
+    default: return "unknown error";
+  }
+}
+
+const char *mfs_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

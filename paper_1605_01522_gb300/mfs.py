@@ -1,0 +1,278 @@
+"""ctypes binding of libmfs (include/mfs.h): argument marshalling only.
+
+Every computation happens inside libmfs.so.  Vectors may be numpy arrays
+(host memory; the library copies them) or CUDA torch tensors (device
+pointers passed straight through).  Loading fails loudly when the library
+has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MAX_FIELDS = 8
+OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_SINGULAR, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6, -7
+BGS_AMG, SIMPLE, AMG_BGS = 0, 1, 2
+BWD, FWD, SYM = 0, 1, 2
+NS_CONST, NS_RBM = 0, 1
+FP64, FP32P = 0, 1
+ABSROWSUM, DIAG = 0, 1
+CHEBYSHEV, JACOBI = 0, 1
+
+PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS}
+ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
+
+# every symbol include/mfs.h declares
+EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_ndofs",
+           "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_free",
+           "mfs_strerror", "mfs_last_error"]
+KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
+
+
+class Block(C.Structure):
+    _fields_ = [("i", C.c_int), ("j", C.c_int), ("br", C.c_int), ("bc", C.c_int),
+                ("nbrows", C.c_int64), ("nbcols", C.c_int64), ("nnzb", C.c_int64),
+                ("rowptr", C.POINTER(C.c_int32)), ("colind", C.POINTER(C.c_int32)),
+                ("vals", C.POINTER(C.c_double))]
+
+
+class FieldDesc(C.Structure):
+    _fields_ = [("nnodes", C.c_int64), ("dofs_per_node", C.c_int), ("dim", C.c_int),
+                ("coords", C.POINTER(C.c_double)), ("nullspace", C.c_int),
+                ("strength_theta", C.c_double)]
+
+
+class Params(C.Structure):
+    _fields_ = [("precond", C.c_int), ("bgs_order", C.c_int), ("bgs_sweeps", C.c_int),
+                ("simple_group", C.c_int * MAX_FIELDS), ("simple_approx", C.c_int),
+                ("max_levels", C.c_int), ("coarse_max", C.c_int64), ("smoother", C.c_int),
+                ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double), ("cheb_boost", C.c_double),
+                ("jacobi_omega", C.c_double), ("jacobi_sweeps", C.c_int), ("restart", C.c_int),
+                ("max_iters", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
+                ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
+                ("profile", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("iters", C.c_int), ("restarts", C.c_int), ("converged", C.c_int),
+                ("true_relres", C.c_double), ("est_relres", C.c_double), ("solve_ms", C.c_double),
+                ("setup_ms", C.c_double), ("levels", C.c_int * 2)]
+
+    def as_dict(self):
+        return {k: (list(getattr(self, k)) if k == "levels" else getattr(self, k)) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libmfs.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmfs.so not built ({path}); run paper_1605_01522_gb300/build.py")
+    lib = C.CDLL(path)
+    H = C.c_void_p
+    lib.mfs_default_params.argtypes = [C.POINTER(Params)]
+    lib.mfs_default_params.restype = None
+    lib.mfs_setup.argtypes = [C.POINTER(Block), C.c_int, C.POINTER(FieldDesc), C.c_int, C.POINTER(Params), C.POINTER(H)]
+    lib.mfs_setup.restype = C.c_int
+    lib.mfs_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(Info)]
+    lib.mfs_solve.restype = C.c_int
+    lib.mfs_apply.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.mfs_apply.restype = C.c_int
+    lib.mfs_matvec.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.mfs_matvec.restype = C.c_int
+    lib.mfs_ndofs.argtypes = [H]
+    lib.mfs_ndofs.restype = C.c_int64
+    lib.mfs_export_csr.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                   C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.mfs_export_csr.restype = C.c_int
+    lib.mfs_export_array.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int64,
+                                     C.POINTER(C.c_int64)]
+    lib.mfs_export_array.restype = C.c_int
+    lib.mfs_num_levels.argtypes = [H, C.c_int]
+    lib.mfs_num_levels.restype = C.c_int
+    lib.mfs_kernel_stats.argtypes = [H, C.POINTER(C.c_double), C.c_int, C.c_int]
+    lib.mfs_kernel_stats.restype = C.c_int
+    lib.mfs_free.argtypes = [H]
+    lib.mfs_free.restype = None
+    lib.mfs_strerror.argtypes = [C.c_int]
+    lib.mfs_strerror.restype = C.c_char_p
+    lib.mfs_last_error.argtypes = []
+    lib.mfs_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class MfsError(RuntimeError):
+    def __init__(self, code, where):
+        lib = load(False)
+        super().__init__(f"{where}: {lib.mfs_strerror(code).decode()} ({code}): {lib.mfs_last_error().decode()}")
+        self.code = code
+
+
+def default_params(**kw) -> Params:
+    lib = load()
+    p = Params()
+    lib.mfs_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k == "precond" and isinstance(v, str):
+            v = PRECONDS[v]
+        elif k == "bgs_order" and isinstance(v, str):
+            v = ORDERS[v]
+        elif k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "fp32p": FP32P}[v]
+        elif k == "simple_approx" and isinstance(v, str):
+            v = {"absrowsum": ABSROWSUM, "diag": DIAG}[v]
+        elif k == "smoother" and isinstance(v, str):
+            v = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI}[v]
+        if k == "simple_group":
+            arr = (C.c_int * MAX_FIELDS)(*([0] * MAX_FIELDS))
+            for i, g in enumerate(v):
+                arr[i] = g
+            v = arr
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """Device pointer of a CUDA tensor or host pointer of a numpy array."""
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__str__() != "torch.float64" or not a.is_contiguous():
+            raise TypeError("vectors must be contiguous float64")
+        return C.c_void_p(a.data_ptr())
+    if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous):
+        raise TypeError("vectors must be contiguous float64")
+    return C.c_void_p(a.ctypes.data)
+
+
+class Solver:
+    """Owns one mfs_handle built from an inputs.BlockSystem."""
+
+    def __init__(self, system, params: Params | None = None, **kw):
+        lib = load()
+        self.lib = lib
+        prm = params if params is not None else default_params(**kw)
+        keep = []
+        blocks = (Block * len(system.blocks))()
+        for k, ((i, j), b) in enumerate(sorted(system.blocks.items())):
+            rp = np.ascontiguousarray(b.rowptr, np.int32)
+            ci = np.ascontiguousarray(b.colind, np.int32)
+            vv = np.ascontiguousarray(b.vals, np.float64)
+            keep += [rp, ci, vv]
+            blocks[k] = Block(i, j, b.br, b.bc, b.nbrows, b.nbcols, b.nnzb,
+                              rp.ctypes.data_as(C.POINTER(C.c_int32)), ci.ctypes.data_as(C.POINTER(C.c_int32)),
+                              vv.ctypes.data_as(C.POINTER(C.c_double)))
+        fields = (FieldDesc * system.nfields)()
+        for i, f in enumerate(system.fields):
+            co = np.ascontiguousarray(f.coords, np.float64)
+            keep.append(co)
+            fields[i] = FieldDesc(f.nnodes, f.b, f.dim, co.ctypes.data_as(C.POINTER(C.c_double)),
+                                  NS_RBM if f.nullspace == "rbm" else NS_CONST, f.theta)
+        h = C.c_void_p()
+        rc = lib.mfs_setup(blocks, len(system.blocks), fields, system.nfields, C.byref(prm), C.byref(h))
+        if rc != OK:
+            raise MfsError(rc, "mfs_setup")
+        self.h = h
+        self.params = prm
+        self.n = lib.mfs_ndofs(h)
+        self.nfields = system.nfields
+
+    def solve(self, rhs, x=None, tol=1e-8, check=True):
+        """Solve A x = rhs; x (host or device float64) is overwritten; returns (x, info dict, rc)."""
+        if x is None:
+            x = np.zeros(self.n) if isinstance(rhs, np.ndarray) else rhs.new_zeros(self.n)
+        info = Info()
+        rc = self.lib.mfs_solve(self.h, _ptr(rhs), _ptr(x), tol, C.byref(info))
+        if check and rc not in (OK, ERR_NOT_CONVERGED):
+            raise MfsError(rc, "mfs_solve")
+        return x, info.as_dict(), rc
+
+    def apply(self, v, z=None):
+        if z is None:
+            z = np.zeros(self.n) if isinstance(v, np.ndarray) else v.new_zeros(self.n)
+        rc = self.lib.mfs_apply(self.h, _ptr(v), _ptr(z))
+        if rc != OK:
+            raise MfsError(rc, "mfs_apply")
+        return z
+
+    def matvec(self, x, y=None):
+        if y is None:
+            y = np.zeros(self.n) if isinstance(x, np.ndarray) else x.new_zeros(self.n)
+        rc = self.lib.mfs_matvec(self.h, _ptr(x), _ptr(y))
+        if rc != OK:
+            raise MfsError(rc, "mfs_matvec")
+        return y
+
+    def num_levels(self, group=0):
+        return self.lib.mfs_num_levels(self.h, group)
+
+    def export_csr(self, what, group, level, i, j=0):
+        """what: 'A', 'P' or 'R'; returns a scipy CSR matrix."""
+        import scipy.sparse as sp
+        w = {"A": 0, "P": 1, "R": 2}[what]
+        nr, nc, nnz = C.c_int64(), C.c_int64(), C.c_int64()
+        rc = self.lib.mfs_export_csr(self.h, w, group, level, i, j, C.byref(nr), C.byref(nc), C.byref(nnz),
+                                     None, None, None)
+        if rc != OK:
+            raise MfsError(rc, "mfs_export_csr")
+        rp = np.zeros(nr.value + 1, np.int32)
+        ci = np.zeros(nnz.value, np.int32)
+        vv = np.zeros(nnz.value, np.float64)
+        rc = self.lib.mfs_export_csr(self.h, w, group, level, i, j, C.byref(nr), C.byref(nc), C.byref(nnz),
+                                     rp.ctypes.data, ci.ctypes.data, vv.ctypes.data)
+        if rc != OK:
+            raise MfsError(rc, "mfs_export_csr")
+        return sp.csr_matrix((vv, ci, rp), shape=(nr.value, nc.value))
+
+    def export_array(self, what, group, level, i):
+        """what: 'agg' (int32 per node), 'lambda' (float), 'dtilde' (float64)."""
+        w = {"agg": 0, "lambda": 1, "dtilde": 2}[what]
+        cnt = C.c_int64()
+        rc = self.lib.mfs_export_array(self.h, w, group, level, i, None, 0, C.byref(cnt))
+        if rc != OK:
+            raise MfsError(rc, "mfs_export_array")
+        buf = np.zeros(cnt.value, np.int32 if w == 0 else np.float64)
+        rc = self.lib.mfs_export_array(self.h, w, group, level, i, buf.ctypes.data, cnt.value, C.byref(cnt))
+        if rc != OK:
+            raise MfsError(rc, "mfs_export_array")
+        return float(buf[0]) if w == 1 else buf
+
+    def kernel_stats(self, reset=True):
+        """{class: (launches, ms, algorithmic bytes)} of the profiled solves."""
+        out = (C.c_double * 15)()
+        k = self.lib.mfs_kernel_stats(self.h, out, 15, 1 if reset else 0)
+        if k < 0:
+            raise MfsError(k, "mfs_kernel_stats")
+        return {KERNEL_CLASSES[c]: (int(out[3 * c]), out[3 * c + 1], out[3 * c + 2]) for c in range(k)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mfs_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,79 @@
+"""Full-size workload (3-field 64^3 coupled box, 1,373,125 dofs) on the GPU,
+in the configuration bench.py times.  Needs a GB300.
+
+* FP64 solves: iterations within +-1 of the oracle's stored counts
+  (tests/golden/oracle_counts.json, written by make_oracle_counts.py from the
+  oracle alone) and a true residual <= 1e-8 recomputed on the host by scipy;
+* FP32-preconditioner solves: true residual <= 1e-8 and at most 10 % (+1)
+  more iterations than the oracle;
+* coupled matvec on sampled rows, each recomputed on the host.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import precond
+from paper_1605_01522_gb300 import inputs, mfs
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+KW = dict(max_levels=5, coarse_max=1000)
+_SYS = {}
+
+
+def _system():
+    if "s" not in _SYS:
+        s = inputs.coupled_box_3d(ne=64, nfields=3, seed=1)
+        _SYS["s"] = s
+        _SYS["D"] = precond.assemble(s.scipy_blocks(), 3)
+    return _SYS["s"], _SYS["D"]
+
+
+def _counts():
+    with open(os.path.join(HERE, "golden", "oracle_counts.json")) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple"])
+def test_fullsize_fp64_matches_oracle_counts(pc):
+    s, D = _system()
+    ref = _counts()[f"coupled_box_3d_ne64_f3/{pc}"]
+    with mfs.Solver(s, precond=pc, **KW) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK
+    true = np.linalg.norm(s.rhs - D @ x) / np.linalg.norm(s.rhs)
+    assert true <= 1e-8
+    assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs"])
+def test_fullsize_fp32_preconditioner(pc):
+    s, D = _system()
+    ref = _counts()[f"coupled_box_3d_ne64_f3/{pc}"]
+    with mfs.Solver(s, precond=pc, precision="fp32p", **KW) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK
+    true = np.linalg.norm(s.rhs - D @ x) / np.linalg.norm(s.rhs)
+    assert true <= 1e-8
+    assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
+
+
+def test_fullsize_matvec_sampled_rows():
+    s, D = _system()
+    rng = np.random.default_rng(9)
+    xv = rng.standard_normal(s.ndofs)
+    with mfs.Solver(s, **KW) as lib:
+        y = lib.matvec(torch.from_numpy(xv).cuda()).cpu().numpy()
+    rows = rng.choice(s.ndofs, 2000, replace=False)
+    rows = np.concatenate([rows, [0, s.ndofs - 1, s.offsets[1], s.offsets[2] - 1]])
+    for r in rows:
+        lo, hi = D.indptr[r], D.indptr[r + 1]
+        ref = float(np.dot(D.data[lo:hi], xv[D.indices[lo:hi]]))
+        assert abs(y[r] - ref) <= 1e-12 * (np.abs(D.data[lo:hi]).sum() * np.abs(xv).max())

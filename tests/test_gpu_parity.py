@@ -1,0 +1,145 @@
+"""CUDA path (through the C ABI) against the FP64 oracle.  Needs a GB300.
+
+* coupled matvec: element-wise against scipy on the same blocks;
+* one preconditioner application (BGS(AMG), SIMPLE, AMG(BGS)), FP64: within
+  1e-12 relative (max-norm) of the oracle applied to the library's own
+  exported hierarchy - the float64 kernels and the oracle differ only in
+  summation order;
+* FGMRES solves: true residual <= 1e-8 recomputed on the host, iterations
+  within +-1 of the oracle's FGMRES (FP64) and within +10% (+1) for the FP32
+  preconditioner;
+* edge cases: zero right-hand side, nonzero initial guess, host and device
+  vectors, one field, one level, ragged slice tails (node counts that are
+  not multiples of 32).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import amg, krylov, precond
+from paper_1605_01522_gb300 import inputs, mfs
+from tests.oracle_from_lib import oracle_preconditioner
+
+pytestmark = pytest.mark.gpu
+
+APPLY_TOL = 1e-12
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def _small(name):
+    if name == "2d":
+        return inputs.thermo_elastic_2d(ne=32), dict(max_levels=3, coarse_max=0)
+    if name == "3d":
+        return inputs.coupled_box_3d(ne=10, nfields=3), dict(max_levels=4, coarse_max=150)
+    if name == "3d2":
+        return inputs.coupled_box_3d(ne=13, nfields=2), dict(max_levels=3, coarse_max=100)
+    raise KeyError(name)
+
+
+def _oracle_solve(s, kw, pc, extra):
+    A = s.scipy_blocks()
+    D = precond.assemble(A, s.nfields)
+    prm = precond.Params(pc, **kw, **extra)
+    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], prm)
+    return krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=600), D
+
+
+@pytest.mark.parametrize("name", ["2d", "3d", "3d2"])
+def test_matvec_matches_scipy(name):
+    s, kw = _small(name)
+    with mfs.Solver(s, **kw) as lib:
+        D = precond.assemble(s.scipy_blocks(), s.nfields)
+        x = np.random.default_rng(1).standard_normal(s.ndofs)
+        y = lib.matvec(_cuda(x)).cpu().numpy()
+        ref = D @ x
+        assert np.abs(y - ref).max() <= 1e-13 * np.abs(ref).max()
+        # host-pointer path gives the same bits
+        assert np.array_equal(lib.matvec(x), y)
+
+
+CASES = [("2d", "bgs_amg", {}), ("2d", "amg_bgs", {}), ("2d", "simple", {}),
+         ("3d", "bgs_amg", {}), ("3d", "amg_bgs", {}), ("3d", "simple", dict(simple_group=[0, 0, 1])),
+         ("3d", "simple", dict(simple_group=[0, 1, 1])), ("3d", "bgs_amg", dict(bgs_order="fwd")),
+         ("3d", "bgs_amg", dict(bgs_order="sym", bgs_sweeps=2)), ("3d2", "amg_bgs", dict(bgs_order="sym")),
+         ("3d2", "simple", dict(simple_approx="diag")), ("3d2", "bgs_amg", dict(smoother="jacobi", jacobi_sweeps=2)),
+         ("3d2", "bgs_amg", dict(cheb_degree=3))]
+
+
+@pytest.mark.parametrize("name,pc,extra", CASES)
+def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
+    s, kw = _small(name)
+    with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
+        Mo = oracle_preconditioner(lib, s)
+        for seed in (2, 3):
+            v = np.random.default_rng(seed).standard_normal(s.ndofs)
+            z = lib.apply(_cuda(v)).cpu().numpy()
+            zr = Mo(v)
+            err = np.abs(z - zr).max() / np.abs(zr).max()
+            assert err <= APPLY_TOL, err
+
+
+@pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8])
+def test_solve_fp64_iterations_match_oracle(name, pc, extra):
+    s, kw = _small(name)
+    okw = {k: v for k, v in extra.items() if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps")}
+    ro, D = _oracle_solve(s, kw, pc, okw)
+    with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
+        x, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK and info["converged"] == 1
+    true = np.linalg.norm(s.rhs - D @ x) / np.linalg.norm(s.rhs)
+    assert true <= 1e-8
+    assert abs(true - info["true_relres"]) <= 1e-3 * true + 1e-15
+    assert abs(info["iters"] - ro.iters) <= 1, (info["iters"], ro.iters)
+    assert np.linalg.norm(x - ro.x) <= 1e-6 * np.linalg.norm(ro.x)
+
+
+@pytest.mark.parametrize("name,pc", [("2d", "bgs_amg"), ("3d", "bgs_amg"), ("3d", "amg_bgs"), ("3d", "simple")])
+def test_solve_fp32_preconditioner(name, pc):
+    s, kw = _small(name)
+    ro, D = _oracle_solve(s, kw, pc, {})
+    with mfs.Solver(s, precond=pc, precision="fp32p", **kw) as lib:
+        x, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
+        x = x.cpu().numpy()
+    true = np.linalg.norm(s.rhs - D @ x) / np.linalg.norm(s.rhs)
+    assert rc == mfs.OK and true <= 1e-8
+    assert info["iters"] <= int(np.ceil(1.10 * ro.iters)) + 1, (info["iters"], ro.iters)
+
+
+def test_solve_edge_cases():
+    s, kw = _small("3d2")
+    D = precond.assemble(s.scipy_blocks(), s.nfields)
+    with mfs.Solver(s, **kw) as lib:
+        # zero right-hand side: zero iterations, x = 0
+        x, info, rc = lib.solve(np.zeros(s.ndofs), tol=1e-8)
+        assert rc == mfs.OK and info["iters"] == 0 and not x.any()
+        # host vectors (copies inside the library) and a nonzero initial guess
+        x0 = np.random.default_rng(5).standard_normal(s.ndofs)
+        xh = x0.copy()
+        _, info, rc = lib.solve(s.rhs, xh, tol=1e-8)
+        assert rc == mfs.OK
+        assert np.linalg.norm(s.rhs - D @ xh) <= 1e-8 * np.linalg.norm(s.rhs - D @ x0)
+        # too few iterations: NOT_CONVERGED with the last iterate returned
+        lib2 = mfs.Solver(s, max_iters=2, **kw)
+        x2, info2, rc2 = lib2.solve(s.rhs, tol=1e-8)
+        assert rc2 == mfs.ERR_NOT_CONVERGED and info2["iters"] == 2 and info2["true_relres"] < 1.0
+        lib2.close()
+
+
+def test_single_field_and_single_level():
+    s, _ = _small("3d2")
+    one = inputs.BlockSystem([s.fields[1]], {(0, 0): s.blocks[(1, 1)]}, s.rhs[s.offsets[1]:])
+    A = one.scipy_blocks()[(0, 0)]
+    for kw in (dict(max_levels=1), dict(max_levels=3, coarse_max=50)):
+        for pc in ("bgs_amg", "amg_bgs"):
+            with mfs.Solver(one, precond=pc, **kw) as lib:
+                x, info, rc = lib.solve(_cuda(one.rhs), tol=1e-8)
+                x = x.cpu().numpy()
+                assert rc == mfs.OK
+                assert np.linalg.norm(one.rhs - A @ x) <= 1e-8 * np.linalg.norm(one.rhs)
+                if kw["max_levels"] == 1:
+                    assert info["iters"] == 1

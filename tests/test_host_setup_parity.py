@@ -1,0 +1,93 @@
+"""Host setup of libmfs (no GPU needed: setup_only handles) against the oracle.
+
+The library's C++ smoothed-aggregation setup and the oracle's numpy/scipy one
+are independent implementations of the same steps; aggregates must agree
+exactly (integer work) and prolongators, Galerkin blocks, lambda_max and the
+SIMPLE objects to float64 rounding.
+"""
+import numpy as np
+import pytest
+
+from oracle import amg, precond
+from paper_1605_01522_gb300 import inputs, mfs
+
+TOL = 1e-12
+
+
+def _rel(a, b):
+    a = a.toarray() if hasattr(a, "toarray") else np.asarray(a)
+    b = b.toarray() if hasattr(b, "toarray") else np.asarray(b)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _systems():
+    return {
+        "2d": (inputs.thermo_elastic_2d(ne=16), dict(max_levels=3, coarse_max=0)),
+        "3d": (inputs.coupled_box_3d(ne=8, nfields=3), dict(max_levels=4, coarse_max=200)),
+    }
+
+
+SYS = None
+
+
+def _get(name):
+    global SYS
+    if SYS is None:
+        SYS = _systems()
+    return SYS[name]
+
+
+@pytest.mark.parametrize("name", ["2d", "3d"])
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs"])
+def test_hierarchy_matches_oracle(name, pc):
+    s, kw = _get(name)
+    lib = mfs.Solver(s, precond=pc, setup_only=1, seed=7, **kw)
+    A = s.scipy_blocks()
+    specs = [amg.FieldSpec.of(f) for f in s.fields]
+    M = precond.Preconditioner(A, specs, precond.Params(pc, seed=7, **kw))
+    lv = M.groups[0].levels
+    assert lib.num_levels(0) == len(lv)
+    for l in range(len(lv)):
+        for i in range(s.nfields):
+            assert _rel(lib.export_csr("A", 0, l, i, i), lv[l][i].A) < TOL
+            if l < len(lv) - 1:
+                agg = lib.export_array("agg", 0, l, i)
+                assert np.array_equal(agg, lv[l][i].agg)
+                assert _rel(lib.export_csr("P", 0, l, i), lv[l][i].P) < TOL
+                assert _rel(lib.export_csr("R", 0, l, i), lv[l][i].R) < TOL
+                assert abs(lib.export_array("lambda", 0, l, i) - lv[l][i].lam) < 1e-13 * lv[l][i].lam
+    if pc == "amg_bgs":
+        for l in range(1, len(lv)):
+            for (i, j), Mij in M.op.A[l].items():
+                if i != j:
+                    assert _rel(lib.export_csr("A", 0, l, i, j), Mij) < TOL
+    lib.close()
+
+
+@pytest.mark.parametrize("approx", ["absrowsum", "diag"])
+def test_simple_objects_match_oracle(approx):
+    s, kw = _get("3d")
+    grp = [0, 0, 1]
+    lib = mfs.Solver(s, precond="simple", simple_group=grp, simple_approx=approx, setup_only=1, **kw)
+    A = s.scipy_blocks()
+    specs = [amg.FieldSpec.of(f) for f in s.fields]
+    M = precond.Preconditioner(A, specs, precond.Params("simple", simple_group=grp, simple_approx=approx, **kw))
+    for jj in range(2):
+        assert _rel(lib.export_array("dtilde", 0, 0, jj), M.dtilde[jj]) < 1e-14
+    assert _rel(lib.export_csr("A", 1, 0, 0, 0), M.schur_blocks[(0, 0)]) < TOL
+    lv1 = M.groups[1].levels
+    assert lib.num_levels(1) == len(lv1)
+    for l in range(len(lv1) - 1):
+        assert np.array_equal(lib.export_array("agg", 1, l, 0), lv1[l][0].agg)
+        assert _rel(lib.export_csr("P", 1, l, 0), lv1[l][0].P) < TOL
+    lib.close()
+
+
+def test_setup_rejects_bad_input():
+    s, kw = _get("2d")
+    bad = inputs.BlockSystem(s.fields, {k: v for k, v in s.blocks.items() if k != (1, 1)}, s.rhs)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(bad, setup_only=1)
+    assert e.value.code == mfs.ERR_INVALID
+    with pytest.raises(mfs.MfsError):
+        mfs.Solver(s, setup_only=1, restart=0)
