@@ -62,6 +62,76 @@ __device__ __forceinline__ void sell_row(const int32_t *__restrict__ sp, const i
   }
 }
 
+// One warp per block row of a plain BSR matrix: lanes stride over the row's
+// blocks, then a fixed xor-butterfly sums the lanes (all lanes get the sums).
+template <int BR, int BC, typename T>
+__device__ __forceinline__ void bsr_warp_row(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                             const T *__restrict__ val, const T *__restrict__ x, int64_t row,
+                                             int lane, T (&acc)[BR]) {
+  const int lo = rp[row], hi = rp[row + 1];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+  for (int k = lo + lane; k < hi; k += 32) {
+    const int64_t c = __ldg(col + k);
+    T xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = __ldg(x + c * BC + q);
+    const T *v = val + (int64_t)k * (BR * BC);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[r] += __ldg(v + r * BC + q) * xv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
+template <int BR, typename T>
+__device__ __forceinline__ T pick(const T (&acc)[BR], int r) {
+  T a = acc[0];
+#pragma unroll
+  for (int q = 1; q < BR; ++q)
+    if (q == r) a = acc[q];
+  return a;
+}
+
+template <int BR, int BC, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_spmv_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+            const T *__restrict__ val, const T *__restrict__ x, T *y, T alpha, T beta, const T *z) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nbr) return;
+  T acc[BR];
+  bsr_warp_row<BR, BC, T>(rp, col, val, x, row, lane, acc);
+  if (lane < BR) {
+    const int64_t i = row * BR + lane;
+    const T a = pick<BR, T>(acc, lane);
+    y[i] = z != nullptr ? alpha * a + beta * z[i] : alpha * a;
+  }
+}
+
+template <int BR, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_smooth_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+              const T *__restrict__ val, const T *__restrict__ dinv, const T *__restrict__ b,
+              const T *__restrict__ x, T *__restrict__ xout, T *__restrict__ d, T c1, T c2) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nbr) return;
+  T acc[BR];
+  bsr_warp_row<BR, BR, T>(rp, col, val, x, row, lane, acc);
+  if (lane < BR) {
+    const int64_t i = row * BR + lane;
+    const T res = b[i] - pick<BR, T>(acc, lane);
+    const T dd = c1 * d[i] + c2 * dinv[i] * res;
+    d[i] = dd;
+    xout[i] = x[i] + dd;
+  }
+}
+
 template <int BR, int BC, typename T>
 __global__ void __launch_bounds__(kThreads)
 k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
@@ -115,26 +185,55 @@ __global__ void k_smooth_first(int64_t n, const T *__restrict__ dinv, const T *_
   }
 }
 
+// Dense LU solve in one CTA, blocked by 32: one warp solves each 32 x 32
+// diagonal block with shuffles, then all warps update the rows below (above)
+// with that block's 32 new unknowns.  y lives in shared memory.
 template <typename T>
 __global__ void __launch_bounds__(1024)
 k_lu_solve(int n, const double *__restrict__ lu, const int32_t *__restrict__ perm,
            const T *__restrict__ b, T *__restrict__ x) {
   extern __shared__ double y[];
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < n; i += nt) y[i] = (double)b[perm[i]];
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    const double yk = y[k];
-    const double *lk = lu + (int64_t)k * n;
-    for (int i = k + 1 + tid; i < n; i += nt) y[i] -= lk[i] * yk;
+  // forward: L y = Pb, unit lower triangle
+  for (int k0 = 0; k0 < n; k0 += 32) {
+    const int nb = min(32, n - k0);
+    if (warp == 0) {
+      double yv = lane < nb ? y[k0 + lane] : 0.0;
+      for (int c = 0; c < nb; ++c) {
+        const double yc = __shfl_sync(0xffffffffu, yv, c);
+        if (lane > c && lane < nb) yv -= lu[(int64_t)(k0 + c) * n + k0 + lane] * yc;
+      }
+      if (lane < nb) y[k0 + lane] = yv;
+    }
+    __syncthreads();
+    for (int i = k0 + nb + tid; i < n; i += nt) {
+      double s = 0.0;
+      for (int c = 0; c < nb; ++c) s += lu[(int64_t)(k0 + c) * n + i] * y[k0 + c];
+      y[i] -= s;
+    }
     __syncthreads();
   }
-  for (int k = n - 1; k >= 0; --k) {
-    const double *uk = lu + (int64_t)k * n;
-    if (tid == 0) y[k] /= uk[k];
+  // backward: U x = y
+  const int last = ((n - 1) / 32) * 32;
+  for (int k0 = last; k0 >= 0; k0 -= 32) {
+    const int nb = min(32, n - k0);
+    if (warp == 0) {
+      double yv = lane < nb ? y[k0 + lane] : 0.0;
+      for (int c = nb - 1; c >= 0; --c) {
+        if (lane == c) yv /= lu[(int64_t)(k0 + c) * n + k0 + c];
+        const double yc = __shfl_sync(0xffffffffu, yv, c);
+        if (lane < c) yv -= lu[(int64_t)(k0 + c) * n + k0 + lane] * yc;
+      }
+      if (lane < nb) y[k0 + lane] = yv;
+    }
     __syncthreads();
-    const double yk = y[k];
-    for (int i = tid; i < k; i += nt) y[i] -= uk[i] * yk;
+    for (int i = tid; i < k0; i += nt) {
+      double s = 0.0;
+      for (int c = 0; c < nb; ++c) s += lu[(int64_t)(k0 + c) * n + i] * y[k0 + c];
+      y[i] -= s;
+    }
     __syncthreads();
   }
   for (int i = tid; i < n; i += nt) x[i] = (T)y[i];
@@ -185,20 +284,91 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
   return s;  // valid in thread 0
 }
 
+constexpr int kTile = kThreads;  // rows of w staged per step
+constexpr int kMaxQ = 64;        // rows of V handled per launch (8 per warp)
+
+// partial[q*nblk + b] = sum over chunk b of V_q[i] * ws[i] for the staged tile;
+// warp p owns rows q = p, p+8, ... and reads them coalesced.
+__device__ __forceinline__ void tile_dots(const double *__restrict__ V, int64_t ldv, int k, int64_t t0, int cnt,
+                                          const double *ws, double (&acc)[kMaxQ / 8]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < kMaxQ / 8; ++m) {
+    const int q = warp + 8 * m;
+    if (q < k) {
+      const double *vq = V + (int64_t)q * ldv + t0;
+      double s = 0.0;
+      for (int t = lane; t < cnt; t += 32) s += vq[t] * ws[t];
+      acc[m] += s;
+    }
+  }
+}
+
+__device__ __forceinline__ void store_dots(int k, int nblk, double (&acc)[kMaxQ / 8], double *__restrict__ partial) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int m = 0; m < kMaxQ / 8; ++m) {
+    const int q = warp + 8 * m;
+    if (q < k) {
+      double v = acc[m];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) partial[(int64_t)q * nblk + blockIdx.x] = v;
+    }
+  }
+}
+
+// h_q = V_q . w for q < k (w may be one of the rows of V)
 __global__ void __launch_bounds__(kThreads)
 k_mdot(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ w, int64_t n,
        double *__restrict__ partial, int nblk) {
-  __shared__ double sh[32];
+  __shared__ double ws[kTile];
   const int64_t chunk = (n + nblk - 1) / nblk;
   const int64_t lo = (int64_t)blockIdx.x * chunk;
   const int64_t hi = min(n, lo + chunk);
-  for (int q = 0; q < k; ++q) {
-    const double *vq = V + (int64_t)q * ldv;
-    double acc = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) acc += vq[i] * w[i];
-    const double s = block_sum(acc, sh);
-    if (threadIdx.x == 0) partial[(int64_t)q * nblk + blockIdx.x] = s;
+  double acc[kMaxQ / 8];
+#pragma unroll
+  for (int m = 0; m < kMaxQ / 8; ++m) acc[m] = 0.0;
+  for (int64_t t0 = lo; t0 < hi; t0 += kTile) {
+    const int cnt = (int)min((int64_t)kTile, hi - t0);
+    ws[threadIdx.x] = threadIdx.x < cnt ? w[t0 + threadIdx.x] : 0.0;
+    __syncthreads();
+    tile_dots(V, ldv, k, t0, cnt, ws, acc);
+    __syncthreads();
   }
+  store_dots(k, nblk, acc, partial);
+}
+
+// w <- w - sum_q V_q h_q, then partial dots V_q . w_new (CGS2 second pass)
+__global__ void __launch_bounds__(kThreads)
+k_cgs_fused(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ h, double *__restrict__ w,
+            int64_t n, double *__restrict__ partial, int nblk) {
+  __shared__ double ws[kTile];
+  __shared__ double hs[kMaxQ];
+  for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
+  __syncthreads();
+  const int64_t chunk = (n + nblk - 1) / nblk;
+  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t hi = min(n, lo + chunk);
+  double acc[kMaxQ / 8];
+#pragma unroll
+  for (int m = 0; m < kMaxQ / 8; ++m) acc[m] = 0.0;
+  for (int64_t t0 = lo; t0 < hi; t0 += kTile) {
+    const int cnt = (int)min((int64_t)kTile, hi - t0);
+    double wn = 0.0;
+    if (threadIdx.x < cnt) {
+      const int64_t i = t0 + threadIdx.x;
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s += V[(int64_t)q * ldv + i] * hs[q];
+      wn = w[i] - s;
+      w[i] = wn;
+    }
+    ws[threadIdx.x] = wn;
+    __syncthreads();
+    tile_dots(V, ldv, k, t0, cnt, ws, acc);
+    __syncthreads();
+  }
+  store_dots(k, nblk, acc, partial);
 }
 
 __global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, double *__restrict__ out) {
@@ -282,6 +452,12 @@ void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStre
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
   HookScope hs(s, K_SPMV, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + A.nrows() * (z ? 2 : 1)));
+  if (A.kind == 1) {
+    MFS_BLOCK_DISPATCH(A.br, A.bc,
+                       (k_spmv_warp<BR_, BC_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
+                           A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
+    return;
+  }
   MFS_BLOCK_DISPATCH(A.br, A.bc,
                      (k_spmv<BR_, BC_, T><<<grid_for(A.nbr), kThreads, 0, s>>>(
                          A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
@@ -302,6 +478,11 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
   HookScope hs(s, K_SMOOTH, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + 5.0 * A.nrows()));
+  if (A.kind == 1) {
+    MFS_SQUARE_DISPATCH(A.br, (k_smooth_warp<BR_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.col, v, dinv, b, x, xout, d, c1, c2)));
+    return;
+  }
   MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T><<<grid_for(A.nbr), kThreads, 0, s>>>(
                                 A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
 }
@@ -367,6 +548,12 @@ void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, doubl
 void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s) {
   HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk);
   k_reduce_partials<<<k, kThreads, 0, s>>>(partial, nblk, out);
+}
+
+void cgs_fused(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n, double *partial,
+               int nblk, cudaStream_t s) {
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2));
+  k_cgs_fused<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
 }
 
 void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,

@@ -14,6 +14,11 @@ namespace mfs {
 namespace dev {
 
 struct Sell {
+  int kind = 0;                // 0: SELL-32, one thread per block row;
+                               // 1: plain BSR, one warp per block row (long rows /
+                               //    few rows: restriction, coarse levels); then sp is
+                               //    the row pointer, col the block columns and the
+                               //    values are contiguous per block (br*bc, row-major)
   int br = 0, bc = 0;
   int64_t nbr = 0, nbc = 0;
   int64_t nslices = 0, nslots = 0;
@@ -77,6 +82,9 @@ int mdot_blocks(int64_t n);
 void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, double *partial,
           int nblk, cudaStream_t s);                                   // partial[q*nblk+b]
 void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s);
+// w -= sum_q V_q h_q and partial dots V_q . w_new in one pass (k <= 64)
+void cgs_fused(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n, double *partial,
+               int nblk, cudaStream_t s);
 // w -= sum_q V_q h_q; if partial != null also partial[b] = sum w_new^2 over block b
 void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,
                 double *partial, int nblk, cudaStream_t s);

@@ -68,6 +68,11 @@ struct Arena {
   }
 };
 
+// Layout choice: rows longer than this many blocks on average, or matrices
+// with fewer block rows than this, get one warp per row.
+constexpr double kWarpRowMinAvg = 40.0;
+constexpr int64_t kWarpRowMaxRows = 8192;
+
 static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32) {
   dev::Sell S;
   S.br = A.br;
@@ -77,6 +82,21 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   S.nnzb = A.nnzb();
   if (A.nbr == 0) return S;
   const int bs = A.br * A.bc;
+  const double avg = (double)A.nnzb() / (double)A.nbr;
+  if (avg > kWarpRowMinAvg || A.nbr < kWarpRowMaxRows) {
+    // plain BSR, one warp per block row
+    if (A.nnzb() > INT32_MAX) throw SetupError(MFS_ERR_INVALID, "matrix too large for 32-bit block offsets");
+    S.kind = 1;
+    std::vector<int32_t> rp(A.rp.begin(), A.rp.end());
+    S.sp = ar.upload(rp);
+    S.col = ar.upload(A.ci);
+    if (want64) S.v64 = ar.upload(A.v);
+    if (want32) {
+      std::vector<float> v32(A.v.begin(), A.v.end());
+      S.v32 = ar.upload(v32);
+    }
+    return S;
+  }
   S.nslices = (A.nbr + 31) / 32;
   std::vector<int32_t> sp(S.nslices + 1, 0), rl(A.nbr);
   for (int64_t s = 0; s < S.nslices; ++s) {
@@ -575,8 +595,7 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
       // CGS2: h1 = V^T w (and |w|^2), w -= V h1, h2 = V^T w, w -= V h2 (and |w|^2)
       dev::mdot(h->V, n, j + 2, w, n, h->partial, h->nblk, s);
       dev::reduce_partials(h->partial, j + 2, h->nblk, h->hdev, s);
-      dev::cgs_update(h->V, n, j + 1, h->hdev, w, n, nullptr, h->nblk, s);
-      dev::mdot(h->V, n, j + 1, w, n, h->partial, h->nblk, s);
+      dev::cgs_fused(h->V, n, j + 1, h->hdev, w, n, h->partial, h->nblk, s);
       dev::reduce_partials(h->partial, j + 1, h->nblk, h->hdev + 64, s);
       dev::cgs_update(h->V, n, j + 1, h->hdev + 64, w, n, h->partial, h->nblk, s);
       dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + 128, s);
