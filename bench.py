@@ -201,7 +201,7 @@ def run_mfs(args, rank, world):
     s = make_system()
     stream = torch.cuda.Stream(device=dev)
     prm = mfs.default_params(precond=args.precond, precision=args.precision, profile=1,
-                             cuda_stream=stream.cuda_stream, **SOLVER_KW)
+                             cuda_stream=stream.cuda_stream, no_graphs=int(args.no_graphs), **SOLVER_KW)
     t0 = time.perf_counter()
     lib = mfs.Solver(s, params=prm)
     setup_s = time.perf_counter() - t0
@@ -211,7 +211,18 @@ def run_mfs(args, rank, world):
         x = torch.zeros(n, dtype=torch.float64, device=dev)
     stream.synchronize()
     infos = []
-    for _ in range(args.warmup):
+    # warm-up 1 times every launch to find the dominant sparse kernel and the
+    # class shares; the other warm-ups and the timed region time only that
+    # kernel (one event pair per launch of it), so the timed solves run at
+    # full speed while its launch durations are measured live
+    x.zero_()
+    torch.cuda.synchronize()
+    lib.solve(b, x, tol=1e-8)
+    detail_all = lib.kernel_detail()
+    stats_all = lib.kernel_stats(reset=True)
+    dom = [r for r in detail_all if r[0].startswith(("spmv", "smooth"))][0]
+    lib.profile_filter(dom[5], dom[1])
+    for _ in range(max(1, args.warmup - 1)):
         x.zero_()
         torch.cuda.synchronize()
         _, info, rc = lib.solve(b, x, tol=1e-8)
@@ -238,30 +249,36 @@ def run_mfs(args, rank, world):
         t = torch.tensor([elapsed], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         elapsed = float(t.item())
+    detail = lib.kernel_detail()
     stats = lib.kernel_stats(reset=True)
     # true residual, recomputed through the library's FP64 matvec (device)
     r = b - lib.matvec(x)
     relres = float(torch.linalg.norm(r) / torch.linalg.norm(b))
     # end-to-end: host (pinned) vectors, copies inside the timed region
-    bh = torch.from_numpy(s.rhs.copy()).pin_memory()
-    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    e2e_times = []
-    for k in range(max(2, args.steps // 2) + 1):
-        xh.zero_()
-        t1 = time.perf_counter()
-        _, info_h, rc = lib.solve(bh.numpy(), xh.numpy(), tol=1e-8)
-        dt = time.perf_counter() - t1
-        if k > 0:
-            e2e_times.append(dt)
-    lib.kernel_stats(reset=True)
-    e2e = {"value": world / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
-           "d2h_bytes_per_step": 8 * n}
-    # roofline of the dominant kernel class (by event time)
+    e2e = None
+    if not args.no_e2e:
+        bh = torch.from_numpy(s.rhs.copy()).pin_memory()
+        xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+        e2e_times = []
+        for k in range(max(2, args.steps // 2) + 1):
+            xh.zero_()
+            t1 = time.perf_counter()
+            _, info_h, rc = lib.solve(bh.numpy(), xh.numpy(), tol=1e-8)
+            dt = time.perf_counter() - t1
+            if k > 0:
+                e2e_times.append(dt)
+        lib.kernel_stats(reset=True)
+        e2e = {"value": world / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
+               "d2h_bytes_per_step": 8 * n}
+    # roofline of the dominant kernel, timed live over the timed region
     peak, peak_kind = measured_hbm_peak()
-    cls = max(("spmv", "smooth"), key=lambda c: stats[c][1])
-    launches, ms, nbytes = stats[cls]
+    kname, krows, launches, ms, nbytes, _ = detail[0]
     achieved = nbytes / (ms / 1e3) / 1e9
-    launches_total = sum(v[0] for v in stats.values())
+    tot_ms = sum(r[3] for r in detail_all)
+    top = [{"kernel": r[0], "rows": r[1], "launches": r[2], "share": round(r[3] / tot_ms, 4),
+            "GBps": round(r[4] / (r[3] / 1e3) / 1e9, 1)} for r in detail_all[:8]]
+    stats = stats_all
+    launches_total = sum(v[0] for v in stats_all.values()) * args.steps
     value = world * args.steps / elapsed
     if rank != 0:
         return
@@ -282,10 +299,11 @@ def run_mfs(args, rank, world):
         "data": "synthetic",
         "config": workload_config(args, s, {"iters": infos[-1]["iters"], "true_relres": relres,
                                             "setup_s": round(setup_s, 2), "levels": infos[-1]["levels"],
-                                            "kernel_time_share": shares}),
-        "roofline": {"bound": "hbm", "kernel": cls, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": None,
-                     "launches": launches, "ms": ms, "algorithmic_bytes": nbytes},
+                                            "kernel_class_share": shares, "top_kernels": top}),
+        "roofline": {"bound": "hbm", "kernel": f"{kname} ({krows} block rows)", "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": None, "launches": launches, "bytes_per_launch": nbytes / launches,
+                     "avg_launch_us": ms / launches * 1e3},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches_total),
@@ -296,6 +314,7 @@ def run_mfs(args, rank, world):
 
 
 def main():
+    global NE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -304,7 +323,11 @@ def main():
     ap.add_argument("--precond", default="bgs_amg", choices=["bgs_amg", "amg_bgs", "simple"])
     ap.add_argument("--precision", default="fp32p", choices=["fp32p", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--ne", type=int, default=NE, help="mesh edge (64 = the benchmark workload)")
+    ap.add_argument("--no-graphs", action="store_true")
     args = ap.parse_args()
+    NE = args.ne
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     if args.impl == "reference":

@@ -18,6 +18,11 @@
  * fallback.  The AMG setup (aggregation, prolongators, Galerkin products,
  * coarse factorisation) runs in this library's host code and is timed apart.
  *
+ * Each GMRES iteration (preconditioner, matvec, CGS2 Arnoldi, readback of
+ * the Hessenberg column) is captured once per Krylov index into a CUDA graph
+ * and replayed; a NULL params.cuda_stream makes the library create its own
+ * stream (blocking with respect to the legacy default stream).
+ *
  * Conventions
  *   - All functions return MFS_OK (0) or a negative MFS_ERR_* code;
  *     mfs_strerror() names it.  A failed call leaves no partial handle.
@@ -109,6 +114,8 @@ typedef struct {
                                         the handle then serves the export calls alone */
   int profile;                       /* 1: time every kernel launch of mfs_solve with CUDA
                                         events, by kernel class (see mfs_kernel_stats) */
+  int no_graphs;                     /* 1: launch kernels one by one instead of replaying
+                                        one captured CUDA graph per GMRES iteration */
 } mfs_params;
 
 typedef struct {
@@ -179,6 +186,23 @@ int mfs_num_levels(const struct mfs_handle *h, int group);
  * classes written; reset != 0 zeroes the counters afterwards.  The event
  * hook is process-wide: profile one handle at a time. */
 int mfs_kernel_stats(struct mfs_handle *h, double *out, int cap, int reset);
+
+/* Per-kernel accounting behind mfs_kernel_stats: one row of 5 doubles per
+ * kernel variant and size, sorted by summed time: [cls*100000 + sig, rows,
+ * launches, ms, algorithmic bytes], where for SpMV (cls 0) and smoothing
+ * (cls 1) sig = layout*1000 + br*100 + bc*10 + (float64 ? 1 : 0) with layout
+ * 0 = SELL-32 / 1 = warp-per-row BSR, and rows = block rows; for the other
+ * classes sig is a kernel id and rows the vector length.  Returns the number
+ * of rows written (cap = length of out).  Cleared by mfs_kernel_stats with
+ * reset != 0. */
+int mfs_kernel_detail(struct mfs_handle *h, double *out, int cap);
+
+/* Record only the launches whose mfs_kernel_detail key equals `key` (and
+ * whose row count equals `rows` unless rows == 0); key 0 records every
+ * launch again.  Drops the captured iteration graphs so that they are
+ * recaptured with the new set of timing events at the next solve.  Meant to
+ * time one kernel inside a long run with little overhead. */
+int mfs_profile_filter(struct mfs_handle *h, int key, int64_t rows);
 
 /* Release every device and host resource of the handle (NULL is a no-op). */
 void mfs_free(struct mfs_handle *h);

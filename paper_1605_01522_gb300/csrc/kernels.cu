@@ -18,13 +18,20 @@ struct HookScope {
   cudaStream_t s;
   int cls;
   double bytes;
-  HookScope(cudaStream_t s_, int c, double b) : s(s_), cls(c), bytes(b) {
-    if (g_hook) g_hook->before(s);
+  int sig;
+  int64_t rows;
+  bool on = false;
+  HookScope(cudaStream_t s_, int c, double b, int sg = 0, int64_t r = 0) : s(s_), cls(c), bytes(b), sig(sg), rows(r) {
+    if (g_hook) on = g_hook->before(s, cls, sig, rows);
   }
   ~HookScope() {
-    if (g_hook) g_hook->after(s, cls, bytes);
+    if (on) g_hook->after(s, cls, bytes, sig, rows);
   }
 };
+
+template <typename T> int sparse_sig(const Sell &A) {
+  return A.kind * 1000 + A.br * 100 + A.bc * 10 + (sizeof(T) == 8 ? 1 : 0);
+}
 
 // algorithmic bytes of one pass over a block matrix: values + block-column
 // indices + row lengths, each read once
@@ -48,7 +55,9 @@ __device__ __forceinline__ void sell_row(const int32_t *__restrict__ sp, const i
   const T *vp = val + base * (BR * BC * 32) + lane;
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = T(0);
-#pragma unroll 2
+  // small blocks: more slots in flight to cover the index -> x dependency
+  constexpr int kUnroll = BR * BC <= 3 ? 4 : 2;
+#pragma unroll kUnroll
   for (int t = 0; t < len; ++t) {
     const int64_t c = __ldg(cp + (int64_t)t * 32);
     T xv[BC];
@@ -153,6 +162,42 @@ k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ 
 #pragma unroll
     for (int r = 0; r < BR; ++r) yp[r] = alpha * acc[r];
   }
+}
+
+template <int BR, int B0, int B1, int B2>
+__global__ void __launch_bounds__(kThreads)
+k_spmv_rows(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+            const int32_t *__restrict__ col, const double *__restrict__ val, const double *__restrict__ x0,
+            const double *__restrict__ x1, const double *__restrict__ x2, double *__restrict__ y) {
+  constexpr int BCT = B0 + B1 + B2;
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  const int lane = (int)(row & 31);
+  const int64_t base = sp[row >> 5];
+  const int len = rl[row];
+  const int32_t *cp = col + base * 32 + lane;
+  const double *vp = val + base * (BR * BCT * 32) + lane;
+  double acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = 0.0;
+#pragma unroll 2
+  for (int t = 0; t < len; ++t) {
+    const int64_t c = __ldg(cp + (int64_t)t * 32);
+    double xv[BCT];
+#pragma unroll
+    for (int q = 0; q < B0; ++q) xv[q] = __ldg(x0 + c * B0 + q);
+#pragma unroll
+    for (int q = 0; q < B1; ++q) xv[B0 + q] = __ldg(x1 + c * B1 + q);
+#pragma unroll
+    for (int q = 0; q < B2; ++q) xv[B0 + B1 + q] = __ldg(x2 + c * B2 + q);
+    const double *v = vp + (int64_t)t * (BR * BCT * 32);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BCT; ++q) acc[r] += __ldg(v + (r * BCT + q) * 32) * xv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r) y[row * BR + r] = acc[r];
 }
 
 template <int BR, typename T>
@@ -447,11 +492,17 @@ inline unsigned ew_grid(int64_t n) {
 
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
 
+void init() {
+  cudaFuncSetAttribute(k_lu_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_lu_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
 template <typename T>
 void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStream_t s) {
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
-  HookScope hs(s, K_SPMV, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + A.nrows() * (z ? 2 : 1)));
+  HookScope hs(s, K_SPMV, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + A.nrows() * (z ? 2 : 1)),
+               sparse_sig<T>(A), A.nbr);
   if (A.kind == 1) {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
                        (k_spmv_warp<BR_, BC_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
@@ -472,12 +523,44 @@ void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStre
     default: fprintf(stderr, "mfs: unsupported block size %d\n", BRV); \
   }
 
+#define MFS_ROWS_DISPATCH(BR, B, CALL)                                          \
+  switch (BR * 1000 + B[0] * 100 + B[1] * 10 + B[2]) {                          \
+    case 3311: { constexpr int R_ = 3, X0 = 3, X1 = 1, X2 = 1; CALL; } break;   \
+    case 1311: { constexpr int R_ = 1, X0 = 3, X1 = 1, X2 = 1; CALL; } break;   \
+    case 3310: { constexpr int R_ = 3, X0 = 3, X1 = 1, X2 = 0; CALL; } break;   \
+    case 1310: { constexpr int R_ = 1, X0 = 3, X1 = 1, X2 = 0; CALL; } break;   \
+    case 2210: { constexpr int R_ = 2, X0 = 2, X1 = 1, X2 = 0; CALL; } break;   \
+    case 1210: { constexpr int R_ = 1, X0 = 2, X1 = 1, X2 = 0; CALL; } break;   \
+    default: break;                                                             \
+  }
+
+bool rows_supported(int br, const int *b, int nb) {
+  const int code = br * 1000 + b[0] * 100 + b[1] * 10 + (nb > 2 ? b[2] : 0);
+  switch (code) {
+    case 3311: case 1311: case 3310: case 1310: case 2210: case 1210: return nb >= 2 && nb <= 3;
+    default: return false;
+  }
+}
+
+void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s) {
+  const Sell &A = R.M;
+  if (A.nbr == 0) return;
+  HookScope hs(s, K_SPMV,
+               (double)A.nnzb * (A.br * A.bc * 8.0 + 4.0) + 4.0 * A.nbr + 8.0 * (A.nbc * A.bc + A.nrows()),
+               2000 + A.br * 100 + A.bc * 10 + 1, A.nbr);
+  const double *x0 = x + R.off[0], *x1 = x + R.off[1], *x2 = R.nb > 2 ? x + R.off[2] : x;
+  const int b3[3] = {R.b[0], R.b[1], R.nb > 2 ? R.b[2] : 0};
+  MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+}
+
 template <typename T>
 void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, T *d, T c1, T c2,
                  cudaStream_t s) {
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
-  HookScope hs(s, K_SMOOTH, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + 5.0 * A.nrows()));
+  HookScope hs(s, K_SMOOTH, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + 5.0 * A.nrows()),
+               sparse_sig<T>(A), A.nbr);
   if (A.kind == 1) {
     MFS_SQUARE_DISPATCH(A.br, (k_smooth_warp<BR_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
                                   A.nbr, A.sp, A.col, v, dinv, b, x, xout, d, c1, c2)));
@@ -490,45 +573,40 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
 template <typename T>
 void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s) {
   if (n == 0) return;
-  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T));
+  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 1, n);
   k_smooth_first<T><<<ew_grid(n), kThreads, 0, s>>>(n, dinv, b, x, d, c2);
 }
 
 template <typename T>
 void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   if (lu.n == 0) return;
-  HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n);
+  HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n);
   const size_t smem = (size_t)lu.n * sizeof(double);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(k_lu_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr_set = true;
-  }
   k_lu_solve<T><<<1, 1024, smem, s>>>(lu.n, lu.lu, lu.perm, b, x);
 }
 
 template <typename T>
 void fill(T *x, int64_t n, T v, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, (double)n * sizeof(T));
+  HookScope hs(s, K_VECTOR, (double)n * sizeof(T), 2, n);
   if (n) k_fill<T><<<ew_grid(n), kThreads, 0, s>>>(x, n, v);
 }
 template <typename T>
 void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T));
+  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 3, n);
   if (n) k_axpy_diag<T><<<ew_grid(n), kThreads, 0, s>>>(x, dinv, t, n);
 }
 template <typename T>
 void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T));
+  HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T), 4, n);
   if (n) k_axpy<T><<<ew_grid(n), kThreads, 0, s>>>(y, x, a, n);
 }
 template <typename TI, typename TO>
 void convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)));
+  HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)), 5, n);
   if (n) k_convert<TI, TO><<<ew_grid(n), kThreads, 0, s>>>(in, out, n);
 }
 void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, 16.0 * n);
+  HookScope hs(s, K_VECTOR, 16.0 * n, 6, n);
   if (n) k_scale<<<ew_grid(n), kThreads, 0, s>>>(x, a, y, n);
 }
 
@@ -541,29 +619,29 @@ int mdot_blocks(int64_t n) {
 
 void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, double *partial, int nblk,
           cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 1));
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 1), 1, n);
   k_mdot<<<nblk, kThreads, 0, s>>>(V, ldv, k, w, n, partial, nblk);
 }
 
 void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk);
+  HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk, 2, k);
   k_reduce_partials<<<k, kThreads, 0, s>>>(partial, nblk, out);
 }
 
 void cgs_fused(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n, double *partial,
                int nblk, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2));
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 3, n);
   k_cgs_fused<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
 }
 
 void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,
                 double *partial, int nblk, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2));
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 4, n);
   k_cgs_update<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
 }
 
 void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2));
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 5, n);
   k_gemv_add<<<ew_grid(n), kThreads, 0, s>>>(Z, ldz, k, y, x, n);
 }
 

@@ -36,12 +36,18 @@ struct Sell {
 // Optional per-launch accounting (CUDA events around every launch, with the
 // launch's algorithmic byte count); installed by the solver when profiling.
 enum KernelClass { K_SPMV = 0, K_SMOOTH = 1, K_VECTOR = 2, K_COARSE = 3, K_ARNOLDI = 4, K_NCLASS = 5 };
+// sig identifies the kernel variant: for SpMV / smoothing
+// kind*1000 + br*100 + bc*10 + (float64 ? 1 : 0); otherwise a small id.
+// rows = block rows (sparse kernels) or vector length.
 struct LaunchHook {
-  virtual void before(cudaStream_t s) = 0;
-  virtual void after(cudaStream_t s, int cls, double bytes) = 0;
+  // returns false when this launch is not to be recorded (after() is then skipped)
+  virtual bool before(cudaStream_t s, int cls, int sig, int64_t rows) = 0;
+  virtual void after(cudaStream_t s, int cls, double bytes, int sig, int64_t rows) = 0;
   virtual ~LaunchHook() {}
 };
 void set_launch_hook(LaunchHook *h);
+// one-time device settings (call before any stream capture)
+void init();
 
 template <typename T> inline const T *vals(const Sell &A);
 template <> inline const double *vals<double>(const Sell &A) { return A.v64; }
@@ -56,6 +62,18 @@ struct DenseLU {
 // y = alpha * A x + beta * z   (z may alias y or be null when beta == 0)
 template <typename T>
 void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStream_t s);
+
+// All blocks of one block row of fields that share one sparsity pattern,
+// merged: each slot holds [A_i0 | A_i1 | A_i2] (br x (b0+b1+b2), row-major,
+// SELL-32 layout of M); y = A_i0 x_0 + A_i1 x_1 + A_i2 x_2 (float64).
+struct RowMerged {
+  Sell M;          // br x bct blocks, bct = b[0] + b[1] + b[2]
+  int nb = 0;      // number of merged column fields (2 or 3)
+  int b[3] = {0, 0, 0};
+  int64_t off[3] = {0, 0, 0};  // offset of each column field in the coupled vector
+};
+bool rows_supported(int br, const int *b, int nb);
+void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s);
 
 // One smoothing step on A with point-diagonal inverse dinv:
 //   r = b - A x;  d = c1 * d + c2 * dinv * r;  xout = x + d

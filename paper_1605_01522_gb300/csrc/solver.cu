@@ -436,42 +436,106 @@ template <typename T> struct Precond {
   }
 };
 
-// Per-launch CUDA-event accounting by kernel class (enabled by params.profile).
+// Per-launch CUDA-event accounting (enabled by params.profile).  Direct
+// launches take events from a pool that is read back at each collect();
+// launches recorded while a graph is being captured become external event
+// record nodes of that graph, owned by the graph's record list and read back
+// after every replay.
+struct ProfRec {
+  cudaEvent_t e0, e1;
+  int cls, sig;
+  int64_t rows;
+  double bytes;
+};
+
+struct KStat {
+  double launches = 0, ms = 0, bytes = 0;
+};
+
 struct EventProf : dev::LaunchHook {
-  std::vector<cudaEvent_t> ev;
+  std::vector<cudaEvent_t> pool;
   size_t used = 0;
-  std::vector<std::pair<int, double>> meta;
-  double ms[dev::K_NCLASS] = {0}, bytes[dev::K_NCLASS] = {0}, launches[dev::K_NCLASS] = {0};
-  cudaEvent_t next() {
-    if (used == ev.size()) {
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> *cap_events = nullptr;  // non-null while capturing
+  std::vector<ProfRec> *cap_recs = nullptr;
+  std::vector<const std::vector<ProfRec> *> pending;  // graph records replayed since the last collect
+  cudaEvent_t open = nullptr;
+  KStat cls[dev::K_NCLASS];
+  std::map<std::pair<int, int64_t>, KStat> detail;  // (cls*100000 + sig, rows)
+
+  cudaEvent_t take() {
+    if (cap_events) {
       cudaEvent_t e;
       MFS_CUDA(cudaEventCreate(&e));
-      ev.push_back(e);
+      cap_events->push_back(e);
+      return e;
     }
-    return ev[used++];
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      MFS_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    return pool[used++];
   }
-  void before(cudaStream_t s) override { MFS_CUDA(cudaEventRecord(next(), s)); }
-  void after(cudaStream_t s, int cls, double b) override {
-    MFS_CUDA(cudaEventRecord(next(), s));
-    meta.push_back({cls, b});
+  void record(cudaEvent_t e, cudaStream_t s) {
+    if (cap_events) MFS_CUDA(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal));
+    else MFS_CUDA(cudaEventRecord(e, s));
   }
+  int filter_key = 0;        // 0: record every launch; else only cls*100000 + sig ...
+  int64_t filter_rows = 0;   // ... with this many rows (0: any)
+  bool before(cudaStream_t s, int c, int sig, int64_t rows) override {
+    if (filter_key && (c * 100000 + sig != filter_key || (filter_rows && rows != filter_rows))) return false;
+    open = take();
+    record(open, s);
+    return true;
+  }
+  void after(cudaStream_t s, int c, double b, int sig, int64_t rows) override {
+    cudaEvent_t e1 = take();
+    record(e1, s);
+    ProfRec r{open, e1, c, sig, rows, b};
+    (cap_recs ? cap_recs : &recs)->push_back(r);
+  }
+  void add(const ProfRec &r) {
+    float t = 0.f;
+    MFS_CUDA(cudaEventElapsedTime(&t, r.e0, r.e1));
+    KStat &a = cls[r.cls];
+    a.launches += 1;
+    a.ms += t;
+    a.bytes += r.bytes;
+    KStat &d = detail[{r.cls * 100000 + r.sig, r.rows}];
+    d.launches += 1;
+    d.ms += t;
+    d.bytes += r.bytes;
+  }
+  // caller has synchronised the stream
   void collect() {
-    if (used) MFS_CUDA(cudaEventSynchronize(ev[used - 1]));
-    for (size_t k = 0; k < meta.size(); ++k) {
-      float t = 0.f;
-      MFS_CUDA(cudaEventElapsedTime(&t, ev[2 * k], ev[2 * k + 1]));
-      ms[meta[k].first] += t;
-      bytes[meta[k].first] += meta[k].second;
-      launches[meta[k].first] += 1;
-    }
+    for (auto &r : recs) add(r);
+    recs.clear();
     used = 0;
-    meta.clear();
+    for (auto *g : pending)
+      for (auto &r : *g) add(r);
+    pending.clear();
   }
   void reset() {
-    for (int c = 0; c < dev::K_NCLASS; ++c) ms[c] = bytes[c] = launches[c] = 0;
+    for (auto &c : cls) c = KStat();
+    detail.clear();
   }
   ~EventProf() override {
-    for (auto e : ev) cudaEventDestroy(e);
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// One captured GMRES iteration body (fixed pointers for a given Krylov index).
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> events;
+  std::vector<ProfRec> recs;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (auto e : events) cudaEventDestroy(e);
+    exec = nullptr;
+    events.clear();
+    recs.clear();
   }
 };
 
@@ -487,6 +551,7 @@ struct mfs_handle {
   cudaStream_t s = nullptr;
   Arena ar;
   std::map<std::pair<int, int>, dev::Sell> A64;
+  std::vector<dev::RowMerged> rows64;  // per row field, when its blocks share one pattern
   std::unique_ptr<Precond<double>> p64;
   std::unique_ptr<Precond<float>> p32;
   HGroup hg0, hg1;
@@ -503,8 +568,13 @@ struct mfs_handle {
   double *hpin = nullptr;
   double setup_ms = 0.0;
   std::unique_ptr<EventProf> prof;
+  bool own_stream = false;
+  bool use_graphs = true;
+  std::vector<IterGraph> graphs;  // per Krylov index j
   ~mfs_handle() {
+    for (auto &g : graphs) g.release();
     if (hpin) cudaFreeHost(hpin);
+    if (own_stream && s) cudaStreamDestroy(s);
   }
 };
 
@@ -524,6 +594,10 @@ bool is_device_ptr(const void *p) {
 }
 
 void matvec(mfs_handle *h, const double *x, double *y) {
+  if (!h->rows64.empty()) {
+    for (int i = 0; i < h->nf; ++i) dev::spmv_rows(h->rows64[i], x, y + h->foff[i], h->s);
+    return;
+  }
   for (int i = 0; i < h->nf; ++i) {
     bool first = true;
     for (int j = 0; j < h->nf; ++j) {
@@ -556,6 +630,36 @@ double dot_host(mfs_handle *h, const double *x, const double *y) {
   return h->hpin[0];
 }
 
+// Capture body() once per Krylov index j into a CUDA graph and replay it:
+// one launch per GMRES iteration instead of one per kernel.
+template <typename F> void run_graph(mfs_handle *h, int j, F &&body) {
+  IterGraph &g = h->graphs[j];
+  if (!g.exec) {
+    if (h->prof) {
+      h->prof->cap_events = &g.events;
+      h->prof->cap_recs = &g.recs;
+    }
+    cudaGraph_t graph = nullptr;
+    MFS_CUDA(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    try {
+      body();
+    } catch (...) {
+      cudaStreamEndCapture(h->s, &graph);
+      if (graph) cudaGraphDestroy(graph);
+      if (h->prof) h->prof->cap_events = nullptr, h->prof->cap_recs = nullptr;
+      g.release();
+      throw;
+    }
+    if (h->prof) h->prof->cap_events = nullptr, h->prof->cap_recs = nullptr;
+    MFS_CUDA(cudaStreamEndCapture(h->s, &graph));
+    const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MFS_CUDA(e);
+  }
+  MFS_CUDA(cudaGraphLaunch(g.exec, h->s));
+  if (h->prof) h->prof->pending.push_back(&g.recs);
+}
+
 int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info) {
   const int64_t n = h->n;
   const int m = h->m;
@@ -585,22 +689,26 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jend = 0;
-    bool stop = false;
     for (int j = 0; j < m; ++j) {
       double *vj = h->V + (int64_t)j * n;
       double *zj = h->Z + (int64_t)j * n;
       double *w = h->V + (int64_t)(j + 1) * n;
-      precond_apply(h, vj, zj);
-      matvec(h, zj, w);
-      // CGS2: h1 = V^T w (and |w|^2), w -= V h1, h2 = V^T w, w -= V h2 (and |w|^2)
-      dev::mdot(h->V, n, j + 2, w, n, h->partial, h->nblk, s);
-      dev::reduce_partials(h->partial, j + 2, h->nblk, h->hdev, s);
-      dev::cgs_fused(h->V, n, j + 1, h->hdev, w, n, h->partial, h->nblk, s);
-      dev::reduce_partials(h->partial, j + 1, h->nblk, h->hdev + 64, s);
-      dev::cgs_update(h->V, n, j + 1, h->hdev + 64, w, n, h->partial, h->nblk, s);
-      dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + 128, s);
-      MFS_CUDA(cudaMemcpyAsync(hp, h->hdev, 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      auto body = [&]() {
+        precond_apply(h, vj, zj);
+        matvec(h, zj, w);
+        // CGS2: h1 = V^T w (and |w|^2), w -= V h1, h2 = V^T w, w -= V h2 (and |w|^2)
+        dev::mdot(h->V, n, j + 2, w, n, h->partial, h->nblk, s);
+        dev::reduce_partials(h->partial, j + 2, h->nblk, h->hdev, s);
+        dev::cgs_fused(h->V, n, j + 1, h->hdev, w, n, h->partial, h->nblk, s);
+        dev::reduce_partials(h->partial, j + 1, h->nblk, h->hdev + 64, s);
+        dev::cgs_update(h->V, n, j + 1, h->hdev + 64, w, n, h->partial, h->nblk, s);
+        dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + 128, s);
+        MFS_CUDA(cudaMemcpyAsync(hp, h->hdev, 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      };
+      if (h->use_graphs) run_graph(h, j, body);
+      else body();
       MFS_CUDA(cudaStreamSynchronize(s));
+      if (h->prof) h->prof->collect();
       const double nw0 = std::sqrt(hp[j + 1]);
       const double hn = std::sqrt(hp[128]);
       if (!std::isfinite(hn) || !std::isfinite(nw0)) return MFS_ERR_BREAKDOWN;
@@ -628,13 +736,9 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
       jend = j + 1;
       est = std::fabs(g[j + 1]) / r0;
       const bool happy = hn <= 1e-14 * nw0;
-      if (est <= tol || happy || iters >= h->prm.max_iters) {
-        stop = true;
-        break;
-      }
+      if (est <= tol || happy || iters >= h->prm.max_iters) break;
       dev::scale(w, 1.0 / hn, w, n, s);
     }
-    (void)stop;
     for (int k = jend - 1; k >= 0; --k) {
       double sum = g[k];
       for (int q = k + 1; q < jend; ++q) sum -= H[(size_t)q * (m + 1) + k] * y[q];
@@ -676,6 +780,57 @@ HBsr to_hbsr(const mfs_block &b) {
     }
   }
   return A;
+}
+
+// Fine operator rows: when every block A_ij of a block row i exists and all
+// share one sparsity pattern (fields on the same nodes), store the row's
+// blocks side by side so one kernel reads each column index once and writes
+// y_i once.  Empty result = per-block SpMVs.
+std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb, int nf,
+                                       const std::vector<int64_t> &foff) {
+  std::vector<dev::RowMerged> out;
+  if (nf < 2 || nf > 3) return out;
+  for (int i = 0; i < nf; ++i) {
+    std::vector<const HBsr *> row;
+    for (int j = 0; j < nf; ++j) {
+      auto it = hb.find({i, j});
+      if (it == hb.end()) return {};
+      row.push_back(&it->second);
+    }
+    int b[3] = {0, 0, 0};
+    for (int j = 0; j < nf; ++j) {
+      if (row[j]->rp != row[0]->rp || row[j]->ci != row[0]->ci) return {};
+      b[j] = row[j]->bc;
+    }
+    const int br = row[0]->br;
+    if (!dev::rows_supported(br, b, nf)) return {};
+    HBsr M;
+    M.br = br;
+    M.bc = b[0] + b[1] + b[2];
+    M.nbr = row[0]->nbr;
+    M.nbc = row[0]->nbc;
+    M.rp = row[0]->rp;
+    M.ci = row[0]->ci;
+    M.v.assign((size_t)M.nnzb() * M.br * M.bc, 0.0);
+    for (int64_t k = 0; k < M.nnzb(); ++k)
+      for (int r = 0; r < br; ++r) {
+        int o = 0;
+        for (int j = 0; j < nf; ++j) {
+          for (int q = 0; q < b[j]; ++q) M.v[(size_t)k * br * M.bc + r * M.bc + o + q] = row[j]->blk(k)[r * b[j] + q];
+          o += b[j];
+        }
+      }
+    dev::RowMerged R;
+    R.M = upload_sell(ar, M, true, false);
+    if (R.M.kind != 0) return {};
+    R.nb = nf;
+    for (int j = 0; j < nf; ++j) {
+      R.b[j] = b[j];
+      R.off[j] = foff[j];
+    }
+    out.push_back(R);
+  }
+  return out;
 }
 
 // Host half of the setup: hierarchies, SIMPLE diagonal and explicit S~.
@@ -877,6 +1032,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     h->prm = p;
     h->nf = nfields;
     h->s = (cudaStream_t)p.cuda_stream;
+    h->use_graphs = p.no_graphs == 0;
     std::vector<FieldInfo> info(nfields);
     h->foff.assign(nfields + 1, 0);
     for (int i = 0; i < nfields; ++i) {
@@ -918,8 +1074,15 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       *out = h.release();
       return MFS_OK;
     }
+    dev::init();
+    if (!h->s) {
+      // the legacy default stream cannot be captured: use a blocking stream of our own
+      MFS_CUDA(cudaStreamCreate(&h->s));
+      h->own_stream = true;
+    }
     const bool f32 = p.precision == MFS_FP32P;
     for (auto &kv : hb) h->A64[kv.first] = upload_sell(h->ar, kv.second, true, f32);
+    h->rows64 = merge_rows(h->ar, hb, h->nf, h->foff);
     if (f32) {
       h->p32.reset(new Precond<float>());
       upload_precond<float>(h.get(), *h->p32, hb, true);
@@ -930,6 +1093,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       upload_precond<double>(h.get(), *h->p64, hb, false);
     }
     h->m = p.restart;
+    h->graphs.resize(h->m);
     h->nblk = dev::mdot_blocks(h->n);
     h->V = h->ar.zeros<double>((int64_t)(h->m + 1) * h->n);
     h->Z = h->ar.zeros<double>((int64_t)h->m * h->n);
@@ -1115,11 +1279,38 @@ int mfs_kernel_stats(mfs_handle *h, double *out, int cap, int reset) {
   if (!h->prof) return fail(MFS_ERR_INVALID, "handle was built without profile");
   int k = 0;
   for (int c = 0; c < dev::K_NCLASS && 3 * c + 2 < cap; ++c, ++k) {
-    out[3 * c] = h->prof->launches[c];
-    out[3 * c + 1] = h->prof->ms[c];
-    out[3 * c + 2] = h->prof->bytes[c];
+    out[3 * c] = h->prof->cls[c].launches;
+    out[3 * c + 1] = h->prof->cls[c].ms;
+    out[3 * c + 2] = h->prof->cls[c].bytes;
   }
   if (reset) h->prof->reset();
+  return k;
+}
+
+int mfs_profile_filter(mfs_handle *h, int key, int64_t rows) {
+  if (!h) return fail(MFS_ERR_INVALID, "bad handle");
+  if (!h->prof) return fail(MFS_ERR_INVALID, "handle was built without profile");
+  h->prof->filter_key = key;
+  h->prof->filter_rows = rows;
+  for (auto &g : h->graphs) g.release();  // recapture with the new set of event nodes
+  return MFS_OK;
+}
+
+int mfs_kernel_detail(mfs_handle *h, double *out, int cap) {
+  if (!h || !out) return fail(MFS_ERR_INVALID, "bad stats arguments");
+  if (!h->prof) return fail(MFS_ERR_INVALID, "handle was built without profile");
+  std::vector<std::pair<std::pair<int, int64_t>, KStat>> rows(h->prof->detail.begin(), h->prof->detail.end());
+  std::sort(rows.begin(), rows.end(), [](const auto &a, const auto &b) { return a.second.ms > b.second.ms; });
+  int k = 0;
+  for (auto &r : rows) {
+    if (5 * k + 4 >= cap) break;
+    out[5 * k] = r.first.first;
+    out[5 * k + 1] = (double)r.first.second;
+    out[5 * k + 2] = r.second.launches;
+    out[5 * k + 3] = r.second.ms;
+    out[5 * k + 4] = r.second.bytes;
+    ++k;
+  }
   return k;
 }
 

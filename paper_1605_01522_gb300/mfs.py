@@ -28,9 +28,25 @@ ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
 EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_ndofs",
-           "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_free",
+           "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
+_OTHER = {2: {1: "smooth_first", 2: "fill", 3: "axpy_diag", 4: "axpy", 5: "convert", 6: "scale"},
+          3: {1: "lu_solve"},
+          4: {1: "mdot", 2: "reduce_partials", 3: "cgs_fused", 4: "cgs_update", 5: "gemv_add"}}
+
+
+def kernel_name(key: int) -> str:
+    """Readable name of a mfs_kernel_detail key (class*100000 + signature)."""
+    cls, sig = divmod(key, 100000)
+    if cls in (0, 1):
+        kind, rest = divmod(sig, 1000)
+        br, rest = divmod(rest, 100)
+        bc, f64 = divmod(rest, 10)
+        base = "spmv" if cls == 0 else "smooth"
+        layout = {0: "sell", 1: "warp", 2: "rows"}.get(kind, str(kind))
+        return f"{base}_{layout}<{br}x{bc},{'f64' if f64 else 'f32'}>"
+    return _OTHER.get(cls, {}).get(sig, f"class{cls}_id{sig}")
 
 
 class Block(C.Structure):
@@ -54,7 +70,7 @@ class Params(C.Structure):
                 ("jacobi_omega", C.c_double), ("jacobi_sweeps", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("no_graphs", C.c_int)]
 
 
 class Info(C.Structure):
@@ -108,6 +124,10 @@ def load(build_if_missing: bool = True):
     lib.mfs_num_levels.restype = C.c_int
     lib.mfs_kernel_stats.argtypes = [H, C.POINTER(C.c_double), C.c_int, C.c_int]
     lib.mfs_kernel_stats.restype = C.c_int
+    lib.mfs_kernel_detail.argtypes = [H, C.POINTER(C.c_double), C.c_int]
+    lib.mfs_kernel_detail.restype = C.c_int
+    lib.mfs_profile_filter.argtypes = [H, C.c_int, C.c_int64]
+    lib.mfs_profile_filter.restype = C.c_int
     lib.mfs_free.argtypes = [H]
     lib.mfs_free.restype = None
     lib.mfs_strerror.argtypes = [C.c_int]
@@ -259,6 +279,26 @@ class Solver:
         if k < 0:
             raise MfsError(k, "mfs_kernel_stats")
         return {KERNEL_CLASSES[c]: (int(out[3 * c]), out[3 * c + 1], out[3 * c + 2]) for c in range(k)}
+
+    def kernel_detail(self):
+        """Per-kernel rows (name, rows, launches, ms, algorithmic bytes), slowest first.
+        Call before kernel_stats(reset=True)."""
+        cap = 5 * 512
+        out = (C.c_double * cap)()
+        k = self.lib.mfs_kernel_detail(self.h, out, cap)
+        if k < 0:
+            raise MfsError(k, "mfs_kernel_detail")
+        rows = []
+        for r in range(k):
+            key, nrows, launches, ms, nbytes = (out[5 * r + q] for q in range(5))
+            rows.append((kernel_name(int(key)), int(nrows), int(launches), ms, nbytes, int(key)))
+        return rows
+
+    def profile_filter(self, key=0, rows=0):
+        """Time only the kernel with this detail key (0 = all kernels)."""
+        rc = self.lib.mfs_profile_filter(self.h, key, rows)
+        if rc != OK:
+            raise MfsError(rc, "mfs_profile_filter")
 
     def close(self):
         if getattr(self, "h", None):
