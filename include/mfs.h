@@ -154,6 +154,13 @@ int mfs_apply(struct mfs_handle *h, const double *v, double *z);
 /* y = A x with the fine coupled operator (all nonzero blocks), float64. */
 int mfs_matvec(struct mfs_handle *h, const double *x, double *y);
 
+/* *out = x . y for two device vectors of n float64 (n = mfs_ndofs), with
+ * the solver's deterministic two-stage reduction (fixed per-block chunks,
+ * then one block sums the partials; the Arnoldi dot products of Sec. 3.1's
+ * GMRES use the same kernels).  The partial sums live in the handle's
+ * device scratch.  Host pointers are rejected (MFS_ERR_INVALID). */
+int mfs_dot(struct mfs_handle *h, const double *x, const double *y, double *out);
+
 /* Total scalar dofs n of the coupled system. */
 int64_t mfs_ndofs(const struct mfs_handle *h);
 
@@ -187,9 +194,9 @@ int mfs_num_levels(const struct mfs_handle *h, int group);
  * hook is process-wide: profile one handle at a time. */
 int mfs_kernel_stats(struct mfs_handle *h, double *out, int cap, int reset);
 
-/* Per-kernel accounting behind mfs_kernel_stats: one row of 5 doubles per
+/* Per-kernel accounting behind mfs_kernel_stats: one row of 6 doubles per
  * kernel variant and size, sorted by summed time: [cls*100000 + sig, rows,
- * launches, ms, algorithmic bytes], where for SpMV (cls 0) and smoothing
+ * launches, ms, algorithmic bytes, algorithmic flops], where for SpMV (cls 0) and smoothing
  * (cls 1) sig = layout*1000 + br*100 + bc*10 + (float64 ? 1 : 0) with layout
  * 0 = SELL-32 / 1 = warp-per-row BSR, and rows = block rows; for the other
  * classes sig is a kernel id and rows the vector length.  Returns the number

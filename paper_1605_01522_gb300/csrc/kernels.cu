@@ -20,12 +20,14 @@ struct HookScope {
   double bytes;
   int sig;
   int64_t rows;
+  double flops;
   bool on = false;
-  HookScope(cudaStream_t s_, int c, double b, int sg = 0, int64_t r = 0) : s(s_), cls(c), bytes(b), sig(sg), rows(r) {
+  HookScope(cudaStream_t s_, int c, double b, int sg, int64_t r, double f)
+      : s(s_), cls(c), bytes(b), sig(sg), rows(r), flops(f) {
     if (g_hook) on = g_hook->before(s, cls, sig, rows);
   }
   ~HookScope() {
-    if (on) g_hook->after(s, cls, bytes, sig, rows);
+    if (on) g_hook->after(s, cls, bytes, sig, rows, flops);
   }
 };
 
@@ -502,7 +504,7 @@ void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStre
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
   HookScope hs(s, K_SPMV, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + A.nrows() * (z ? 2 : 1)),
-               sparse_sig<T>(A), A.nbr);
+               sparse_sig<T>(A), A.nbr, 2.0 * A.nnzb * A.br * A.bc + (z ? 3.0 : 1.0) * A.nrows());
   if (A.kind == 1) {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
                        (k_spmv_warp<BR_, BC_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
@@ -547,7 +549,7 @@ void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s) {
   if (A.nbr == 0) return;
   HookScope hs(s, K_SPMV,
                (double)A.nnzb * (A.br * A.bc * 8.0 + 4.0) + 4.0 * A.nbr + 8.0 * (A.nbc * A.bc + A.nrows()),
-               2000 + A.br * 100 + A.bc * 10 + 1, A.nbr);
+               2000 + A.br * 100 + A.bc * 10 + 1, A.nbr, 2.0 * A.nnzb * A.br * A.bc);
   const double *x0 = x + R.off[0], *x1 = x + R.off[1], *x2 = R.nb > 2 ? x + R.off[2] : x;
   const int b3[3] = {R.b[0], R.b[1], R.nb > 2 ? R.b[2] : 0};
   MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2><<<grid_for(A.nbr), kThreads, 0, s>>>(
@@ -560,7 +562,7 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
   HookScope hs(s, K_SMOOTH, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + 5.0 * A.nrows()),
-               sparse_sig<T>(A), A.nbr);
+               sparse_sig<T>(A), A.nbr, 2.0 * A.nnzb * A.br * A.bc + 6.0 * A.nrows());
   if (A.kind == 1) {
     MFS_SQUARE_DISPATCH(A.br, (k_smooth_warp<BR_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
                                   A.nbr, A.sp, A.col, v, dinv, b, x, xout, d, c1, c2)));
@@ -573,40 +575,41 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
 template <typename T>
 void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s) {
   if (n == 0) return;
-  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 1, n);
+  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 1, n, 2.0 * n);
   k_smooth_first<T><<<ew_grid(n), kThreads, 0, s>>>(n, dinv, b, x, d, c2);
 }
 
 template <typename T>
 void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   if (lu.n == 0) return;
-  HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n);
+  HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n,
+               2.0 * lu.n * (double)lu.n);
   const size_t smem = (size_t)lu.n * sizeof(double);
   k_lu_solve<T><<<1, 1024, smem, s>>>(lu.n, lu.lu, lu.perm, b, x);
 }
 
 template <typename T>
 void fill(T *x, int64_t n, T v, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, (double)n * sizeof(T), 2, n);
+  HookScope hs(s, K_VECTOR, (double)n * sizeof(T), 2, n, 0.0);
   if (n) k_fill<T><<<ew_grid(n), kThreads, 0, s>>>(x, n, v);
 }
 template <typename T>
 void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 3, n);
+  HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 3, n, 2.0 * n);
   if (n) k_axpy_diag<T><<<ew_grid(n), kThreads, 0, s>>>(x, dinv, t, n);
 }
 template <typename T>
 void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T), 4, n);
+  HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T), 4, n, 2.0 * n);
   if (n) k_axpy<T><<<ew_grid(n), kThreads, 0, s>>>(y, x, a, n);
 }
 template <typename TI, typename TO>
 void convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)), 5, n);
+  HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)), 5, n, 0.0);
   if (n) k_convert<TI, TO><<<ew_grid(n), kThreads, 0, s>>>(in, out, n);
 }
 void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_VECTOR, 16.0 * n, 6, n);
+  HookScope hs(s, K_VECTOR, 16.0 * n, 6, n, (double)n);
   if (n) k_scale<<<ew_grid(n), kThreads, 0, s>>>(x, a, y, n);
 }
 
@@ -619,29 +622,29 @@ int mdot_blocks(int64_t n) {
 
 void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, double *partial, int nblk,
           cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 1), 1, n);
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 1), 1, n, 2.0 * n * k);
   k_mdot<<<nblk, kThreads, 0, s>>>(V, ldv, k, w, n, partial, nblk);
 }
 
 void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk, 2, k);
+  HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk, 2, k, (double)k * nblk);
   k_reduce_partials<<<k, kThreads, 0, s>>>(partial, nblk, out);
 }
 
 void cgs_fused(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n, double *partial,
                int nblk, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 3, n);
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 3, n, 4.0 * n * k);
   k_cgs_fused<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
 }
 
 void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,
                 double *partial, int nblk, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 4, n);
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 4, n, 2.0 * n * k + 2.0 * n);
   k_cgs_update<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
 }
 
 void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, int64_t n, cudaStream_t s) {
-  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 5, n);
+  HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 5, n, 2.0 * n * k);
   k_gemv_add<<<ew_grid(n), kThreads, 0, s>>>(Z, ldz, k, y, x, n);
 }
 

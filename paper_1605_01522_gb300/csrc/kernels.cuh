@@ -42,7 +42,7 @@ enum KernelClass { K_SPMV = 0, K_SMOOTH = 1, K_VECTOR = 2, K_COARSE = 3, K_ARNOL
 struct LaunchHook {
   // returns false when this launch is not to be recorded (after() is then skipped)
   virtual bool before(cudaStream_t s, int cls, int sig, int64_t rows) = 0;
-  virtual void after(cudaStream_t s, int cls, double bytes, int sig, int64_t rows) = 0;
+  virtual void after(cudaStream_t s, int cls, double bytes, int sig, int64_t rows, double flops) = 0;
   virtual ~LaunchHook() {}
 };
 void set_launch_hook(LaunchHook *h);

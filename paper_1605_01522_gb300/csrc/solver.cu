@@ -445,11 +445,11 @@ struct ProfRec {
   cudaEvent_t e0, e1;
   int cls, sig;
   int64_t rows;
-  double bytes;
+  double bytes, flops;
 };
 
 struct KStat {
-  double launches = 0, ms = 0, bytes = 0;
+  double launches = 0, ms = 0, bytes = 0, flops = 0;
 };
 
 struct EventProf : dev::LaunchHook {
@@ -489,10 +489,10 @@ struct EventProf : dev::LaunchHook {
     record(open, s);
     return true;
   }
-  void after(cudaStream_t s, int c, double b, int sig, int64_t rows) override {
+  void after(cudaStream_t s, int c, double b, int sig, int64_t rows, double f) override {
     cudaEvent_t e1 = take();
     record(e1, s);
-    ProfRec r{open, e1, c, sig, rows, b};
+    ProfRec r{open, e1, c, sig, rows, b, f};
     (cap_recs ? cap_recs : &recs)->push_back(r);
   }
   void add(const ProfRec &r) {
@@ -502,10 +502,12 @@ struct EventProf : dev::LaunchHook {
     a.launches += 1;
     a.ms += t;
     a.bytes += r.bytes;
+    a.flops += r.flops;
     KStat &d = detail[{r.cls * 100000 + r.sig, r.rows}];
     d.launches += 1;
     d.ms += t;
     d.bytes += r.bytes;
+    d.flops += r.flops;
   }
   // caller has synchronised the stream
   void collect() {
@@ -1193,6 +1195,19 @@ static int with_io(mfs_handle *h, const double *in, double *out, void (*fn)(mfs_
   return MFS_OK;
 }
 
+int mfs_dot(mfs_handle *h, const double *x, const double *y, double *out) {
+  if (!h || !x || !y || !out) return fail(MFS_ERR_INVALID, "bad dot arguments");
+  if (h->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(MFS_ERR_INVALID, "mfs_dot needs device vectors");
+  try {
+    *out = dot_host(h, x, y);
+    MFS_CUDA(cudaGetLastError());
+  } catch (const CudaError &e) {
+    return fail(e.code, e.what());
+  }
+  return MFS_OK;
+}
+
 int mfs_apply(mfs_handle *h, const double *v, double *z) {
   if (!h || !v || !z || v == z) return fail(MFS_ERR_INVALID, "bad apply arguments");
   return with_io(h, v, z, precond_apply);
@@ -1303,12 +1318,13 @@ int mfs_kernel_detail(mfs_handle *h, double *out, int cap) {
   std::sort(rows.begin(), rows.end(), [](const auto &a, const auto &b) { return a.second.ms > b.second.ms; });
   int k = 0;
   for (auto &r : rows) {
-    if (5 * k + 4 >= cap) break;
-    out[5 * k] = r.first.first;
-    out[5 * k + 1] = (double)r.first.second;
-    out[5 * k + 2] = r.second.launches;
-    out[5 * k + 3] = r.second.ms;
-    out[5 * k + 4] = r.second.bytes;
+    if (6 * k + 5 >= cap) break;
+    out[6 * k] = r.first.first;
+    out[6 * k + 1] = (double)r.first.second;
+    out[6 * k + 2] = r.second.launches;
+    out[6 * k + 3] = r.second.ms;
+    out[6 * k + 4] = r.second.bytes;
+    out[6 * k + 5] = r.second.flops;
     ++k;
   }
   return k;

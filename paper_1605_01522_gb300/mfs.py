@@ -27,7 +27,7 @@ PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
-EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_ndofs",
+EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_ndofs",
            "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
@@ -111,6 +111,8 @@ def load(build_if_missing: bool = True):
     lib.mfs_apply.restype = C.c_int
     lib.mfs_matvec.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.mfs_matvec.restype = C.c_int
+    lib.mfs_dot.argtypes = [H, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
+    lib.mfs_dot.restype = C.c_int
     lib.mfs_ndofs.argtypes = [H]
     lib.mfs_ndofs.restype = C.c_int64
     lib.mfs_export_csr.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -238,6 +240,14 @@ class Solver:
             raise MfsError(rc, "mfs_matvec")
         return y
 
+    def dot(self, x, y):
+        """x . y (device float64 vectors of length n) with the solver's reduction."""
+        out = C.c_double()
+        rc = self.lib.mfs_dot(self.h, _ptr(x), _ptr(y), C.byref(out))
+        if rc != OK:
+            raise MfsError(rc, "mfs_dot")
+        return out.value
+
     def num_levels(self, group=0):
         return self.lib.mfs_num_levels(self.h, group)
 
@@ -281,17 +291,17 @@ class Solver:
         return {KERNEL_CLASSES[c]: (int(out[3 * c]), out[3 * c + 1], out[3 * c + 2]) for c in range(k)}
 
     def kernel_detail(self):
-        """Per-kernel rows (name, rows, launches, ms, algorithmic bytes), slowest first.
+        """Per-kernel rows (name, rows, launches, ms, algorithmic bytes, key, flops), slowest first.
         Call before kernel_stats(reset=True)."""
-        cap = 5 * 512
+        cap = 6 * 512
         out = (C.c_double * cap)()
         k = self.lib.mfs_kernel_detail(self.h, out, cap)
         if k < 0:
             raise MfsError(k, "mfs_kernel_detail")
         rows = []
         for r in range(k):
-            key, nrows, launches, ms, nbytes = (out[5 * r + q] for q in range(5))
-            rows.append((kernel_name(int(key)), int(nrows), int(launches), ms, nbytes, int(key)))
+            key, nrows, launches, ms, nbytes, flops = (out[6 * r + q] for q in range(6))
+            rows.append((kernel_name(int(key)), int(nrows), int(launches), ms, nbytes, int(key), flops))
         return rows
 
     def profile_filter(self, key=0, rows=0):

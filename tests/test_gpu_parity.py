@@ -143,3 +143,15 @@ def test_single_field_and_single_level():
                 assert np.linalg.norm(one.rhs - A @ x) <= 1e-8 * np.linalg.norm(one.rhs)
                 if kw["max_levels"] == 1:
                     assert info["iters"] == 1
+
+
+def test_dot_matches_host():
+    s, kw = _small("3d2")
+    rng = np.random.default_rng(12)
+    with mfs.Solver(s, **kw) as lib:
+        for _ in range(2):
+            x, y = rng.standard_normal(s.ndofs), rng.standard_normal(s.ndofs)
+            d = lib.dot(_cuda(x), _cuda(y))
+            assert abs(d - float(np.dot(x, y))) <= 1e-13 * np.abs(x).max() * np.abs(y).max() * s.ndofs ** 0.5
+        with pytest.raises(mfs.MfsError):
+            lib.dot(x, y)  # host vectors are rejected
