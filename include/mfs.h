@@ -161,6 +161,30 @@ int mfs_matvec(struct mfs_handle *h, const double *x, double *y);
  * device scratch.  Host pointers are rejected (MFS_ERR_INVALID). */
 int mfs_dot(struct mfs_handle *h, const double *x, const double *y, double *out);
 
+/* Allocation-free variant of mfs_dot.  The paper has no counterpart: it is
+ * for callers that must not call cudaMalloc while they run - a host
+ * framework whose caching allocator already holds the device memory, a
+ * latency-critical loop that cannot take cudaMalloc's implicit device-wide
+ * synchronisation, or a plug-in that may only allocate at initialisation.
+ * *out (host) = x . y for device float64 vectors x, y of length n, computed
+ * by the same two-stage reduction kernels as mfs_dot on `stream` (NULL =
+ * legacy default stream) and synchronised before return; no handle needed.
+ * The partial sums live in a static device array of
+ * MFS_DOT_NOALLOC_PARTIALS + 32 doubles compiled into the library: every
+ * device that loads the library holds it until the process exits.  The
+ * call makes no cudaMalloc / cudaFree or other allocating call.  Its first
+ * call on a device looks up that array's device address
+ * (cudaGetSymbolAddress) with the device current; make that first call
+ * before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other host threads) race, so
+ * serialise them.  Nothing in the array needs clearing between calls.
+ * Errors: MFS_ERR_INVALID for NULL pointers, host vectors, n < 0 or
+ * n > MFS_DOT_NOALLOC_MAX_N (see mfs_last_error); MFS_ERR_CUDA when a CUDA
+ * call fails. */
+#define MFS_DOT_NOALLOC_PARTIALS 1024
+#define MFS_DOT_NOALLOC_MAX_N ((int64_t)1 << 32)
+int mfs_dot_noalloc(const double *x, const double *y, int64_t n, double *out, void *stream);
+
 /* Total scalar dofs n of the coupled system. */
 int64_t mfs_ndofs(const struct mfs_handle *h);
 

@@ -35,6 +35,7 @@ struct CudaError : std::runtime_error {
 };
 
 static thread_local std::string g_last_error;
+void set_last_error(const char *msg) { g_last_error = msg; }
 
 #define MFS_CUDA(call)                                                                      \
   do {                                                                                      \

@@ -27,7 +27,7 @@ PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
-EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_ndofs",
+EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_ndofs",
            "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True):
     lib.mfs_matvec.restype = C.c_int
     lib.mfs_dot.argtypes = [H, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]
     lib.mfs_dot.restype = C.c_int
+    lib.mfs_dot_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_void_p]
+    lib.mfs_dot_noalloc.restype = C.c_int
     lib.mfs_ndofs.argtypes = [H]
     lib.mfs_ndofs.restype = C.c_int64
     lib.mfs_export_csr.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -138,6 +140,21 @@ def load(build_if_missing: bool = True):
     lib.mfs_last_error.restype = C.c_char_p
     _lib = lib
     return lib
+
+
+DOT_NOALLOC_MAX_N = 1 << 32
+
+
+def dot_noalloc(x, y, n=None, stream=None):
+    """x . y of two device float64 vectors through mfs_dot_noalloc (no device
+    allocation; partial sums in the library's static device array)."""
+    lib = load()
+    out = C.c_double()
+    n = x.numel() if n is None else n
+    rc = lib.mfs_dot_noalloc(_ptr(x), _ptr(y), n, C.byref(out), stream)
+    if rc != OK:
+        raise MfsError(rc, "mfs_dot_noalloc")
+    return out.value
 
 
 class MfsError(RuntimeError):
