@@ -147,6 +147,26 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
  * iterate in x when max_iters is reached. */
 int mfs_solve(struct mfs_handle *h, const double *rhs, double *x, double tol, mfs_info *info);
 
+/* A new handle for the same system that shares `src`'s read-only device
+ * hierarchy (matrices, transfers, smoother data, LU factors) and host copy,
+ * with its own work vectors, Krylov basis, CUDA graphs and stream (`stream`,
+ * or a new library-owned one when NULL).  Clones of one setup can solve
+ * different right-hand sides at the same time (mfs_solve_batch).  The shared
+ * data lives until the last of the handles is freed.  Profiling is off in
+ * clones. */
+int mfs_clone(const struct mfs_handle *src, void *stream, struct mfs_handle **out);
+
+/* Solve nsys independent systems, one per handle (distinct handles; clones
+ * of one setup allowed), each A_k x_k = rhs_k to tol as mfs_solve does.
+ * `nthreads` host threads (<= 0: 16) each drive one handle's FGMRES at a
+ * time on that handle's stream, so the systems' kernels overlap on the GPU;
+ * every result is bit-for-bit the one mfs_solve gives for that system alone.
+ * infos / status (may be NULL) receive per-system results; the return value
+ * is MFS_OK or the first failing system's code.  The per-launch profiler is
+ * not used in batches. */
+int mfs_solve_batch(struct mfs_handle *const *hs, int nsys, const double *const *rhs, double *const *x, double tol,
+                    mfs_info *infos, int *status, int nthreads);
+
 /* One preconditioner application z = M^-1 v (the Sec. 4 preconditioner with
  * x^(0) = 0 and k_max sweeps).  v, z: n float64, host or device. */
 int mfs_apply(struct mfs_handle *h, const double *v, double *z);

@@ -234,13 +234,22 @@ __global__ void k_smooth_first(int64_t n, const T *__restrict__ dinv, const T *_
 
 // Dense LU solve in one CTA, blocked by 32: one warp solves each 32 x 32
 // diagonal block with shuffles, then all warps update the rows below (above)
-// with that block's 32 new unknowns.  y lives in shared memory.
+// with that block's 32 new unknowns.  y lives in shared memory, and so do the
+// factors when they fit (staged == 1), which keeps the warp's sequential
+// steps off global-memory latency.
 template <typename T>
 __global__ void __launch_bounds__(1024)
-k_lu_solve(int n, const double *__restrict__ lu, const int32_t *__restrict__ perm,
-           const T *__restrict__ b, T *__restrict__ x) {
-  extern __shared__ double y[];
+k_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ perm,
+           const T *__restrict__ b, T *__restrict__ x, int staged) {
+  extern __shared__ double sm[];
+  double *y = sm;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  const double *lu = lu_g;
+  if (staged) {
+    double *ls = sm + n;
+    for (int64_t i = tid; i < (int64_t)n * n; i += nt) ls[i] = lu_g[i];
+    lu = ls;
+  }
   for (int i = tid; i < n; i += nt) y[i] = (double)b[perm[i]];
   __syncthreads();
   // forward: L y = Pb, unit lower triangle
@@ -584,8 +593,11 @@ void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   if (lu.n == 0) return;
   HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n,
                2.0 * lu.n * (double)lu.n);
-  const size_t smem = (size_t)lu.n * sizeof(double);
-  k_lu_solve<T><<<1, 1024, smem, s>>>(lu.n, lu.lu, lu.perm, b, x);
+  // stage the factors in shared memory when y and LU fit in 200 KB
+  const int staged = (size_t)lu.n * (lu.n + 1) * sizeof(double) <= 200 * 1024 ? 1 : 0;
+  const size_t smem = (size_t)lu.n * (staged ? lu.n + 1 : 1) * sizeof(double);
+  const int threads = lu.n <= 64 ? 256 : 1024;
+  k_lu_solve<T><<<1, threads, smem, s>>>(lu.n, lu.lu, lu.perm, b, x, staged);
 }
 
 template <typename T>

@@ -12,6 +12,8 @@
 // Every step of a solve runs as a kernel of kernels.cu; the host only
 // sequences launches and runs the (m+1) x m Givens least-squares update.
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -196,8 +198,9 @@ static void smoother_coeffs(const mfs_params &p, double lam, std::vector<double>
   }
 }
 
-// Build the device copy of a host group.  level0 gives the Sell objects of
-// the level-0 diagonal / off-diagonal blocks (shared with the fine operator).
+// Device copy of a host group's matrices and smoother data (read-only after
+// setup, shared by clones).  level0 gives the Sell objects of the level-0
+// diagonal / off-diagonal blocks (shared with the fine operator).
 template <typename T>
 static void upload_group(Arena &ar, DGroup<T> &g, const HGroup &h, const mfs_params &p,
                          const std::vector<dev::Sell> &level0_diag,
@@ -223,6 +226,23 @@ static void upload_group(Arena &ar, DGroup<T> &g, const HGroup &h, const mfs_par
         f.c1.assign(c1.begin(), c1.end());
         f.c2.assign(c2.begin(), c2.end());
         f.dinv = upload_as<T>(ar, hf.dinv);
+      }
+    }
+    if (l > 0 && mono)
+      for (auto &kv : h.off[l]) g.off[l][kv.first] = upload_sell(ar, kv.second, !f32, f32);
+  }
+  g.cf.resize(g.nf);
+  for (int i = 0; i < g.nf; ++i) g.cf[i] = upload_lu(ar, h.coarse_field[i]);
+  if (mono) g.cc = upload_lu(ar, h.coarse_coupled);
+}
+
+// Work vectors of a group (per handle; a clone gets its own).
+template <typename T> static void alloc_group_work(Arena &ar, DGroup<T> &g) {
+  for (int l = 0; l < g.L; ++l)
+    for (int i = 0; i < g.nf; ++i) {
+      FL<T> &f = g.lv[l][i];
+      f.t = f.d = f.r = f.bv = f.xv = nullptr;
+      if (l + 1 < g.L) {
         f.t = ar.zeros<T>(f.n);
         f.d = ar.zeros<T>(f.n);
         f.r = ar.zeros<T>(f.n);
@@ -230,13 +250,11 @@ static void upload_group(Arena &ar, DGroup<T> &g, const HGroup &h, const mfs_par
       f.c = ar.zeros<T>(f.n);
       f.e = ar.zeros<T>(f.n);
     }
-    if (l > 0 && mono)
-      for (auto &kv : h.off[l]) g.off[l][kv.first] = upload_sell(ar, kv.second, !f32, f32);
-  }
   // level vectors of coarse levels; the coarsest ones contiguous for the coupled LU
   int64_t ctot = 0;
   for (int i = 0; i < g.nf; ++i) ctot += g.lv[g.L - 1][i].n;
-  if (g.L > 1 || mono) {
+  g.cb = g.cx = nullptr;
+  if (g.L > 1 || g.mono) {
     g.cb = ar.zeros<T>(ctot);
     g.cx = ar.zeros<T>(ctot);
   }
@@ -246,15 +264,12 @@ static void upload_group(Arena &ar, DGroup<T> &g, const HGroup &h, const mfs_par
       g.lv[l][i].bv = ar.zeros<T>(g.lv[l][i].n);
       g.lv[l][i].xv = ar.zeros<T>(g.lv[l][i].n);
     }
-    if (g.L > 1 || mono) {
+    if (g.L > 1 || g.mono) {
       g.lv[g.L - 1][i].bv = g.cb + o;
       g.lv[g.L - 1][i].xv = g.cx + o;
     }
     o += g.lv[g.L - 1][i].n;
   }
-  g.cf.resize(g.nf);
-  for (int i = 0; i < g.nf; ++i) g.cf[i] = upload_lu(ar, h.coarse_field[i]);
-  if (mono) g.cc = upload_lu(ar, h.coarse_coupled);
 }
 
 template <typename T> struct Precond {
@@ -265,6 +280,16 @@ template <typename T> struct Precond {
   std::map<std::pair<int, int>, dev::Sell> cross;
   std::vector<T *> dtinv, sr2, st;
   cudaStream_t s = nullptr;
+
+  // (re)allocate every work vector in `ar` (setup, and each clone)
+  void alloc_work(Arena &ar) {
+    if (g0.L) alloc_group_work(ar, g0);
+    if (g1.L) alloc_group_work(ar, g1);
+    st.clear();
+    sr2.clear();
+    for (int j : G1) st.push_back(ar.zeros<T>(fsize[j]));
+    for (int k : G2) sr2.push_back(ar.zeros<T>(fsize[k]));
+  }
 
   // single-field polynomial smoother S^l_i; zero: x enters as 0
   void smooth(FL<T> &f, const T *rhs, T *x, bool zero) {
@@ -542,6 +567,15 @@ struct IterGraph {
   }
 };
 
+// Host copy of the hierarchy (for the export calls), shared by clones.
+struct HostSide {
+  HGroup hg0, hg1;
+  std::vector<std::vector<double>> dtilde;
+  BlockMap schur_off;
+  std::vector<HBsr> schur_diag;
+  std::vector<int> G1, G2;
+};
+
 }  // namespace mfs
 
 using namespace mfs;
@@ -557,11 +591,9 @@ struct mfs_handle {
   std::vector<dev::RowMerged> rows64;  // per row field, when its blocks share one pattern
   std::unique_ptr<Precond<double>> p64;
   std::unique_ptr<Precond<float>> p32;
-  HGroup hg0, hg1;
-  std::vector<std::vector<double>> dtilde;
-  BlockMap schur_off;
-  std::vector<HBsr> schur_diag;
-  std::vector<int> G1, G2;
+  std::shared_ptr<HostSide> host = std::make_shared<HostSide>();
+  std::shared_ptr<Arena> mat = std::make_shared<Arena>();  // matrices, shared by clones
+  int device = 0;
   bool host_only = false;
   // solve workspace
   int m = 0, nblk = 1;
@@ -635,10 +667,10 @@ double dot_host(mfs_handle *h, const double *x, const double *y) {
 
 // Capture body() once per Krylov index j into a CUDA graph and replay it:
 // one launch per GMRES iteration instead of one per kernel.
-template <typename F> void run_graph(mfs_handle *h, int j, F &&body) {
+template <typename F> void run_graph(mfs_handle *h, int j, F &&body, bool prof) {
   IterGraph &g = h->graphs[j];
   if (!g.exec) {
-    if (h->prof) {
+    if (prof) {
       h->prof->cap_events = &g.events;
       h->prof->cap_recs = &g.recs;
     }
@@ -649,21 +681,21 @@ template <typename F> void run_graph(mfs_handle *h, int j, F &&body) {
     } catch (...) {
       cudaStreamEndCapture(h->s, &graph);
       if (graph) cudaGraphDestroy(graph);
-      if (h->prof) h->prof->cap_events = nullptr, h->prof->cap_recs = nullptr;
+      if (prof) h->prof->cap_events = nullptr, h->prof->cap_recs = nullptr;
       g.release();
       throw;
     }
-    if (h->prof) h->prof->cap_events = nullptr, h->prof->cap_recs = nullptr;
+    if (prof) h->prof->cap_events = nullptr, h->prof->cap_recs = nullptr;
     MFS_CUDA(cudaStreamEndCapture(h->s, &graph));
     const cudaError_t e = cudaGraphInstantiate(&g.exec, graph, 0);
     cudaGraphDestroy(graph);
     MFS_CUDA(e);
   }
   MFS_CUDA(cudaGraphLaunch(g.exec, h->s));
-  if (h->prof) h->prof->pending.push_back(&g.recs);
+  if (prof) h->prof->pending.push_back(&g.recs);
 }
 
-int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info) {
+int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info, bool prof) {
   const int64_t n = h->n;
   const int m = h->m;
   cudaStream_t s = h->s;
@@ -708,10 +740,10 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
         dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + 128, s);
         MFS_CUDA(cudaMemcpyAsync(hp, h->hdev, 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
       };
-      if (h->use_graphs) run_graph(h, j, body);
+      if (h->use_graphs) run_graph(h, j, body, prof);
       else body();
       MFS_CUDA(cudaStreamSynchronize(s));
-      if (h->prof) h->prof->collect();
+      if (prof) h->prof->collect();
       const double nw0 = std::sqrt(hp[j + 1]);
       const double hn = std::sqrt(hp[128]);
       if (!std::isfinite(hn) || !std::isfinite(nw0)) return MFS_ERR_BREAKDOWN;
@@ -846,35 +878,35 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
     for (auto &kv : blocks)
       if (kv.first.first == kv.first.second) diag.push_back(kv.second);
       else off[kv.first] = kv.second;
-    build_group(h->hg0, diag, info, p.max_levels, p.coarse_max, p.seed, p.precond == MFS_AMG_BGS, &off);
+    build_group(h->host->hg0, diag, info, p.max_levels, p.coarse_max, p.seed, p.precond == MFS_AMG_BGS, &off);
     return;
   }
-  h->G1.clear();
-  h->G2.clear();
+  h->host->G1.clear();
+  h->host->G2.clear();
   bool any = false;
   for (int i = 0; i < h->nf; ++i) any |= p.simple_group[i] != 0;
   for (int i = 0; i < h->nf; ++i) {
     const bool schur = any ? p.simple_group[i] != 0 : i == h->nf - 1;
-    (schur ? h->G2 : h->G1).push_back(i);
+    (schur ? h->host->G2 : h->host->G1).push_back(i);
   }
-  if (h->G1.empty() || h->G2.empty()) throw SetupError(MFS_ERR_INVALID, "SIMPLE needs a non-empty predictor and Schur group");
+  if (h->host->G1.empty() || h->host->G2.empty()) throw SetupError(MFS_ERR_INVALID, "SIMPLE needs a non-empty predictor and Schur group");
   std::map<int, int> l2;
-  for (size_t a = 0; a < h->G2.size(); ++a) l2[h->G2[a]] = (int)a;
+  for (size_t a = 0; a < h->host->G2.size(); ++a) l2[h->host->G2[a]] = (int)a;
   std::vector<HBsr> diag1;
   std::vector<FieldInfo> info1;
-  for (int j : h->G1) {
+  for (int j : h->host->G1) {
     diag1.push_back(blocks.at({j, j}));
     info1.push_back(info[j]);
   }
-  build_group(h->hg0, diag1, info1, p.max_levels, p.coarse_max, p.seed, false, nullptr);
+  build_group(h->host->hg0, diag1, info1, p.max_levels, p.coarse_max, p.seed, false, nullptr);
   // A~_11: SIMPLEC sums of absolute entries over the merged predictor rows, or the diagonal
-  h->dtilde.clear();
-  for (int j : h->G1) {
+  h->host->dtilde.clear();
+  for (int j : h->host->G1) {
     std::vector<double> d(h->fsize[j], 0.0);
     if (p.simple_approx == MFS_DIAG) {
       d = bsr_point_diagonal(blocks.at({j, j}));
     } else {
-      for (int l : h->G1) {
+      for (int l : h->host->G1) {
         auto it = blocks.find({j, l});
         if (it == blocks.end()) continue;
         std::vector<double> sr = bsr_abs_row_sums(it->second);
@@ -883,14 +915,14 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
     }
     for (double v : d)
       if (v == 0.0) throw SetupError(MFS_ERR_SINGULAR, "zero entry in the SIMPLE diagonal approximation");
-    h->dtilde.push_back(d);
+    h->host->dtilde.push_back(d);
   }
   // S~_kl = A_kl - sum_j A_kj diag(1/d~_j) A_jl
   std::vector<FieldInfo> sinfo;
-  h->schur_off.clear();
-  h->schur_diag.clear();
-  for (int k : h->G2)
-    for (int l : h->G2) {
+  h->host->schur_off.clear();
+  h->host->schur_diag.clear();
+  for (int k : h->host->G2)
+    for (int l : h->host->G2) {
       HBsr M;
       bool have = false;
       auto it = blocks.find({k, l});
@@ -898,14 +930,14 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
         M = it->second;
         have = true;
       }
-      for (size_t jj = 0; jj < h->G1.size(); ++jj) {
-        const int j = h->G1[jj];
+      for (size_t jj = 0; jj < h->host->G1.size(); ++jj) {
+        const int j = h->host->G1[jj];
         auto a = blocks.find({k, j});
         auto c = blocks.find({j, l});
         if (a == blocks.end() || c == blocks.end()) continue;
         HBsr Cs = c->second;
-        std::vector<double> inv(h->dtilde[jj].size());
-        for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / h->dtilde[jj][r];
+        std::vector<double> inv(h->host->dtilde[jj].size());
+        for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / h->host->dtilde[jj][r];
         bsr_scale_rows(Cs, inv);
         HBsr Tm = bsr_spgemm(a->second, Cs);
         if (have) {
@@ -917,22 +949,25 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
       }
       if (!have) continue;
       if (k == l) {
-        h->schur_diag.push_back(M);
+        h->host->schur_diag.push_back(M);
         FieldInfo fi = info[k];
         fi.ns = 0;
         sinfo.push_back(fi);
       } else {
-        h->schur_off[{l2[k], l2[l]}] = M;
+        h->host->schur_off[{l2[k], l2[l]}] = M;
       }
     }
-  if (h->schur_diag.size() != h->G2.size()) throw SetupError(MFS_ERR_INVALID, "missing Schur diagonal block");
-  build_group(h->hg1, h->schur_diag, sinfo, p.max_levels, p.coarse_max, p.seed, false, nullptr);
+  if (h->host->schur_diag.size() != h->host->G2.size()) throw SetupError(MFS_ERR_INVALID, "missing Schur diagonal block");
+  build_group(h->host->hg1, h->host->schur_diag, sinfo, p.max_levels, p.coarse_max, p.seed, false, nullptr);
 }
 
-// Device half of the setup: upload the host hierarchy in precision T.
+// Device half of the setup: upload the host hierarchy in precision T
+// (matrices into the shared arena `mat`), then the work vectors into h->ar.
 template <typename T>
-void upload_precond(mfs_handle *h, Precond<T> &P, const std::map<std::pair<int, int>, HBsr> &blocks, bool f32) {
+void upload_precond(mfs_handle *h, Arena &mat, Precond<T> &P, const std::map<std::pair<int, int>, HBsr> &blocks,
+                    bool f32) {
   const mfs_params &p = h->prm;
+  const HostSide &hs = *h->host;
   P.kind = p.precond;
   P.nf = h->nf;
   P.order = p.bgs_order;
@@ -947,35 +982,54 @@ void upload_precond(mfs_handle *h, Precond<T> &P, const std::map<std::pair<int, 
     for (int i = 0; i < h->nf; ++i) d0.push_back(fine_sell(i, i));
     for (auto &kv : blocks)
       if (kv.first.first != kv.first.second) o0[kv.first] = fine_sell(kv.first.first, kv.first.second);
-    upload_group(h->ar, P.g0, h->hg0, p, d0, o0, p.precond == MFS_AMG_BGS);
-    return;
+    upload_group(mat, P.g0, hs.hg0, p, d0, o0, p.precond == MFS_AMG_BGS);
+  } else {
+    P.G1 = hs.G1;
+    P.G2 = hs.G2;
+    std::map<int, int> l1, l2;
+    for (size_t a = 0; a < hs.G1.size(); ++a) l1[hs.G1[a]] = (int)a;
+    for (size_t a = 0; a < hs.G2.size(); ++a) l2[hs.G2[a]] = (int)a;
+    std::vector<dev::Sell> d0;
+    std::map<std::pair<int, int>, dev::Sell> o0;
+    for (int j : hs.G1) d0.push_back(fine_sell(j, j));
+    for (auto &kv : blocks) {
+      const int i = kv.first.first, j = kv.first.second;
+      if (i != j && l1.count(i) && l1.count(j)) o0[{l1[i], l1[j]}] = fine_sell(i, j);
+      if ((l1.count(i) && l2.count(j)) || (l2.count(i) && l1.count(j))) P.cross[kv.first] = fine_sell(i, j);
+    }
+    upload_group(mat, P.g0, hs.hg0, p, d0, o0, false);
+    std::vector<dev::Sell> sd0;
+    std::map<std::pair<int, int>, dev::Sell> so0;
+    for (auto &M : hs.schur_diag) sd0.push_back(upload_sell(mat, M, !f32, f32));
+    for (auto &kv : hs.schur_off) so0[kv.first] = upload_sell(mat, kv.second, !f32, f32);
+    upload_group(mat, P.g1, hs.hg1, p, sd0, so0, false);
+    for (size_t jj = 0; jj < hs.G1.size(); ++jj) {
+      std::vector<double> inv(hs.dtilde[jj].size());
+      for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / hs.dtilde[jj][r];
+      P.dtinv.push_back(upload_as<T>(mat, inv));
+    }
   }
-  P.G1 = h->G1;
-  P.G2 = h->G2;
-  std::map<int, int> l1, l2;
-  for (size_t a = 0; a < h->G1.size(); ++a) l1[h->G1[a]] = (int)a;
-  for (size_t a = 0; a < h->G2.size(); ++a) l2[h->G2[a]] = (int)a;
-  std::vector<dev::Sell> d0;
-  std::map<std::pair<int, int>, dev::Sell> o0;
-  for (int j : h->G1) d0.push_back(fine_sell(j, j));
-  for (auto &kv : blocks) {
-    const int i = kv.first.first, j = kv.first.second;
-    if (i != j && l1.count(i) && l1.count(j)) o0[{l1[i], l1[j]}] = fine_sell(i, j);
-    if ((l1.count(i) && l2.count(j)) || (l2.count(i) && l1.count(j))) P.cross[kv.first] = fine_sell(i, j);
+  P.alloc_work(h->ar);
+}
+
+// GMRES workspace of a handle.
+void alloc_solver_work(mfs_handle *h) {
+  h->m = h->prm.restart;
+  h->graphs.assign(h->m, IterGraph());
+  h->nblk = dev::mdot_blocks(h->n);
+  h->V = h->ar.zeros<double>((int64_t)(h->m + 1) * h->n);
+  h->Z = h->ar.zeros<double>((int64_t)h->m * h->n);
+  h->rd = h->ar.zeros<double>(h->n);
+  h->xd = h->ar.zeros<double>(h->n);
+  h->bd = h->ar.zeros<double>(h->n);
+  h->partial = h->ar.zeros<double>((int64_t)64 * h->nblk);
+  h->hdev = h->ar.zeros<double>(256);
+  h->ydev = h->ar.zeros<double>(64);
+  if (h->prm.precision == MFS_FP32P) {
+    h->in32 = h->ar.zeros<float>(h->n);
+    h->out32 = h->ar.zeros<float>(h->n);
   }
-  upload_group(h->ar, P.g0, h->hg0, p, d0, o0, false);
-  std::vector<dev::Sell> sd0;
-  std::map<std::pair<int, int>, dev::Sell> so0;
-  for (auto &M : h->schur_diag) sd0.push_back(upload_sell(h->ar, M, !f32, f32));
-  for (auto &kv : h->schur_off) so0[kv.first] = upload_sell(h->ar, kv.second, !f32, f32);
-  upload_group(h->ar, P.g1, h->hg1, p, sd0, so0, false);
-  for (size_t jj = 0; jj < h->G1.size(); ++jj) {
-    std::vector<double> inv(h->dtilde[jj].size());
-    for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / h->dtilde[jj][r];
-    P.dtinv.push_back(upload_as<T>(h->ar, inv));
-    P.st.push_back(h->ar.zeros<T>(h->fsize[h->G1[jj]]));
-  }
-  for (int k : h->G2) P.sr2.push_back(h->ar.zeros<T>(h->fsize[k]));
+  MFS_CUDA(cudaMallocHost(&h->hpin, 256 * sizeof(double)));
 }
 
 int fail(int code, const std::string &msg) {
@@ -1084,29 +1138,18 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       h->own_stream = true;
     }
     const bool f32 = p.precision == MFS_FP32P;
-    for (auto &kv : hb) h->A64[kv.first] = upload_sell(h->ar, kv.second, true, f32);
-    h->rows64 = merge_rows(h->ar, hb, h->nf, h->foff);
+    MFS_CUDA(cudaGetDevice(&h->device));
+    Arena &mat = *h->mat;
+    for (auto &kv : hb) h->A64[kv.first] = upload_sell(mat, kv.second, true, f32);
+    h->rows64 = merge_rows(mat, hb, h->nf, h->foff);
     if (f32) {
       h->p32.reset(new Precond<float>());
-      upload_precond<float>(h.get(), *h->p32, hb, true);
-      h->in32 = h->ar.zeros<float>(h->n);
-      h->out32 = h->ar.zeros<float>(h->n);
+      upload_precond<float>(h.get(), mat, *h->p32, hb, true);
     } else {
       h->p64.reset(new Precond<double>());
-      upload_precond<double>(h.get(), *h->p64, hb, false);
+      upload_precond<double>(h.get(), mat, *h->p64, hb, false);
     }
-    h->m = p.restart;
-    h->graphs.resize(h->m);
-    h->nblk = dev::mdot_blocks(h->n);
-    h->V = h->ar.zeros<double>((int64_t)(h->m + 1) * h->n);
-    h->Z = h->ar.zeros<double>((int64_t)h->m * h->n);
-    h->rd = h->ar.zeros<double>(h->n);
-    h->xd = h->ar.zeros<double>(h->n);
-    h->bd = h->ar.zeros<double>(h->n);
-    h->partial = h->ar.zeros<double>((int64_t)64 * h->nblk);
-    h->hdev = h->ar.zeros<double>(256);
-    h->ydev = h->ar.zeros<double>(64);
-    MFS_CUDA(cudaMallocHost(&h->hpin, 256 * sizeof(double)));
+    alloc_solver_work(h.get());
     if (p.profile) h->prof.reset(new EventProf());
     MFS_CUDA(cudaDeviceSynchronize());
   } catch (const SetupError &e) {
@@ -1127,12 +1170,12 @@ int64_t mfs_ndofs(const mfs_handle *h) { return h ? h->n : 0; }
 
 int mfs_num_levels(const mfs_handle *h, int group) {
   if (!h) return 0;
-  if (group == 0) return h->hg0.nlevels();
-  if (group == 1) return h->hg1.nlevels();
+  if (group == 0) return h->host->hg0.nlevels();
+  if (group == 1) return h->host->hg1.nlevels();
   return 0;
 }
 
-int mfs_solve(mfs_handle *h, const double *rhs, double *x, double tol, mfs_info *info) {
+static int solve_impl(mfs_handle *h, const double *rhs, double *x, double tol, mfs_info *info, bool hook) {
   if (!h || !rhs || !x || !(tol > 0.0)) return fail(MFS_ERR_INVALID, "bad solve arguments");
   if (h->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
   mfs_info local{};
@@ -1152,15 +1195,18 @@ int mfs_solve(mfs_handle *h, const double *rhs, double *x, double tol, mfs_info 
       MFS_CUDA(cudaMemcpyAsync(h->xd, x, h->n * sizeof(double), cudaMemcpyHostToDevice, h->s));
       xx = h->xd;
     }
-    if (h->prof) dev::set_launch_hook(h->prof.get());
+    const bool prof = hook && h->prof;
+    if (prof) dev::set_launch_hook(h->prof.get());
     try {
-      rc = fgmres(h, b, xx, tol, info);
+      rc = fgmres(h, b, xx, tol, info, prof);
     } catch (...) {
-      dev::set_launch_hook(nullptr);
+      if (prof) dev::set_launch_hook(nullptr);
       throw;
     }
-    dev::set_launch_hook(nullptr);
-    if (h->prof) h->prof->collect();
+    if (prof) {
+      dev::set_launch_hook(nullptr);
+      h->prof->collect();
+    }
     if (!dx) MFS_CUDA(cudaMemcpyAsync(x, h->xd, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     MFS_CUDA(cudaStreamSynchronize(h->s));
     MFS_CUDA(cudaGetLastError());
@@ -1169,9 +1215,101 @@ int mfs_solve(mfs_handle *h, const double *rhs, double *x, double tol, mfs_info 
   }
   info->solve_ms = now_ms() - t0;
   info->setup_ms = h->setup_ms;
-  info->levels[0] = h->hg0.nlevels();
-  info->levels[1] = h->hg1.nlevels();
+  info->levels[0] = h->host->hg0.nlevels();
+  info->levels[1] = h->host->hg1.nlevels();
   if (rc == MFS_ERR_NOT_CONVERGED) g_last_error = "GMRES reached max_iters";
+  return rc;
+}
+
+int mfs_solve(mfs_handle *h, const double *rhs, double *x, double tol, mfs_info *info) {
+  return solve_impl(h, rhs, x, tol, info, true);
+}
+
+int mfs_clone(const mfs_handle *src, void *stream, mfs_handle **out) {
+  if (!src || !out) return fail(MFS_ERR_INVALID, "bad clone arguments");
+  *out = nullptr;
+  if (src->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
+  std::unique_ptr<mfs_handle> h(new mfs_handle());
+  try {
+    MFS_CUDA(cudaSetDevice(src->device));
+    h->prm = src->prm;
+    h->prm.profile = 0;
+    h->prm.cuda_stream = stream;
+    h->nf = src->nf;
+    h->fsize = src->fsize;
+    h->foff = src->foff;
+    h->n = src->n;
+    h->device = src->device;
+    h->host = src->host;
+    h->mat = src->mat;
+    h->A64 = src->A64;
+    h->rows64 = src->rows64;
+    h->setup_ms = src->setup_ms;
+    h->use_graphs = src->use_graphs;
+    h->s = (cudaStream_t)stream;
+    if (!h->s) {
+      MFS_CUDA(cudaStreamCreate(&h->s));
+      h->own_stream = true;
+    }
+    if (src->p32) {
+      h->p32.reset(new Precond<float>(*src->p32));
+      h->p32->s = h->s;
+      h->p32->alloc_work(h->ar);
+    } else {
+      h->p64.reset(new Precond<double>(*src->p64));
+      h->p64->s = h->s;
+      h->p64->alloc_work(h->ar);
+    }
+    alloc_solver_work(h.get());
+    MFS_CUDA(cudaDeviceSynchronize());
+  } catch (const CudaError &e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(MFS_ERR_OOM, "host allocation failed");
+  }
+  *out = h.release();
+  return MFS_OK;
+}
+
+int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, double *const *x, double tol,
+                    mfs_info *infos, int *status, int nthreads) {
+  if (!hs || nsys < 0 || !rhs || !x || !(tol > 0.0)) return fail(MFS_ERR_INVALID, "bad batch arguments");
+  for (int k = 0; k < nsys; ++k) {
+    if (!hs[k] || !rhs[k] || !x[k]) return fail(MFS_ERR_INVALID, "NULL handle or vector in batch");
+    for (int q = 0; q < k; ++q)
+      if (hs[q] == hs[k]) return fail(MFS_ERR_INVALID, "a handle appears twice in one batch");
+  }
+  if (nsys == 0) return MFS_OK;
+  int nt = nthreads > 0 ? nthreads : 16;
+  if (nt > nsys) nt = nsys;
+  std::atomic<int> next(0);
+  std::vector<int> st(nsys, MFS_OK);
+  std::vector<mfs_info> inf(nsys);
+  std::vector<std::string> err(nsys);
+  auto worker = [&]() {
+    int dev_set = -1;
+    for (int k = next++; k < nsys; k = next++) {
+      if (hs[k]->device != dev_set) {
+        cudaSetDevice(hs[k]->device);
+        dev_set = hs[k]->device;
+      }
+      st[k] = solve_impl(hs[k], rhs[k], x[k], tol, &inf[k], false);
+      if (st[k] != MFS_OK) err[k] = g_last_error;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int t = 1; t < nt; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &t : pool) t.join();
+  int rc = MFS_OK;
+  for (int k = 0; k < nsys; ++k) {
+    if (infos) infos[k] = inf[k];
+    if (status) status[k] = st[k];
+    if (st[k] != MFS_OK && rc == MFS_OK) {
+      rc = st[k];
+      g_last_error = "system " + std::to_string(k) + ": " + err[k];
+    }
+  }
   return rc;
 }
 
@@ -1220,7 +1358,7 @@ int mfs_matvec(mfs_handle *h, const double *x, double *y) {
 }
 
 static const HBsr *export_matrix(const mfs_handle *h, int what, int group, int level, int i, int j) {
-  const HGroup &g = group == 0 ? h->hg0 : h->hg1;
+  const HGroup &g = group == 0 ? h->host->hg0 : h->host->hg1;
   if (group < 0 || group > 1 || level < 0 || level >= g.nlevels() || i < 0 || i >= g.nf) return nullptr;
   if (what == 0) {
     if (j < 0 || j >= g.nf) return nullptr;
@@ -1230,8 +1368,8 @@ static const HBsr *export_matrix(const mfs_handle *h, int what, int group, int l
       if (it != g.off[level].end()) return &it->second;
     }
     if (group == 1 && level == 0) {
-      auto it = h->schur_off.find({i, j});
-      if (it != h->schur_off.end()) return &it->second;
+      auto it = h->host->schur_off.find({i, j});
+      if (it != h->host->schur_off.end()) return &it->second;
     }
     return nullptr;
   }
@@ -1270,7 +1408,7 @@ int mfs_export_csr(const mfs_handle *h, int what, int group, int level, int i, i
 int mfs_export_array(const mfs_handle *h, int what, int group, int level, int i, void *buf, int64_t cap,
                      int64_t *count) {
   if (!h || !count) return fail(MFS_ERR_INVALID, "bad export arguments");
-  const HGroup &g = group == 0 ? h->hg0 : h->hg1;
+  const HGroup &g = group == 0 ? h->host->hg0 : h->host->hg1;
   if (group < 0 || group > 1 || level < 0 || level >= g.nlevels() || i < 0 || i >= g.nf)
     return fail(MFS_ERR_INVALID, "no such level/field");
   const HLevelField &f = g.lv[level][i];
@@ -1281,9 +1419,9 @@ int mfs_export_array(const mfs_handle *h, int what, int group, int level, int i,
     *count = 1;
     if (buf && cap >= 1) *(double *)buf = f.lam;
   } else if (what == 2) {
-    if (group != 0 || i >= (int)h->dtilde.size()) return fail(MFS_ERR_INVALID, "no SIMPLE diagonal");
-    *count = (int64_t)h->dtilde[i].size();
-    if (buf && cap >= *count) std::memcpy(buf, h->dtilde[i].data(), h->dtilde[i].size() * sizeof(double));
+    if (group != 0 || i >= (int)h->host->dtilde.size()) return fail(MFS_ERR_INVALID, "no SIMPLE diagonal");
+    *count = (int64_t)h->host->dtilde[i].size();
+    if (buf && cap >= *count) std::memcpy(buf, h->host->dtilde[i].data(), h->host->dtilde[i].size() * sizeof(double));
   } else {
     return fail(MFS_ERR_INVALID, "bad export kind");
   }

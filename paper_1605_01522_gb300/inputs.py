@@ -360,3 +360,19 @@ def batch_sizes_log_uniform(nsys=256, lo=12, hi=48, seed=3):
     """Per-system mesh edge n_e = round(exp(U(ln lo, ln hi)))."""
     rng = np.random.default_rng(seed)
     return np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=nsys))).astype(int)
+
+
+def system_rhs(system, seed):
+    """A fresh seeded N(0,1) right-hand side for an existing system (zero on
+    its Dirichlet nodes)."""
+    return _seeded_rhs(system.fields, seed, system.fields[0].dirichlet_nodes)
+
+
+def batch_workload(nsys=256, lo=12, hi=48, seed=3, nfields=2):
+    """Batch of independent 3D coupled boxes: mesh edge n_e log-uniform in
+    [lo, hi] per system (the matrix depends on n_e only), right-hand side
+    seeded with seed*1000 + k.  Returns (sizes, {n_e: BlockSystem}, [rhs_k])."""
+    sizes = batch_sizes_log_uniform(nsys, lo, hi, seed)
+    mats = {int(ne): coupled_box_3d(ne=int(ne), nfields=nfields, seed=seed) for ne in sorted(set(sizes.tolist()))}
+    rhs = [system_rhs(mats[int(ne)], seed * 1000 + k) for k, ne in enumerate(sizes)]
+    return sizes, mats, rhs

@@ -27,7 +27,7 @@ PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
-EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_ndofs",
+EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_solve_batch", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_ndofs",
            "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
@@ -107,6 +107,11 @@ def load(build_if_missing: bool = True):
     lib.mfs_setup.restype = C.c_int
     lib.mfs_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_double, C.POINTER(Info)]
     lib.mfs_solve.restype = C.c_int
+    lib.mfs_clone.argtypes = [H, C.c_void_p, C.POINTER(H)]
+    lib.mfs_clone.restype = C.c_int
+    lib.mfs_solve_batch.argtypes = [C.POINTER(H), C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p), C.c_double,
+                                    C.POINTER(Info), C.POINTER(C.c_int), C.c_int]
+    lib.mfs_solve_batch.restype = C.c_int
     lib.mfs_apply.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.mfs_apply.restype = C.c_int
     lib.mfs_matvec.argtypes = [H, C.c_void_p, C.c_void_p]
@@ -199,6 +204,24 @@ def _ptr(a):
     return C.c_void_p(a.ctypes.data)
 
 
+def solve_batch(solvers, rhs, xs=None, tol=1e-8, nthreads=0, check=True):
+    """Solve independent systems concurrently (mfs_solve_batch): solvers[k]
+    (distinct handles) with rhs[k]; returns (xs, infos, status)."""
+    lib = load()
+    n = len(solvers)
+    if xs is None:
+        xs = [np.zeros(s.n) if isinstance(b, np.ndarray) else b.new_zeros(s.n) for s, b in zip(solvers, rhs)]
+    hs = (C.c_void_p * n)(*[s.h.value if isinstance(s.h, C.c_void_p) else s.h for s in solvers])
+    rp = (C.c_void_p * n)(*[_ptr(b).value for b in rhs])
+    xp = (C.c_void_p * n)(*[_ptr(x).value for x in xs])
+    infos = (Info * n)()
+    status = (C.c_int * n)()
+    rc = lib.mfs_solve_batch(hs, n, rp, xp, tol, infos, status, nthreads)
+    if check and rc not in (OK, ERR_NOT_CONVERGED):
+        raise MfsError(rc, "mfs_solve_batch")
+    return xs, [i.as_dict() for i in infos], list(status)
+
+
 class Solver:
     """Owns one mfs_handle built from an inputs.BlockSystem."""
 
@@ -264,6 +287,16 @@ class Solver:
         if rc != OK:
             raise MfsError(rc, "mfs_dot")
         return out.value
+
+    def clone(self, stream=None):
+        """A Solver sharing this one's device hierarchy, with its own workspace and stream."""
+        h = C.c_void_p()
+        rc = self.lib.mfs_clone(self.h, stream, C.byref(h))
+        if rc != OK:
+            raise MfsError(rc, "mfs_clone")
+        other = Solver.__new__(Solver)
+        other.lib, other.h, other.params, other.n, other.nfields = self.lib, h, self.params, self.n, self.nfields
+        return other
 
     def num_levels(self, group=0):
         return self.lib.mfs_num_levels(self.h, group)
