@@ -441,6 +441,47 @@ def run_batch(args, rank, world):
         sv.close()
 
 
+def run_serve(args, rank, world):
+    """Serving workload: Poisson arrivals of solve requests, each a 2- or
+    3-field 3D box with n_e from {16,24,32,48,64}, 30 % reusing a resident
+    hierarchy with a new right-hand side, admission by an HBM budget,
+    concurrent solves.  Reports p50/p99 latency and solves/s."""
+    import torch
+    from paper_1605_01522_gb300 import inputs, serving
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    sizes = [int(v) for v in args.serve_sizes.split(",")]
+    pool = {(ne, nf): inputs.coupled_box_3d(ne=ne, nfields=nf, seed=4) for ne in sizes for nf in (2, 3)}
+    rhs = {key: [inputs.system_rhs(sy, 4000 + 10 * i + k) for k in range(3)] for i, (key, sy) in enumerate(pool.items())}
+    rng = np.random.default_rng(4)
+    keys = list(pool)
+    gaps = rng.exponential(1.0 / args.rate, size=args.requests)
+    picks = rng.integers(len(keys), size=args.requests)
+    reuse = rng.random(args.requests) < 0.3
+    srv = serving.Server(hbm_budget=int(args.hbm_gb * (1 << 30)), workers=args.threads, precond=args.precond,
+                         precision=args.precision, **SOLVER_KW)
+    t0 = time.perf_counter()
+    t = t0
+    for i in range(args.requests):
+        t += gaps[i]
+        delay = t - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        key = keys[picks[i]]
+        srv.submit(key, pool[key], rhs[key][i % 3], bool(reuse[i]))
+    srv.drain()
+    st = srv.stats()
+    srv.close()
+    line = {"metric": METRIC, "value": st["solves_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.requests,
+            "warmup": 0, "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "fp32p" else "f64", "data": "synthetic",
+            "config": {"workload": f"serving: {args.requests} Poisson requests at {args.rate}/s, 2- or 3-field 3D boxes, "
+                                   f"n_e in {sizes}, 30 % reuse a resident hierarchy, HBM budget {args.hbm_gb} GB, "
+                                   f"{args.threads} workers, {args.precond.upper()} {args.precision.upper()}, rtol 1e-8",
+                       **st}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global NE
     ap = argparse.ArgumentParser()
@@ -454,10 +495,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--ne", type=int, default=NE, help="mesh edge (64 = the benchmark workload)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "batch"],
+    ap.add_argument("--workload", default="box", choices=["box", "batch", "serve"],
                     help="box: the 64^3 three-field system (headline); batch: 256 independent systems")
     ap.add_argument("--nsys", type=int, default=256)
     ap.add_argument("--threads", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--hbm-gb", type=float, default=150.0)
+    ap.add_argument("--serve-sizes", default="16,24,32,48,64")
     args = ap.parse_args()
     NE = args.ne
     rank = int(os.environ.get("RANK", 0))
@@ -466,6 +511,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "batch":
         run_batch(args, rank, world)
+    elif args.workload == "serve":
+        run_serve(args, rank, world)
     else:
         run_mfs(args, rank, world)
 

@@ -21,7 +21,8 @@
  * Each GMRES iteration (preconditioner, matvec, CGS2 Arnoldi, readback of
  * the Hessenberg column) is captured once per Krylov index into a CUDA graph
  * and replayed; a NULL params.cuda_stream makes the library create its own
- * stream (blocking with respect to the legacy default stream).
+ * (non-blocking) stream, which waits for the legacy default stream's earlier
+ * work at the start of every call.
  *
  * Conventions
  *   - All functions return MFS_OK (0) or a negative MFS_ERR_* code;
@@ -207,6 +208,10 @@ int mfs_dot_noalloc(const double *x, const double *y, int64_t n, double *out, vo
 
 /* Total scalar dofs n of the coupled system. */
 int64_t mfs_ndofs(const struct mfs_handle *h);
+
+/* Device bytes held by the handle: shared != 0 -> the hierarchy shared with
+ * its clones (matrices, transfers, LU factors); 0 -> its own workspace. */
+int64_t mfs_device_bytes(const struct mfs_handle *h, int shared);
 
 /* Export one hierarchy matrix as point CSR (float64) for inspection.
  * what: 0 = A block (i, j) of level, 1 = P of field i (level -> level+1),

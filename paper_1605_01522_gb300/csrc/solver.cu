@@ -49,11 +49,13 @@ void set_last_error(const char *msg) { g_last_error = msg; }
 
 struct Arena {
   std::vector<void *> ptrs;
+  int64_t bytes = 0;
   template <typename T> T *alloc(int64_t count) {
     if (count <= 0) return nullptr;
     void *p = nullptr;
     MFS_CUDA(cudaMalloc(&p, (size_t)count * sizeof(T)));
     ptrs.push_back(p);
+    bytes += count * (int64_t)sizeof(T);
     return (T *)p;
   }
   template <typename T> T *upload(const std::vector<T> &h) {
@@ -604,11 +606,13 @@ struct mfs_handle {
   double setup_ms = 0.0;
   std::unique_ptr<EventProf> prof;
   bool own_stream = false;
+  cudaEvent_t entry = nullptr;
   bool use_graphs = true;
   std::vector<IterGraph> graphs;  // per Krylov index j
   ~mfs_handle() {
     for (auto &g : graphs) g.release();
     if (hpin) cudaFreeHost(hpin);
+    if (entry) cudaEventDestroy(entry);
     if (own_stream && s) cudaStreamDestroy(s);
   }
 };
@@ -1133,8 +1137,10 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     }
     dev::init();
     if (!h->s) {
-      // the legacy default stream cannot be captured: use a blocking stream of our own
-      MFS_CUDA(cudaStreamCreate(&h->s));
+      // the legacy default stream cannot be captured: use a stream of our own,
+      // non-blocking so that legacy-stream work of other threads (another
+      // handle's setup) never joins a graph capture running on it
+      MFS_CUDA(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
       h->own_stream = true;
     }
     const bool f32 = p.precision == MFS_FP32P;
@@ -1151,7 +1157,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     }
     alloc_solver_work(h.get());
     if (p.profile) h->prof.reset(new EventProf());
-    MFS_CUDA(cudaDeviceSynchronize());
+    MFS_CUDA(cudaStreamSynchronize(0));  // uploads and memsets ran on the legacy stream
   } catch (const SetupError &e) {
     return fail(e.code, e.what());
   } catch (const CudaError &e) {
@@ -1167,6 +1173,11 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
 }
 
 int64_t mfs_ndofs(const mfs_handle *h) { return h ? h->n : 0; }
+
+int64_t mfs_device_bytes(const mfs_handle *h, int shared) {
+  if (!h) return 0;
+  return shared ? h->mat->bytes : h->ar.bytes;
+}
 
 int mfs_num_levels(const mfs_handle *h, int group) {
   if (!h) return 0;
@@ -1184,6 +1195,12 @@ static int solve_impl(mfs_handle *h, const double *rhs, double *x, double tol, m
   const double t0 = now_ms();
   int rc = MFS_OK;
   try {
+    if (h->own_stream) {
+      // the caller's vectors come from the legacy default stream: start after it
+      if (!h->entry) MFS_CUDA(cudaEventCreateWithFlags(&h->entry, cudaEventDisableTiming));
+      MFS_CUDA(cudaEventRecord(h->entry, 0));
+      MFS_CUDA(cudaStreamWaitEvent(h->s, h->entry, 0));
+    }
     const bool drhs = is_device_ptr(rhs), dx = is_device_ptr(x);
     const double *b = rhs;
     double *xx = x;
@@ -1248,7 +1265,7 @@ int mfs_clone(const mfs_handle *src, void *stream, mfs_handle **out) {
     h->use_graphs = src->use_graphs;
     h->s = (cudaStream_t)stream;
     if (!h->s) {
-      MFS_CUDA(cudaStreamCreate(&h->s));
+      MFS_CUDA(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking));
       h->own_stream = true;
     }
     if (src->p32) {
@@ -1261,7 +1278,7 @@ int mfs_clone(const mfs_handle *src, void *stream, mfs_handle **out) {
       h->p64->alloc_work(h->ar);
     }
     alloc_solver_work(h.get());
-    MFS_CUDA(cudaDeviceSynchronize());
+    MFS_CUDA(cudaStreamSynchronize(0));  // uploads and memsets ran on the legacy stream
   } catch (const CudaError &e) {
     return fail(e.code, e.what());
   } catch (const std::bad_alloc &) {
@@ -1316,6 +1333,11 @@ int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, d
 static int with_io(mfs_handle *h, const double *in, double *out, void (*fn)(mfs_handle *, const double *, double *)) {
   if (h->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
   try {
+    if (h->own_stream) {
+      if (!h->entry) MFS_CUDA(cudaEventCreateWithFlags(&h->entry, cudaEventDisableTiming));
+      MFS_CUDA(cudaEventRecord(h->entry, 0));
+      MFS_CUDA(cudaStreamWaitEvent(h->s, h->entry, 0));
+    }
     const bool din = is_device_ptr(in), dout = is_device_ptr(out);
     const double *a = in;
     double *b = out;
@@ -1339,6 +1361,11 @@ int mfs_dot(mfs_handle *h, const double *x, const double *y, double *out) {
   if (h->host_only) return fail(MFS_ERR_INVALID, "handle was built with setup_only");
   if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(MFS_ERR_INVALID, "mfs_dot needs device vectors");
   try {
+    if (h->own_stream) {
+      if (!h->entry) MFS_CUDA(cudaEventCreateWithFlags(&h->entry, cudaEventDisableTiming));
+      MFS_CUDA(cudaEventRecord(h->entry, 0));
+      MFS_CUDA(cudaStreamWaitEvent(h->s, h->entry, 0));
+    }
     *out = dot_host(h, x, y);
     MFS_CUDA(cudaGetLastError());
   } catch (const CudaError &e) {

@@ -27,7 +27,7 @@ PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
-EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_solve_batch", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_ndofs",
+EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_solve_batch", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_ndofs", "mfs_device_bytes",
            "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
@@ -120,6 +120,8 @@ def load(build_if_missing: bool = True):
     lib.mfs_dot.restype = C.c_int
     lib.mfs_dot_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_void_p]
     lib.mfs_dot_noalloc.restype = C.c_int
+    lib.mfs_device_bytes.argtypes = [H, C.c_int]
+    lib.mfs_device_bytes.restype = C.c_int64
     lib.mfs_ndofs.argtypes = [H]
     lib.mfs_ndofs.restype = C.c_int64
     lib.mfs_export_csr.argtypes = [H, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -297,6 +299,10 @@ class Solver:
         other = Solver.__new__(Solver)
         other.lib, other.h, other.params, other.n, other.nfields = self.lib, h, self.params, self.n, self.nfields
         return other
+
+    def device_bytes(self, shared=True):
+        """Device bytes of the shared hierarchy (shared=True) or of this handle's workspace."""
+        return int(self.lib.mfs_device_bytes(self.h, 1 if shared else 0))
 
     def num_levels(self, group=0):
         return self.lib.mfs_num_levels(self.h, group)

@@ -1,0 +1,206 @@
+"""Continuous-batching solve server over libmfs.
+
+Requests (a coupled block system plus a right-hand side) arrive at any time;
+a request is admitted when a worker is free and its device memory fits the
+HBM budget; admitted requests run concurrently, each on its own handle and
+CUDA stream, so their V-cycles and Krylov kernels overlap on the GPU while
+new requests keep being admitted as slots and memory free up.  A request may
+reuse a resident hierarchy of the same system (a clone: no setup, only a new
+workspace) or bring a new matrix (a full setup).  Resident hierarchies are
+evicted least-recently-used when the budget is short.  Every result is the
+one a solo solve of that request gives (the same kernels and reductions run
+on the request's own stream), which the serving test checks.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+
+import numpy as np
+
+from . import mfs
+
+BYTES_PER_DOF_ESTIMATE = 3200  # before a system's first setup (measured after it)
+
+
+class Request:
+    def __init__(self, rid, key, system, rhs, reuse):
+        self.rid, self.key, self.system, self.rhs, self.reuse = rid, key, system, rhs, reuse
+        self.t_arrive = time.perf_counter()
+        self.t_admit = self.t_start = self.t_setup = self.t_done = None
+        self.x = None
+        self.info = None
+        self.rc = None
+        self.error = None
+        self.reserved = 0
+        self.setup_done_here = False
+        self.event = threading.Event()
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.t_arrive
+
+
+class Server:
+    """hbm_budget: bytes of device memory the server may hold (resident
+    hierarchies + running requests); workers: requests in flight at once."""
+
+    def __init__(self, hbm_budget, workers=8, tol=1e-8, keep_resident=True, **solver_kw):
+        self.budget = int(hbm_budget)
+        self.tol = tol
+        self.kw = solver_kw
+        self.keep_resident = keep_resident
+        self.cv = threading.Condition()
+        self.pending = collections.deque()
+        self.resident = collections.OrderedDict()  # key -> [Solver, shared_bytes, own_bytes, users]
+        self.footprint = {}  # key -> (shared bytes, workspace bytes) measured
+        self.used = 0
+        self.peak_used = 0
+        self.running = 0
+        self.peak_running = 0
+        self.done = []
+        self.stop = False
+        self.next_id = 0
+        self.threads = [threading.Thread(target=self._work, daemon=True) for _ in range(workers)]
+        for t in self.threads:
+            t.start()
+
+    # ------------------------------------------------------------------ API
+    def submit(self, key, system, rhs, reuse=True):
+        with self.cv:
+            r = Request(self.next_id, key, system, rhs, reuse)
+            self.next_id += 1
+            self.pending.append(r)
+            self.cv.notify_all()
+        return r
+
+    def drain(self, timeout=None):
+        """Wait until every submitted request has finished."""
+        t0 = time.perf_counter()
+        with self.cv:
+            while self.pending or self.running:
+                left = None if timeout is None else timeout - (time.perf_counter() - t0)
+                if left is not None and left <= 0:
+                    raise TimeoutError("serving drain timed out")
+                self.cv.wait(left if left is not None else 1.0)
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        for t in self.threads:
+            t.join()
+        for entry in self.resident.values():
+            entry[0].close()
+        self.resident.clear()
+
+    def stats(self):
+        lat = np.array([r.latency for r in self.done if r.latency is not None])
+        solve = np.array([r.t_done - r.t_start for r in self.done if r.t_done])
+        setup = np.array([r.t_start - r.t_admit for r in self.done if r.t_done and r.setup_done_here])
+        t0 = min(r.t_arrive for r in self.done)
+        t1 = max(r.t_done for r in self.done)
+        ok = sum(1 for r in self.done if r.rc == mfs.OK)
+        return {"requests": len(self.done), "converged": ok,
+                "p50_latency_ms": float(np.percentile(lat, 50) * 1e3), "p99_latency_ms": float(np.percentile(lat, 99) * 1e3),
+                "p50_solve_ms": float(np.percentile(solve, 50) * 1e3), "p99_solve_ms": float(np.percentile(solve, 99) * 1e3),
+                "mean_setup_ms": float(setup.mean() * 1e3) if len(setup) else 0.0,
+                "solves_per_s": ok / (t1 - t0), "peak_hbm_bytes": self.peak_used, "peak_in_flight": self.peak_running,
+                "setups": int(sum(1 for r in self.done if r.setup_done_here))}
+
+    # ------------------------------------------------------------- internals
+    def _estimate(self, r):
+        shared, own = self.footprint.get(r.key, (None, None))
+        if shared is None:
+            n = r.system.ndofs
+            shared, own = BYTES_PER_DOF_ESTIMATE * n // 2, BYTES_PER_DOF_ESTIMATE * n // 2
+        if r.reuse and r.key in self.resident:
+            return own
+        return shared + own
+
+    def _evict_for(self, need):
+        """Drop idle resident hierarchies (LRU first) until `need` bytes fit."""
+        for key in list(self.resident.keys()):
+            if self.used + need <= self.budget:
+                return
+            sv, shared, own, users = self.resident[key]
+            if users:
+                continue
+            del self.resident[key]
+            self.used -= shared + own
+            sv.close()
+
+    def _take(self):
+        """Admit the oldest pending request that fits (called with the lock held)."""
+        if not self.pending:
+            return None
+        r = self.pending[0]
+        need = self._estimate(r)
+        if self.used + need > self.budget:
+            self._evict_for(need)
+        if self.used + need > self.budget:
+            if self.running == 0 and need > self.budget:
+                self.pending.popleft()
+                r.error = "request larger than the HBM budget"
+                r.rc = mfs.ERR_OOM
+                r.t_done = time.perf_counter()
+                self.done.append(r)
+                r.event.set()
+            return None
+        self.pending.popleft()
+        r.reserved = need
+        self.used += need
+        self.peak_used = max(self.peak_used, self.used)
+        self.running += 1
+        self.peak_running = max(self.peak_running, self.running)
+        r.t_admit = time.perf_counter()
+        if r.reuse and r.key in self.resident:
+            self.resident.move_to_end(r.key)
+            self.resident[r.key][3] += 1
+        return r
+
+    def _work(self):
+        while True:
+            with self.cv:
+                r = None
+                while not self.stop:
+                    r = self._take()
+                    if r is not None:
+                        break
+                    self.cv.wait(0.05)
+                if r is None:
+                    return
+                base = self.resident[r.key][0] if (r.reuse and r.key in self.resident) else None
+            sv, keep = None, False
+            try:
+                if base is not None:
+                    sv = base.clone()
+                else:
+                    sv = mfs.Solver(r.system, **self.kw)
+                    r.setup_done_here = True
+                r.t_start = time.perf_counter()
+                x = np.zeros(r.system.ndofs)
+                _, r.info, r.rc = sv.solve(r.rhs, x, tol=self.tol)
+                r.x = x
+            except mfs.MfsError as e:
+                r.rc, r.error = e.code, str(e)
+            r.t_done = time.perf_counter()
+            with self.cv:
+                self.used -= r.reserved
+                if sv is not None:
+                    shared, own = sv.device_bytes(True), sv.device_bytes(False)
+                    if r.setup_done_here:
+                        self.footprint[r.key] = (shared, own)
+                        if self.keep_resident and r.key not in self.resident and self.used + shared + own <= self.budget:
+                            self.resident[r.key] = [sv, shared, own, 0]
+                            self.used += shared + own
+                            keep = True
+                if base is not None and r.key in self.resident:
+                    self.resident[r.key][3] -= 1
+                self.running -= 1
+                self.done.append(r)
+                self.cv.notify_all()
+            if sv is not None and not keep:
+                sv.close()
+            r.event.set()
