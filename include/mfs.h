@@ -15,8 +15,11 @@
  *                Galerkin coarse blocks and block Gauss-Seidel level smoothing
  *                (Sec. 4.3).
  * Every solve-phase step runs in this library's CUDA kernels; there is no CPU
- * fallback.  The AMG setup (aggregation, prolongators, Galerkin products,
- * coarse factorisation) runs in this library's host code and is timed apart.
+ * fallback.  The AMG setup (strength graph, aggregation, tentative and
+ * smoothed prolongators, Galerkin products, power iteration) runs in this
+ * library's CUDA kernels too (the dense LU of the coarsest level, at most a
+ * few hundred unknowns, is factored on the host) and is timed apart; a
+ * host-only setup path computes the same hierarchy without a GPU.
  *
  * Each GMRES iteration (preconditioner, matvec, CGS2 Arnoldi, readback of
  * the Hessenberg column) is captured once per Krylov index into a CUDA graph
@@ -117,6 +120,8 @@ typedef struct {
                                         events, by kernel class (see mfs_kernel_stats) */
   int no_graphs;                     /* 1: launch kernels one by one instead of replaying
                                         one captured CUDA graph per GMRES iteration */
+  int setup_device;                  /* 1 (default): AMG setup on the GPU; 0: on the host
+                                        (C++/OpenMP); both compute the same hierarchy */
 } mfs_params;
 
 typedef struct {

@@ -20,7 +20,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libmfs.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["host_sparse.cpp", "amg_setup.cpp", "kernels.cu", "solver.cu", "noalloc.cu"]
+SOURCES = ["host_sparse.cpp", "amg_setup.cpp", "kernels.cu", "solver.cu", "noalloc.cu", "setup_gpu.cu"]
 
 
 def _nvcc():

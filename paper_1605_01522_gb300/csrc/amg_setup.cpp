@@ -2,7 +2,9 @@
 #include "amg_setup.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <numeric>
 
 namespace mfs {
@@ -291,9 +293,14 @@ HDenseLU dense_lu(int n, std::vector<double> a) {
   return out;
 }
 
+static double now_s() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
 void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<FieldInfo> &info,
                  int max_levels, int64_t coarse_max, uint64_t seed, bool want_off,
-                 const BlockMap *fine_off) {
+                 const BlockMap *fine_off, int verbose) {
+  double tm[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // power, strength, aggregate, tentative, AP, RAP, off, LU
   g.nf = (int)diag.size();
   g.info = info;
   g.lv.assign(1, std::vector<HLevelField>(g.nf));
@@ -315,34 +322,49 @@ void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<Fie
     for (int i = 0; i < g.nf; ++i) {
       HLevelField &fl = g.lv[l][i];
       const FieldInfo &f = info[i];
+      double t = now_s();
       fl.lam = power_lambda(fl.A, fl.dinv, seed);
+      tm[0] += now_s() - t;
+      t = now_s();
       Graph G = strength_graph(fl.A, f.theta);
+      tm[1] += now_s() - t;
+      t = now_s();
       aggregate(G, seed, fl.agg, fl.nagg);
+      tm[2] += now_s() - t;
       if (fl.nagg == 0) throw SetupError(-7, "aggregation produced no aggregate");
       const int k = fine ? nullspace_dim(f) : fl.A.br;
       HBsr Pt;
       std::vector<double> Bc;
+      t = now_s();
       tentative(fl.agg, fl.nagg, fl.A.br, k, fine, f, fl.B, Pt, Bc);
+      tm[3] += now_s() - t;
+      t = now_s();
       HBsr DAP = bsr_spgemm(fl.A, Pt);
       bsr_scale_rows(DAP, fl.dinv);
       const double omega = 4.0 / (3.0 * fl.lam);
       fl.P = bsr_axpby(1.0, Pt, -omega, DAP);
       fl.R = bsr_transpose(fl.P);
+      tm[4] += now_s() - t;
+      t = now_s();
       nxt[i].A = bsr_spgemm(fl.R, bsr_spgemm(fl.A, fl.P));
+      tm[5] += now_s() - t;
       nxt[i].B = std::move(Bc);
       fill_dinv(nxt[i]);
     }
     if (want_off) {
+      const double t = now_s();
       BlockMap noff;
       for (auto &kv : g.off[l]) {
         const int i = kv.first.first, j = kv.first.second;
         noff[kv.first] = bsr_spgemm(g.lv[l][i].R, bsr_spgemm(kv.second, g.lv[l][j].P));
       }
       g.off.push_back(std::move(noff));
+      tm[6] += now_s() - t;
     }
     g.lv.push_back(std::move(nxt));
   }
   // coarsest-level direct solvers
+  const double tlu = now_s();
   const int L = (int)g.lv.size() - 1;
   g.coarse_field.resize(g.nf);
   for (int i = 0; i < g.nf; ++i) {
@@ -364,6 +386,12 @@ void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<Fie
     for (auto &kv : g.off[L]) put(kv.second, kv.first.first, kv.first.second);
     g.coarse_coupled = dense_lu((int)n, std::move(D));
   }
+  tm[7] += now_s() - tlu;
+  if (verbose)
+    std::fprintf(stderr,
+                 "mfs setup group (%d fields, %d levels): power %.3f strength %.3f aggregate %.3f tentative %.3f "
+                 "smooth+transpose %.3f RAP %.3f offdiag %.3f LU %.3f s\n",
+                 g.nf, (int)g.lv.size(), tm[0], tm[1], tm[2], tm[3], tm[4], tm[5], tm[6], tm[7]);
 }
 
 }  // namespace mfs

@@ -62,7 +62,7 @@ struct HGroup {
 
 void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<FieldInfo> &info,
                  int max_levels, int64_t coarse_max, uint64_t seed, bool want_off,
-                 const BlockMap *fine_off);
+                 const BlockMap *fine_off, int verbose = 0);
 HDenseLU dense_lu(int n, std::vector<double> a_rowmajor);
 std::vector<double> bsr_to_dense(const HBsr &A);
 

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "amg_setup.h"
+#include "setup_gpu.h"
 #include "kernels.cuh"
 #include "mfs.h"
 
@@ -876,13 +877,19 @@ std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, 
 void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks,
                 const std::vector<FieldInfo> &info) {
   const mfs_params &p = h->prm;
+  const bool gpu = p.setup_device == 1 && !p.setup_only;
+  auto group = [&](HGroup &g, const std::vector<HBsr> &d, const std::vector<FieldInfo> &fi, bool off,
+                   const BlockMap *fo) {
+    if (gpu) build_group_gpu(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
+    else build_group(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
+  };
   if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS) {
     std::vector<HBsr> diag;
     BlockMap off;
     for (auto &kv : blocks)
       if (kv.first.first == kv.first.second) diag.push_back(kv.second);
       else off[kv.first] = kv.second;
-    build_group(h->host->hg0, diag, info, p.max_levels, p.coarse_max, p.seed, p.precond == MFS_AMG_BGS, &off);
+    group(h->host->hg0, diag, info, p.precond == MFS_AMG_BGS, &off);
     return;
   }
   h->host->G1.clear();
@@ -902,7 +909,7 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
     diag1.push_back(blocks.at({j, j}));
     info1.push_back(info[j]);
   }
-  build_group(h->host->hg0, diag1, info1, p.max_levels, p.coarse_max, p.seed, false, nullptr);
+  group(h->host->hg0, diag1, info1, false, nullptr);
   // A~_11: SIMPLEC sums of absolute entries over the merged predictor rows, or the diagonal
   h->host->dtilde.clear();
   for (int j : h->host->G1) {
@@ -943,7 +950,7 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
         std::vector<double> inv(h->host->dtilde[jj].size());
         for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / h->host->dtilde[jj][r];
         bsr_scale_rows(Cs, inv);
-        HBsr Tm = bsr_spgemm(a->second, Cs);
+        HBsr Tm = gpu ? gpu_spgemm(a->second, Cs) : bsr_spgemm(a->second, Cs);
         if (have) {
           M = bsr_axpby(1.0, M, -1.0, Tm);
         } else {
@@ -962,7 +969,7 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
       }
     }
   if (h->host->schur_diag.size() != h->host->G2.size()) throw SetupError(MFS_ERR_INVALID, "missing Schur diagonal block");
-  build_group(h->host->hg1, h->host->schur_diag, sinfo, p.max_levels, p.coarse_max, p.seed, false, nullptr);
+  group(h->host->hg1, h->host->schur_diag, sinfo, false, nullptr);
 }
 
 // Device half of the setup: upload the host hierarchy in precision T
@@ -1066,6 +1073,7 @@ void mfs_default_params(mfs_params *p) {
   p->seed = 7;
   p->cuda_stream = nullptr;
   p->verbose = 0;
+  p->setup_device = 1;
 }
 
 int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int nfields,
@@ -1079,7 +1087,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       p.max_levels < 1 || p.coarse_max < 0 || p.restart < 1 || p.restart > 60 || p.max_iters < 1 ||
       (p.smoother == MFS_CHEBYSHEV && (p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0))) ||
       (p.smoother == MFS_JACOBI && p.jacobi_sweeps < 1) || (p.smoother != MFS_CHEBYSHEV && p.smoother != MFS_JACOBI) ||
-      (p.precision != MFS_FP64 && p.precision != MFS_FP32P))
+      (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1)
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;

@@ -70,7 +70,7 @@ class Params(C.Structure):
                 ("jacobi_omega", C.c_double), ("jacobi_sweeps", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
-                ("profile", C.c_int), ("no_graphs", C.c_int)]
+                ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int)]
 
 
 class Info(C.Structure):

@@ -1,0 +1,77 @@
+"""GPU AMG setup (setup_device=1) against the host setup and the oracle.
+Needs a GB300.
+
+Aggregation is integer work: the GPU's parallel LFMIS rounds must give
+exactly the host's (and the oracle's) greedy aggregates.  Prolongators,
+restrictions, Galerkin blocks (diagonal and, for AMG(BGS), off-diagonal),
+lambda_max, the SIMPLE diagonal and S~ must agree to float64 rounding
+(1e-12 relative), at several sizes including ragged and coarse levels.
+"""
+import numpy as np
+import pytest
+
+pytest.importorskip("torch")
+
+from oracle import amg, precond
+from paper_1605_01522_gb300 import inputs, mfs
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+def _rel(a, b):
+    a, b = a.toarray(), b.toarray()
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+SYSTEMS = {
+    "2d": (lambda: inputs.thermo_elastic_2d(ne=20), dict(max_levels=3, coarse_max=0)),
+    "3d3": (lambda: inputs.coupled_box_3d(ne=11, nfields=3), dict(max_levels=4, coarse_max=100)),
+    "3d2": (lambda: inputs.coupled_box_3d(ne=17, nfields=2), dict(max_levels=4, coarse_max=200)),
+}
+
+
+@pytest.mark.parametrize("name", list(SYSTEMS))
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs"])
+def test_gpu_setup_matches_host_setup_and_oracle(name, pc):
+    gen, kw = SYSTEMS[name]
+    s = gen()
+    g = mfs.Solver(s, precond=pc, setup_device=1, **kw)
+    h = mfs.Solver(s, precond=pc, setup_only=1, **kw)
+    M = precond.Preconditioner(s.scipy_blocks(), [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params(pc, seed=7, **kw))
+    lv = M.groups[0].levels
+    assert g.num_levels(0) == h.num_levels(0) == len(lv)
+    for l in range(len(lv)):
+        for i in range(s.nfields):
+            assert _rel(g.export_csr("A", 0, l, i, i), h.export_csr("A", 0, l, i, i)) < TOL
+            if l < len(lv) - 1:
+                ag = g.export_array("agg", 0, l, i)
+                assert np.array_equal(ag, h.export_array("agg", 0, l, i))
+                assert np.array_equal(ag, lv[l][i].agg)
+                assert _rel(g.export_csr("P", 0, l, i), h.export_csr("P", 0, l, i)) < TOL
+                assert _rel(g.export_csr("R", 0, l, i), lv[l][i].R) < TOL
+                lg, lh = g.export_array("lambda", 0, l, i), h.export_array("lambda", 0, l, i)
+                assert abs(lg - lh) <= 1e-13 * lh
+    if pc == "amg_bgs":
+        for l in range(1, len(lv)):
+            for (i, j) in s.blocks:
+                if i != j:
+                    assert _rel(g.export_csr("A", 0, l, i, j), h.export_csr("A", 0, l, i, j)) < TOL
+    g.close()
+    h.close()
+
+
+def test_gpu_setup_simple_objects():
+    s = inputs.coupled_box_3d(ne=11, nfields=3)
+    kw = dict(max_levels=4, coarse_max=100, simple_group=[0, 0, 1])
+    g = mfs.Solver(s, precond="simple", setup_device=1, **kw)
+    h = mfs.Solver(s, precond="simple", setup_only=1, **kw)
+    for jj in range(2):
+        assert np.array_equal(g.export_array("dtilde", 0, 0, jj), h.export_array("dtilde", 0, 0, jj))
+    assert _rel(g.export_csr("A", 1, 0, 0, 0), h.export_csr("A", 1, 0, 0, 0)) < TOL
+    for l in range(g.num_levels(1) - 1):
+        assert np.array_equal(g.export_array("agg", 1, l, 0), h.export_array("agg", 1, l, 0))
+        assert _rel(g.export_csr("P", 1, l, 0), h.export_csr("P", 1, l, 0)) < TOL
+    g.close()
+    h.close()
