@@ -5,6 +5,7 @@
 #include "kernels.cuh"
 
 #include <cstdio>
+#include <mutex>
 
 namespace mfs {
 namespace dev {
@@ -504,8 +505,16 @@ inline unsigned ew_grid(int64_t n) {
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
 
 void init() {
+  // once per device and process (concurrent setups must not race on it)
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
   cudaFuncSetAttribute(k_lu_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_lu_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  done[dev] = true;
 }
 
 template <typename T>

@@ -37,6 +37,30 @@ namespace {
   } while (0)
 
 constexpr int kT = 256;
+
+// Every GPU-setup launch, copy and allocation goes to this thread's private
+// non-blocking stream (stream-ordered allocation), so a setup never touches
+// the legacy stream or synchronises the device while other threads replay
+// or capture solve graphs.
+thread_local cudaStream_t tls_stream = nullptr;
+inline cudaStream_t gstream() { return tls_stream; }
+
+struct StreamScope {
+  cudaStream_t prev;
+  cudaStream_t s = nullptr;
+  StreamScope() : prev(tls_stream) {
+    GS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    tls_stream = s;
+  }
+  ~StreamScope() {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+    tls_stream = prev;
+  }
+};
+
+inline void sync() { GS_CUDA(cudaStreamSynchronize(gstream())); }
+
 inline unsigned nblocks(int64_t n, int t = kT) { return (unsigned)std::max<int64_t>(1, (n + t - 1) / t); }
 
 template <typename T> struct DVec {
@@ -53,24 +77,26 @@ template <typename T> struct DVec {
     return *this;
   }
   ~DVec() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, gstream());
   }
   void resize(int64_t m, bool zero = false) {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, gstream());
     p = nullptr;
     n = m;
     if (m > 0) {
-      GS_CUDA(cudaMalloc(&p, (size_t)m * sizeof(T)));
-      if (zero) GS_CUDA(cudaMemset(p, 0, (size_t)m * sizeof(T)));
+      GS_CUDA(cudaMallocAsync((void **)&p, (size_t)m * sizeof(T), gstream()));
+      if (zero) GS_CUDA(cudaMemsetAsync(p, 0, (size_t)m * sizeof(T), gstream()));
     }
   }
   void upload(const T *h, int64_t m) {
     resize(m);
-    if (m) GS_CUDA(cudaMemcpy(p, h, (size_t)m * sizeof(T), cudaMemcpyHostToDevice));
+    if (m) GS_CUDA(cudaMemcpyAsync(p, h, (size_t)m * sizeof(T), cudaMemcpyHostToDevice, gstream()));
+    sync();
   }
   std::vector<T> download() const {
     std::vector<T> h(n);
-    if (n) GS_CUDA(cudaMemcpy(h.data(), p, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost));
+    if (n) GS_CUDA(cudaMemcpyAsync(h.data(), p, (size_t)n * sizeof(T), cudaMemcpyDeviceToHost, gstream()));
+    sync();
     return h;
   }
 };
@@ -169,10 +195,10 @@ void scan64(const int64_t *in, int64_t n, int64_t *out) {
   const int t = 1024;
   const int64_t nb = (n + t - 1) / t;
   DVec<int64_t> sums(nb), offs(nb);
-  k_scan_block64<<<(unsigned)nb, t>>>(in, n, out, sums.p);
+  k_scan_block64<<<(unsigned)nb, t, 0, gstream()>>>(in, n, out, sums.p);
   if (nb > 1) {
     scan64(sums.p, nb, offs.p);
-    k_scan_add<<<(unsigned)nb, t>>>(out, n, offs.p);
+    k_scan_add<<<(unsigned)nb, t, 0, gstream()>>>(out, n, offs.p);
   }
   GS_CUDA(cudaGetLastError());
 }
@@ -180,12 +206,13 @@ void scan64(const int64_t *in, int64_t n, int64_t *out) {
 // counts (int32, n entries) -> row pointer (int32, n + 1 entries); returns the total
 int64_t counts_to_rowptr(const int32_t *cnt, int64_t n, int32_t *rp) {
   DVec<int64_t> w(n + 1, true), o(n + 1);
-  if (n) k_widen<<<nblocks(n), kT>>>(cnt, w.p, n);
+  if (n) k_widen<<<nblocks(n), kT, 0, gstream()>>>(cnt, w.p, n);
   scan64(w.p, n + 1, o.p);
   int64_t total = 0;
-  GS_CUDA(cudaMemcpy(&total, o.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  GS_CUDA(cudaMemcpyAsync(&total, o.p + n, sizeof(int64_t), cudaMemcpyDeviceToHost, gstream()));
+  sync();
   if (total > INT32_MAX) throw SetupError(-1, "GPU setup: product too large for 32-bit offsets");
-  k_to_i32<<<nblocks(n + 1), kT>>>(o.p, rp, n + 1);
+  k_to_i32<<<nblocks(n + 1), kT, 0, gstream()>>>(o.p, rp, n + 1);
   GS_CUDA(cudaGetLastError());
   return total;
 }
@@ -284,19 +311,20 @@ __global__ void k_scale_rows(double *__restrict__ v, const int32_t *__restrict__
 double power_lambda_gpu(const DB &A, const double *dinv, uint64_t seed) {
   const int64_t n = A.nbr * A.br;
   DVec<double> v(n), w(n), part(256), nrm(1);
-  k_uniform<<<nblocks(n), kT>>>(v.p, n, seed);
-  k_sumsq_partial<<<256, kT>>>(v.p, n, part.p);
-  k_final_sqrt<<<1, 32>>>(part.p, 256, nrm.p);
-  k_scale_by<<<nblocks(n), kT>>>(v.p, n, nrm.p);
+  k_uniform<<<nblocks(n), kT, 0, gstream()>>>(v.p, n, seed);
+  k_sumsq_partial<<<256, kT, 0, gstream()>>>(v.p, n, part.p);
+  k_final_sqrt<<<1, 32, 0, gstream()>>>(part.p, 256, nrm.p);
+  k_scale_by<<<nblocks(n), kT, 0, gstream()>>>(v.p, n, nrm.p);
   for (int it = 0; it < 10; ++it) {
-    k_dinv_spmv<<<nblocks(A.nbr), kT>>>(view(A), v.p, dinv, w.p);
-    k_sumsq_partial<<<256, kT>>>(w.p, n, part.p);
-    k_final_sqrt<<<1, 32>>>(part.p, 256, nrm.p);
-    k_div_into<<<nblocks(n), kT>>>(w.p, v.p, n, nrm.p);
+    k_dinv_spmv<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), v.p, dinv, w.p);
+    k_sumsq_partial<<<256, kT, 0, gstream()>>>(w.p, n, part.p);
+    k_final_sqrt<<<1, 32, 0, gstream()>>>(part.p, 256, nrm.p);
+    k_div_into<<<nblocks(n), kT, 0, gstream()>>>(w.p, v.p, n, nrm.p);
   }
   GS_CUDA(cudaGetLastError());
   double lam = 0.0;
-  GS_CUDA(cudaMemcpy(&lam, nrm.p, sizeof(double), cudaMemcpyDeviceToHost));
+  GS_CUDA(cudaMemcpyAsync(&lam, nrm.p, sizeof(double), cudaMemcpyDeviceToHost, gstream()));
+  sync();
   return lam;
 }
 
@@ -436,10 +464,11 @@ DB spgemm(const DB &A, const DB &B) {
   DVec<int32_t> cnt(A.nbr, true);
   DVec<int> ovf(1, true);
   const unsigned g = (unsigned)((A.nbr + kWarpsSp - 1) / kWarpsSp);
-  k_spgemm_count<<<g, 32 * kWarpsSp>>>(view(A), view(B), cnt.p, ovf.p);
+  k_spgemm_count<<<g, 32 * kWarpsSp, 0, gstream()>>>(view(A), view(B), cnt.p, ovf.p);
   GS_CUDA(cudaGetLastError());
   int o = 0;
-  GS_CUDA(cudaMemcpy(&o, ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  GS_CUDA(cudaMemcpyAsync(&o, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, gstream()));
+  sync();
   if (o) {  // a row with more than kCap distinct columns: do this product on the host
     C = upload(bsr_spgemm(download(A), download(B)));
     return C;
@@ -447,7 +476,7 @@ DB spgemm(const DB &A, const DB &B) {
   C.nnzb = counts_to_rowptr(cnt.p, A.nbr, C.rp.p);
   C.ci.resize(C.nnzb);
   C.v.resize(C.nnzb * C.br * C.bc);
-  k_spgemm_fill<<<g, 32 * kWarpsSp>>>(view(A), view(B), C.rp.p, C.ci.p, C.v.p, ovf.p);
+  k_spgemm_fill<<<g, 32 * kWarpsSp, 0, gstream()>>>(view(A), view(B), C.rp.p, C.ci.p, C.v.p, ovf.p);
   GS_CUDA(cudaGetLastError());
   return C;
 }
@@ -515,16 +544,17 @@ DB transpose(const DB &A, bool values = true) {
   T.nnzb = A.nnzb;
   if (A.nbc == 0) return T;
   DVec<int32_t> cnt(A.nbc, true), fill(A.nbc, true);
-  if (A.nnzb) k_col_count<<<nblocks(A.nnzb), kT>>>(A.ci.p, A.nnzb, cnt.p);
+  if (A.nnzb) k_col_count<<<nblocks(A.nnzb), kT, 0, gstream()>>>(A.ci.p, A.nnzb, cnt.p);
   counts_to_rowptr(cnt.p, A.nbc, T.rp.p);
   T.ci.resize(A.nnzb);
   DVec<int32_t> src(A.nnzb);
-  k_t_scatter<<<nblocks(A.nbr), kT>>>(A.rp.p, A.ci.p, A.nbr, T.rp.p, fill.p, T.ci.p, src.p);
+  k_t_scatter<<<nblocks(A.nbr), kT, 0, gstream()>>>(A.rp.p, A.ci.p, A.nbr, T.rp.p, fill.p, T.ci.p, src.p);
   DVec<int> ovf(1, true);
-  k_t_sort<<<(unsigned)((A.nbc + kWarpsT - 1) / kWarpsT), 32 * kWarpsT>>>(T.rp.p, A.nbc, T.ci.p, src.p, ovf.p);
+  k_t_sort<<<(unsigned)((A.nbc + kWarpsT - 1) / kWarpsT), 32 * kWarpsT, 0, gstream()>>>(T.rp.p, A.nbc, T.ci.p, src.p, ovf.p);
   GS_CUDA(cudaGetLastError());
   int o = 0;
-  GS_CUDA(cudaMemcpy(&o, ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+  GS_CUDA(cudaMemcpyAsync(&o, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, gstream()));
+  sync();
   if (o) {  // a transposed row longer than the warp sort handles: host transpose
     HBsr H = download(A);
     if (!values) H.v.assign((size_t)H.nnzb() * H.br * H.bc, 0.0);
@@ -532,7 +562,7 @@ DB transpose(const DB &A, bool values = true) {
   }
   if (values) {
     T.v.resize(A.nnzb * A.br * A.bc);
-    if (A.nnzb) k_t_values<<<nblocks(A.nnzb), kT>>>(A.v.p, src.p, A.nnzb, A.br, A.bc, T.v.p);
+    if (A.nnzb) k_t_values<<<nblocks(A.nnzb), kT, 0, gstream()>>>(A.v.p, src.p, A.nnzb, A.br, A.bc, T.v.p);
   }
   GS_CUDA(cudaGetLastError());
   return T;
@@ -589,11 +619,11 @@ DB merge(double sa, const DB &A, double sb, const DB &B, bool values) {
   C.shape(A.br, A.bc, A.nbr, A.nbc);
   if (A.nbr == 0) return C;
   DVec<int32_t> cnt(A.nbr);
-  k_merge_count<<<nblocks(A.nbr), kT>>>(A.rp.p, A.ci.p, B.rp.p, B.ci.p, A.nbr, cnt.p);
+  k_merge_count<<<nblocks(A.nbr), kT, 0, gstream()>>>(A.rp.p, A.ci.p, B.rp.p, B.ci.p, A.nbr, cnt.p);
   C.nnzb = counts_to_rowptr(cnt.p, A.nbr, C.rp.p);
   C.ci.resize(C.nnzb);
   if (values) C.v.resize(C.nnzb * A.br * A.bc);
-  k_merge_fill<<<nblocks(A.nbr), kT>>>(A.rp.p, A.ci.p, values ? A.v.p : nullptr, B.rp.p, B.ci.p,
+  k_merge_fill<<<nblocks(A.nbr), kT, 0, gstream()>>>(A.rp.p, A.ci.p, values ? A.v.p : nullptr, B.rp.p, B.ci.p,
                                        values ? B.v.p : nullptr, A.nbr, A.br * A.bc, sa, sb, C.rp.p, C.ci.p,
                                        values ? C.v.p : nullptr);
   GS_CUDA(cudaGetLastError());
@@ -632,14 +662,14 @@ __global__ void k_strong(BV A, const double *__restrict__ fro, const double *__r
 // node graph of strong connections, symmetrised (pattern only)
 DB strength(const DB &A, double theta) {
   DVec<double> fro(std::max<int64_t>(1, A.nnzb)), dn(A.nbr, true);
-  k_block_fro<<<nblocks(A.nbr), kT>>>(view(A), fro.p, dn.p);
+  k_block_fro<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p);
   DB S;
   S.shape(1, 1, A.nbr, A.nbr);
   DVec<int32_t> cnt(A.nbr);
-  k_strong<<<nblocks(A.nbr), kT>>>(view(A), fro.p, dn.p, theta, nullptr, cnt.p, nullptr);
+  k_strong<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p, theta, nullptr, cnt.p, nullptr);
   S.nnzb = counts_to_rowptr(cnt.p, A.nbr, S.rp.p);
   S.ci.resize(S.nnzb);
-  k_strong<<<nblocks(A.nbr), kT>>>(view(A), fro.p, dn.p, theta, S.rp.p, cnt.p, S.ci.p);
+  k_strong<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p, theta, S.rp.p, cnt.p, S.ci.p);
   GS_CUDA(cudaGetLastError());
   DB ST = transpose(S, false);
   return merge(1.0, S, 1.0, ST, false);
@@ -752,29 +782,31 @@ int64_t aggregate_gpu(const DB &G, uint64_t seed, DVec<int32_t> &agg) {
   DVec<int8_t> st(n), r1(n);
   DVec<int32_t> b1(n), flags(n), rid(n + 1);
   DVec<int> left(1);
-  k_agg_init<<<nblocks(n), kT>>>(G.rp.p, n, st.p);
+  k_agg_init<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, n, st.p);
   for (int round = 0; round < 10000; ++round) {
-    k_root_near<<<nblocks(n), kT>>>(G.rp.p, G.ci.p, n, st.p, r1.p);
-    k_mark_out<<<nblocks(n), kT>>>(G.rp.p, G.ci.p, n, st.p, r1.p);
-    k_best_near<<<nblocks(n), kT>>>(G.rp.p, G.ci.p, n, st.p, b1.p, seed);
-    GS_CUDA(cudaMemset(left.p, 0, sizeof(int)));
-    k_pick<<<nblocks(n), kT>>>(G.rp.p, G.ci.p, n, st.p, b1.p, seed, left.p);
+    k_root_near<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, G.ci.p, n, st.p, r1.p);
+    k_mark_out<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, G.ci.p, n, st.p, r1.p);
+    k_best_near<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, G.ci.p, n, st.p, b1.p, seed);
+    GS_CUDA(cudaMemsetAsync(left.p, 0, sizeof(int), gstream()));
+    k_pick<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, G.ci.p, n, st.p, b1.p, seed, left.p);
     int l = 0;
-    GS_CUDA(cudaMemcpy(&l, left.p, sizeof(int), cudaMemcpyDeviceToHost));
+    GS_CUDA(cudaMemcpyAsync(&l, left.p, sizeof(int), cudaMemcpyDeviceToHost, gstream()));
+  sync();
     if (l == 0) break;
     if (round == 9999) throw SetupError(-7, "GPU setup: aggregation did not settle");
   }
-  k_root_flags<<<nblocks(n), kT>>>(st.p, n, flags.p);
+  k_root_flags<<<nblocks(n), kT, 0, gstream()>>>(st.p, n, flags.p);
   const int64_t nagg = counts_to_rowptr(flags.p, n, rid.p);
   agg.resize(n);
   DVec<int32_t> agg2(n), roots(std::max<int64_t>(1, nagg));
-  k_phase12<<<nblocks(n), kT>>>(G.rp.p, G.ci.p, n, st.p, rid.p, agg2.p, roots.p);
-  GS_CUDA(cudaMemcpy(agg.p, agg2.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice));
+  k_phase12<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, G.ci.p, n, st.p, rid.p, agg2.p, roots.p);
+  GS_CUDA(cudaMemcpyAsync(agg.p, agg2.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, gstream()));
   DVec<int> bad(1, true);
-  k_phase3<<<nblocks(n), kT>>>(G.rp.p, G.ci.p, n, st.p, agg2.p, roots.p, agg.p, seed, bad.p);
+  k_phase3<<<nblocks(n), kT, 0, gstream()>>>(G.rp.p, G.ci.p, n, st.p, agg2.p, roots.p, agg.p, seed, bad.p);
   GS_CUDA(cudaGetLastError());
   int b = 0;
-  GS_CUDA(cudaMemcpy(&b, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+  GS_CUDA(cudaMemcpyAsync(&b, bad.p, sizeof(int), cudaMemcpyDeviceToHost, gstream()));
+  sync();
   if (b) throw SetupError(-7, "GPU setup: node not within distance 2 of a root");
   return nagg;
 }
@@ -915,20 +947,30 @@ struct GLevel {
 void fill_dinv(const DB &A, DVec<double> &dinv) {
   dinv.resize(A.nbr * A.br);
   DVec<int> bad(1, true);
-  k_diag_inv<<<nblocks(A.nbr), kT>>>(view(A), dinv.p, bad.p);
+  k_diag_inv<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), dinv.p, bad.p);
   GS_CUDA(cudaGetLastError());
   int b = 0;
-  GS_CUDA(cudaMemcpy(&b, bad.p, sizeof(int), cudaMemcpyDeviceToHost));
+  GS_CUDA(cudaMemcpyAsync(&b, bad.p, sizeof(int), cudaMemcpyDeviceToHost, gstream()));
+  sync();
   if (b) throw SetupError(-4, "zero diagonal entry in a diagonal block");
 }
 
 }  // namespace
 
-HBsr gpu_spgemm(const HBsr &A, const HBsr &B) { return download(spgemm(upload(A), upload(B))); }
+HBsr gpu_spgemm(const HBsr &A, const HBsr &B) {
+  StreamScope scope;
+  HBsr C;
+  {
+    DB a = upload(A), b = upload(B);
+    C = download(spgemm(a, b));
+  }
+  return C;
+}
 
 void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector<FieldInfo> &info,
                      int max_levels, int64_t coarse_max, uint64_t seed, bool want_off,
                      const BlockMap *fine_off, int verbose) {
+  StreamScope scope;  // outlives every device array below
   double tm[7] = {0, 0, 0, 0, 0, 0, 0};  // power, strength, aggregate, tentative, smooth+transpose, RAP, offdiag
   g.nf = (int)diag.size();
   g.info = info;
@@ -955,11 +997,11 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       const FieldInfo &f = info[i];
       double t = now_s();
       fl.lam = power_lambda_gpu(fl.A, fl.dinv.p, seed);
-      GS_CUDA(cudaDeviceSynchronize());
+      sync();
       tm[0] += now_s() - t;
       t = now_s();
       DB G = strength(fl.A, f.theta);
-      GS_CUDA(cudaDeviceSynchronize());
+      sync();
       tm[1] += now_s() - t;
       t = now_s();
       fl.nagg = aggregate_gpu(G, seed, fl.agg);
@@ -970,18 +1012,19 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       const int k = fine ? (f.ns == 0 ? f.b : (f.dim == 2 ? 3 : 6)) : b;
       const int64_t n = fl.A.nbr;
       DVec<int32_t> cnt(fl.nagg, true), start(fl.nagg + 1), fillc(fl.nagg, true), members(n), flg(n);
-      k_agg_count<<<nblocks(n), kT>>>(fl.agg.p, n, cnt.p);
+      k_agg_count<<<nblocks(n), kT, 0, gstream()>>>(fl.agg.p, n, cnt.p);
       const int64_t nmem = counts_to_rowptr(cnt.p, fl.nagg, start.p);
       members.resize(std::max<int64_t>(1, nmem));
-      k_agg_scatter<<<nblocks(n), kT>>>(fl.agg.p, n, start.p, fillc.p, members.p);
+      k_agg_scatter<<<nblocks(n), kT, 0, gstream()>>>(fl.agg.p, n, start.p, fillc.p, members.p);
       DVec<int> ovf(1, true);
-      k_agg_sort<<<(unsigned)((fl.nagg + kWarpsT - 1) / kWarpsT), 32 * kWarpsT>>>(start.p, fl.nagg, members.p, ovf.p);
+      k_agg_sort<<<(unsigned)((fl.nagg + kWarpsT - 1) / kWarpsT), 32 * kWarpsT, 0, gstream()>>>(start.p, fl.nagg, members.p, ovf.p);
       int o = 0;
-      GS_CUDA(cudaMemcpy(&o, ovf.p, sizeof(int), cudaMemcpyDeviceToHost));
+      GS_CUDA(cudaMemcpyAsync(&o, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, gstream()));
+  sync();
       if (o) throw SetupError(-7, "GPU setup: aggregate larger than 1024 nodes");
       DB Pt;
       Pt.shape(b, k, n, fl.nagg);
-      k_agg_flag<<<nblocks(n), kT>>>(fl.agg.p, n, flg.p);
+      k_agg_flag<<<nblocks(n), kT, 0, gstream()>>>(fl.agg.p, n, flg.p);
       Pt.nnzb = counts_to_rowptr(flg.p, n, Pt.rp.p);
       Pt.ci.resize(Pt.nnzb);
       Pt.v.resize(Pt.nnzb * b * k);
@@ -989,18 +1032,18 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       if (fine && f.ns == 1) coords.upload(f.coords.data(), (int64_t)f.coords.size());
       nxt[i].B.resize(fl.nagg * k * k);
       const int kind = fine ? (f.ns == 0 ? 0 : 1) : 2;
-      k_tentative<<<(unsigned)((fl.nagg + 3) / 4), 128>>>(start.p, members.p, fl.nagg, b, k, kind, f.dim, coords.p,
+      k_tentative<<<(unsigned)((fl.nagg + 3) / 4), 128, 0, gstream()>>>(start.p, members.p, fl.nagg, b, k, kind, f.dim, coords.p,
                                                           fl.B.p, Pt.rp.p, Pt.ci.p, Pt.v.p, nxt[i].B.p);
       GS_CUDA(cudaGetLastError());
-      GS_CUDA(cudaDeviceSynchronize());
+      sync();
       tm[3] += now_s() - t;
       t = now_s();
       DB DAP = spgemm(fl.A, Pt);
-      k_scale_rows<<<nblocks(DAP.nbr), kT>>>(DAP.v.p, DAP.rp.p, DAP.nbr, DAP.br, DAP.bc, fl.dinv.p);
+      k_scale_rows<<<nblocks(DAP.nbr), kT, 0, gstream()>>>(DAP.v.p, DAP.rp.p, DAP.nbr, DAP.br, DAP.bc, fl.dinv.p);
       const double omega = 4.0 / (3.0 * fl.lam);
       fl.P = merge(1.0, Pt, -omega, DAP, true);
       fl.R = transpose(fl.P, true);
-      GS_CUDA(cudaDeviceSynchronize());
+      sync();
       tm[4] += now_s() - t;
       t = now_s();
       {
@@ -1008,7 +1051,7 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
         nxt[i].A = spgemm(fl.R, AP);
       }
       fill_dinv(nxt[i].A, nxt[i].dinv);
-      GS_CUDA(cudaDeviceSynchronize());
+      sync();
       tm[5] += now_s() - t;
     }
     if (want_off) {
@@ -1020,7 +1063,7 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
         noff[kv.first] = spgemm(lv[l][i].R, AP);
       }
       off.push_back(std::move(noff));
-      GS_CUDA(cudaDeviceSynchronize());
+      sync();
       tm[6] += now_s() - t;
     }
     lv.push_back(std::move(nxt));
