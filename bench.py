@@ -41,9 +41,11 @@ CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_eve
 
 
 def workload_config(args, s, extra=None):
+    what = (f"3-field 3D coupled box {NE}^3 Q1 ({s.ndofs} dofs: elasticity+heat+diffusion)"
+            if args.workload != "fsi" else
+            f"4-field split-box saddle 48^3 Q1 ({s.ndofs} dofs: structure | mesh + PSPG Stokes u, p)")
     cfg = {
-        "workload": f"3-field 3D coupled box {NE}^3 Q1 ({s.ndofs} dofs: elasticity+heat+diffusion), "
-                    f"{args.precond.upper()} preconditioner in {args.precision.upper()}, FGMRES(50), rtol 1e-8",
+        "workload": f"{what}, {args.precond.upper()} preconditioner in {args.precision.upper()}, FGMRES(50), rtol 1e-8",
         "ndofs": s.ndofs,
         "precond": args.precond,
         "precision": args.precision,
@@ -173,9 +175,23 @@ def ncu_traffic(kernel, rows):
     return None
 
 
-def make_system():
+def make_system(args=None):
     from paper_1605_01522_gb300 import inputs
+    if args is not None and args.workload == "fsi":
+        return inputs.fsi_box(ne=48, seed=2)
     return inputs.coupled_box_3d(ne=NE, nfields=3, seed=1)
+
+
+def counts_key(args):
+    return ("fsi_box_ne48" if args.workload == "fsi" else WORKLOAD) + "/" + args.precond
+
+
+def precond_extra(args):
+    """Preconditioner options of the workload (the split box uses SIMPLE with a
+    diagonal A~11 over the predictor fields S, G, Fu and the pressure as Schur field)."""
+    if args.workload == "fsi" and args.precond == "simple":
+        return dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
+    return {}
 
 
 def oracle_counts():
@@ -184,14 +200,15 @@ def oracle_counts():
         return json.load(f)
 
 
-def oracle_sample(s, precond_name, n_iter):
+def oracle_sample(s, precond_name, n_iter, extra=None):
     """Time n_iter FGMRES iterations of the FP64 oracle (its own hierarchy,
     built untimed) on the full workload; returns (seconds per iteration, setup s)."""
     from oracle import amg, krylov, precond
     A = s.scipy_blocks()
     D = precond.assemble(A, s.nfields)
     t0 = time.perf_counter()
-    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], precond.Params(precond_name, **SOLVER_KW))
+    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params(precond_name, **SOLVER_KW, **(extra or {})))
     t1 = time.perf_counter()
     krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=n_iter)
     t2 = time.perf_counter()
@@ -201,9 +218,9 @@ def oracle_sample(s, precond_name, n_iter):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    s = make_system()
+    s = make_system(args)
     counts = oracle_counts()
-    key = f"{WORKLOAD}/{args.precond}"
+    key = counts_key(args)
     iters = counts[key]["iters"]
     n_iter = 2
     times = []
@@ -212,7 +229,8 @@ def run_reference(args, rank, world):
     A = s.scipy_blocks()
     D = precond.assemble(A, s.nfields)
     t0 = time.perf_counter()
-    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], precond.Params(args.precond, **SOLVER_KW))
+    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params(args.precond, **SOLVER_KW, **precond_extra(args)))
     setup_s = time.perf_counter() - t0
     for k in range(args.warmup + args.steps):
         t1 = time.perf_counter()
@@ -243,10 +261,11 @@ def run_mfs(args, rank, world):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
-    s = make_system()
+    s = make_system(args)
     stream = torch.cuda.Stream(device=dev)
     prm = mfs.default_params(precond=args.precond, precision=args.precision, profile=1,
-                             cuda_stream=stream.cuda_stream, no_graphs=int(args.no_graphs), **SOLVER_KW)
+                             cuda_stream=stream.cuda_stream, no_graphs=int(args.no_graphs), **SOLVER_KW,
+                             **precond_extra(args))
     t0 = time.perf_counter()
     lib = mfs.Solver(s, params=prm)
     setup_s = time.perf_counter() - t0
@@ -352,9 +371,9 @@ def run_mfs(args, rank, world):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         counts = oracle_counts()
-        iters_o = counts[f"{WORKLOAD}/{args.precond}"]["iters"]
+        iters_o = counts[counts_key(args)]["iters"]
         n_iter = 3
-        per_iter, osetup = oracle_sample(s, args.precond, n_iter)
+        per_iter, osetup = oracle_sample(s, args.precond, n_iter, precond_extra(args))
         cpu = {"value": 1.0 / (per_iter * iters_o), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n_iter} FGMRES({args.precond}) iterations of the FP64 oracle on the full workload "
                          f"(own hierarchy, setup {osetup:.1f} s untimed), scaled by its {iters_o} iterations/solve"}
@@ -495,8 +514,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--ne", type=int, default=NE, help="mesh edge (64 = the benchmark workload)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "batch", "serve"],
-                    help="box: the 64^3 three-field system (headline); batch: 256 independent systems")
+    ap.add_argument("--workload", default="box", choices=["box", "fsi", "batch", "serve"],
+                    help="box: the 64^3 three-field system (headline); fsi: the 48^3 split-box saddle; "
+                         "batch: 256 independent systems; serve: Poisson request stream")
     ap.add_argument("--nsys", type=int, default=256)
     ap.add_argument("--threads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=1000)

@@ -120,6 +120,7 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   std::vector<float> v32;
   if (want64) v64.assign((size_t)S.nslots * bs * 32, 0.0);
   if (want32) v32.assign((size_t)S.nslots * bs * 32, 0.0f);
+#pragma omp parallel for schedule(static)
   for (int64_t I = 0; I < A.nbr; ++I) {
     const int64_t s = I >> 5, lane = I & 31;
     for (int64_t t = 0; t < A.rp[I + 1] - A.rp[I]; ++t) {
@@ -812,13 +813,21 @@ HBsr to_hbsr(const mfs_block &b) {
   A.ci.assign(b.colind, b.colind + b.nnzb);
   A.v.assign(b.vals, b.vals + b.nnzb * b.br * b.bc);
   if (A.rp[0] != 0 || A.rp[A.nbr] != b.nnzb) throw SetupError(MFS_ERR_INVALID, "block rowptr inconsistent with nnzb");
+  int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
   for (int64_t I = 0; I < A.nbr; ++I) {
-    if (A.rp[I + 1] < A.rp[I]) throw SetupError(MFS_ERR_INVALID, "block rowptr not monotone");
+    if (A.rp[I + 1] < A.rp[I]) {
+      bad |= 1;
+      continue;
+    }
     for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a) {
-      if (A.ci[a] < 0 || A.ci[a] >= A.nbc) throw SetupError(MFS_ERR_INVALID, "block column index out of range");
-      if (a > A.rp[I] && A.ci[a] <= A.ci[a - 1]) throw SetupError(MFS_ERR_INVALID, "block columns not sorted/unique");
+      if (A.ci[a] < 0 || A.ci[a] >= A.nbc) bad |= 2;
+      else if (a > A.rp[I] && A.ci[a] <= A.ci[a - 1]) bad |= 4;
     }
   }
+  if (bad & 1) throw SetupError(MFS_ERR_INVALID, "block rowptr not monotone");
+  if (bad & 2) throw SetupError(MFS_ERR_INVALID, "block column index out of range");
+  if (bad & 4) throw SetupError(MFS_ERR_INVALID, "block columns not sorted/unique");
   return A;
 }
 
@@ -852,6 +861,7 @@ std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, 
     M.rp = row[0]->rp;
     M.ci = row[0]->ci;
     M.v.assign((size_t)M.nnzb() * M.br * M.bc, 0.0);
+#pragma omp parallel for schedule(static)
     for (int64_t k = 0; k < M.nnzb(); ++k)
       for (int r = 0; r < br; ++r) {
         int o = 0;

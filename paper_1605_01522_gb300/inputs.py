@@ -14,6 +14,10 @@ whose meshes are not available:
 * ``thermo_elastic_2d``  - 2 fields on the unit square: plane-strain elasticity
   (2 dof/node) + transient heat (1 dof/node), coupled through
   A_12 = alpha * int B^T m N and A_21 = 1e-3 * int N m^T B.
+* ``fsi_box``            - 4 fields on the unit cube split at z = 0.5: elasticity
+  above, mesh motion + PSPG Stokes velocity / pressure below, coupled through an
+  interface penalty and volume blocks (saddle point: the pressure block is
+  negative definite).
 * ``coupled_box_3d``     - the 3D analogue on the unit cube with 2 or 3 fields:
   elasticity (3 dof/node), heat (1 dof/node) and an optional scalar diffusion
   field whose diffusivity is log-uniform in [1e-3, 1e3] per element.  The
@@ -32,8 +36,8 @@ import itertools
 import numpy as np
 
 __all__ = [
-    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d",
-    "batch_sizes_log_uniform",
+    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d", "fsi_box",
+    "batch_sizes_log_uniform", "batch_workload", "system_rhs",
 ]
 
 
@@ -205,15 +209,23 @@ def q1_element_matrices(dim, h, E=1.0, nu=0.3):
 # ----------------------------------------------------------------------------
 
 class _Grid:
-    def __init__(self, ne, dim):
+    """Structured node grid of ne cells per direction, or of `shape` cells
+    (x, y[, z]) with edge h and the given origin."""
+
+    def __init__(self, ne, dim, shape=None, h=None, origin=None):
+        shape = tuple(shape) if shape is not None else (ne,) * dim
         self.ne = ne
         self.dim = dim
-        self.n1 = ne + 1
-        self.nnodes = self.n1 ** dim
-        ijk = np.indices((self.n1,) * dim).reshape(dim, -1)[::-1]  # x fastest
-        self.ijk = ijk.T.copy()                                      # (nnodes, dim): (i, j[, k])
-        self.coords = self.ijk / float(ne)
-        self.stride = np.array([self.n1 ** d for d in range(dim)])
+        self.shape = shape
+        self.h = h if h is not None else 1.0 / ne
+        n1 = [c + 1 for c in shape]
+        self.n1 = n1[0]
+        self.nnodes = int(np.prod(n1))
+        ijk = np.indices(tuple(reversed(n1))).reshape(dim, -1)[::-1]  # x fastest
+        self.ijk = ijk.T.copy()                                        # (nnodes, dim): (i, j[, k])
+        org = np.zeros(dim) if origin is None else np.asarray(origin, float)
+        self.coords = self.ijk * self.h + org
+        self.stride = np.array([int(np.prod(n1[:d])) for d in range(dim)])
         # neighbour stencil, in increasing node-index order (z slowest)
         self.stencil = [tuple(reversed(t)) for t in itertools.product((-1, 0, 1), repeat=dim)]
         self.sidx = {s: k for k, s in enumerate(self.stencil)}
@@ -222,7 +234,7 @@ class _Grid:
         for k, s in enumerate(self.stencil):
             for d in range(dim):
                 c = self.ijk[:, d] + s[d]
-                valid[:, k] &= (c >= 0) & (c <= ne)
+                valid[:, k] &= (c >= 0) & (c <= shape[d])
         self.valid = valid
         counts = valid.sum(1)
         self.rowptr = np.zeros(self.nnodes + 1, np.int64)
@@ -238,7 +250,7 @@ class _Grid:
             colind[pos[v, k]] = np.nonzero(v)[0] + off
         self.colind = colind
         # elements: base node index for every cell
-        eijk = np.indices((ne,) * dim).reshape(dim, -1)[::-1].T
+        eijk = np.indices(tuple(reversed(shape))).reshape(dim, -1)[::-1].T
         self.nelem = eijk.shape[0]
         self.ebase = eijk @ self.stride
         self.loc = _local_offsets(dim)
@@ -354,6 +366,141 @@ def coupled_box_3d(ne=64, nfields=3, alpha=1e-2, beta=1e-3, E=1.0, nu=0.3, k=1.0
     return BlockSystem(fields, blocks, _seeded_rhs(fields, seed, dnodes),
                        name=f"coupled_box_3d_ne{ne}_f{nfields}",
                        meta=dict(ne=ne, nfields=nfields, alpha=alpha, seed=seed))
+
+
+def q1_flow_matrices(h):
+    """3D Q1 cell matrices for the flow blocks: G[a*3+c, b] = -int dN_a/dx_c N_b
+    (velocity x pressure, the discrete divergence) and Dz[a, b] = int N_a dN_b/dz."""
+    pts, wts = _gauss_2pt()
+    G = np.zeros((24, 8))
+    Dz = np.zeros((8, 8))
+    for idx in itertools.product(range(2), repeat=3):
+        xi = np.array([pts[i] for i in idx])
+        w = np.prod([wts[i] for i in idx]) * h ** 3
+        N, dN = _shape_at(3, xi)
+        dNdx = dN / h
+        for a in range(8):
+            for c in range(3):
+                G[a * 3 + c] -= w * dNdx[a, c] * N
+        Dz += w * np.outer(N, dNdx[:, 2])
+    return G, Dz
+
+
+def _vector_cell(K, b):
+    """Cell matrix acting componentwise on b-vectors: (K kron I_b) in dof order a*b + c."""
+    return np.kron(K, np.eye(b))
+
+
+def _interface_nodes(grid, k):
+    """Node-level interface mass between layer k of `grid` and itself (CSR)."""
+    import scipy.sparse as sp
+    nx, ny = grid.shape[0], grid.shape[1]
+    M2 = q1_element_matrices(2, grid.h)[2]
+    loc2 = _local_offsets(2)
+    ci, cj = np.meshgrid(np.arange(nx), np.arange(ny), indexing="xy")
+    ci, cj = ci.ravel(), cj.ravel()
+    rows, cols, vals = [], [], []
+    for a, oa in enumerate(loc2):
+        for b, ob in enumerate(loc2):
+            rows.append((ci + oa[0]) + grid.stride[1] * (cj + oa[1]) + grid.stride[2] * k)
+            cols.append((ci + ob[0]) + grid.stride[1] * (cj + ob[1]) + grid.stride[2] * k)
+            vals.append(np.full(ci.shape, M2[a, b]))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(grid.nnodes, grid.nnodes))
+
+
+def _add_to_grid_block(grid, vals, Nm, scale, b):
+    """vals (grid BSR of b x b blocks) += scale * Nm (node-level, inside the stencil) kron I_b."""
+    Nm = Nm.tocoo()
+    d = grid.ijk[Nm.col] - grid.ijk[Nm.row]
+    sidx = np.array([grid.sidx[tuple(t)] for t in d])
+    p = grid.pos[Nm.row, sidx]
+    assert np.all(p >= 0)
+    np.add.at(vals, p, scale * Nm.data[:, None, None] * np.eye(b)[None])
+
+
+def _node_bsr(Nm, b, scale):
+    """BSR of b x b blocks scale * Nm kron I_b from a node-level CSR."""
+    Nm = Nm.tocsr()
+    Nm.sort_indices()
+    return BSR(b, b, Nm.shape[0], Nm.shape[1], Nm.indptr.astype(np.int32), Nm.indices.astype(np.int32),
+               scale * Nm.data[:, None, None] * np.eye(b)[None])
+
+
+def _dirichlet_fields(blocks, dmasks):
+    """Symmetric elimination with a Dirichlet node mask per field."""
+    for (i, j), m in blocks.items():
+        rows = np.repeat(np.arange(m.nbrows), np.diff(m.rowptr))
+        kill = dmasks[i][rows] | dmasks[j][m.colind]
+        m.vals[kill] = 0.0
+        if i == j:
+            diag = dmasks[i][rows] & (rows == m.colind)
+            m.vals[diag] = np.eye(m.br)
+
+
+def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2):
+    """Fluid / structure / mesh-motion-like saddle system on the unit cube split
+    at z = 0.5 (stand-in for the FSI block system of Sec. 6.2).  Fields:
+      0 S  elasticity (3 dof/node, E, clamped top face) on the upper half;
+      1 G  mesh motion, vector Laplacian (3 dof/node, zero on the lower half's
+           outer faces) on the lower half;
+      2 Fu Stokes velocity, nu * vector Laplacian (no-slip lateral faces, open
+           bottom) on the lower half;
+      3 Fp pressure (PSPG: -tau L, tau = h^2/(12 nu), p = 0 on the bottom face).
+    Couplings: Fu-Fp discrete divergence and gradient; S-Fu and G-Fu interface
+    penalties gamma * M_Gamma on the z = 0.5 plane (-M off the diagonal, +M on
+    it); Fu <- G volume block eta * int N dN/dz.  S-G, S-Fp, G-Fp are zero."""
+    h = 1.0 / ne
+    nz = ne // 2
+    up = _Grid(ne, 3, shape=(ne, ne, ne - nz), h=h, origin=(0.0, 0.0, nz * h))
+    lo = _Grid(ne, 3, shape=(ne, ne, nz), h=h, origin=(0.0, 0.0, 0.0))
+    Ke, Kl, Me, Ce = q1_element_matrices(3, h, E, poisson)
+    Gd, Dz = q1_flow_matrices(h)
+    tau = h * h / (12.0 * nu)
+    blocks = {
+        (0, 0): up.bsr(up.assemble(Ke, 3, 3), 3, 3),
+        (1, 1): lo.bsr(lo.assemble(_vector_cell(Kl, 3), 3, 3), 3, 3),
+        (2, 2): lo.bsr(lo.assemble(nu * _vector_cell(Kl, 3), 3, 3), 3, 3),
+        (3, 3): lo.bsr(lo.assemble(-tau * Kl, 1, 1), 1, 1),
+        (2, 3): lo.bsr(lo.assemble(Gd, 3, 1), 3, 1),
+        (3, 2): lo.bsr(lo.assemble(Gd.T.copy(), 1, 3), 1, 3),
+        (2, 1): lo.bsr(lo.assemble(eta * _vector_cell(Dz, 3), 3, 3), 3, 3),
+    }
+    Mup = _interface_nodes(up, 0)        # S side of the interface (local layer 0)
+    Mlo = _interface_nodes(lo, nz)       # fluid / mesh side (top layer of the lower half)
+    _add_to_grid_block(up, blocks[(0, 0)].vals, Mup, gamma, 3)
+    _add_to_grid_block(lo, blocks[(2, 2)].vals, Mlo, 2 * gamma, 3)
+    _add_to_grid_block(lo, blocks[(1, 1)].vals, Mlo, gamma, 3)
+    # S <-> Fu: upper layer-0 node (i, j) pairs with lower layer-nz node (i, j)
+    shift = nz * lo.stride[2]
+    Mx = Mlo.tocoo()
+    rows_up = Mx.row - shift
+    import scipy.sparse as sp
+    Msf = sp.csr_matrix((Mx.data, (rows_up, Mx.col)), shape=(up.nnodes, lo.nnodes))
+    blocks[(0, 2)] = _node_bsr(Msf, 3, -gamma)
+    blocks[(2, 0)] = _node_bsr(Msf.T.tocsr(), 3, -gamma)
+    blocks[(1, 2)] = _node_bsr(Mlo, 3, -gamma)
+    dS = up.ijk[:, 2] == (ne - nz)
+    xi, yi, zi = lo.ijk[:, 0], lo.ijk[:, 1], lo.ijk[:, 2]
+    lateral = (xi == 0) | (xi == ne) | (yi == 0) | (yi == ne)
+    dG = lateral | (zi == 0)
+    dF = lateral
+    dP = zi == 0
+    _dirichlet_fields(blocks, [dS, dG, dF, dP])
+    fields = [
+        Field("structure", 3, up.nnodes, 3, up.coords, "rbm", 0.0, np.nonzero(dS)[0]),
+        Field("mesh", 3, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dG)[0]),
+        Field("fluid_velocity", 3, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dF)[0]),
+        Field("fluid_pressure", 1, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dP)[0]),
+    ]
+    rng = np.random.default_rng(seed)
+    rhs = rng.standard_normal(sum(f.ndofs for f in fields))
+    off = 0
+    for f in fields:
+        d = (f.dirichlet_nodes[:, None] * f.b + np.arange(f.b)[None, :]).ravel()
+        rhs[off + d] = 0.0
+        off += f.ndofs
+    return BlockSystem(fields, blocks, rhs, name=f"fsi_box_ne{ne}", meta=dict(ne=ne, nu=nu, seed=seed))
 
 
 def batch_sizes_log_uniform(nsys=256, lo=12, hi=48, seed=3):

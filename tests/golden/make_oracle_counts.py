@@ -4,7 +4,7 @@ residuals of the FP64 oracle on the full-size synthetic workloads.
 Calls only the oracle and the seeded input generators (no GPU code).  The
 stored counts pin the CUDA path at full size (iterations within +-1) and
 scale the oracle's timed CPU sample in bench.py.
-Run:  PYTHONPATH=. python tests/golden/make_oracle_counts.py
+Run:  PYTHONPATH=. python tests/golden/make_oracle_counts.py [workload ...]
 """
 import json
 import os
@@ -20,26 +20,35 @@ from paper_1605_01522_gb300 import inputs  # noqa: E402
 # workload name -> (generator, solver parameters)
 WORKLOADS = {
     "coupled_box_3d_ne64_f3": (lambda: inputs.coupled_box_3d(ne=64, nfields=3, seed=1),
-                               dict(max_levels=5, coarse_max=1000)),
+                               dict(max_levels=5, coarse_max=1000),
+                               {"bgs_amg": {}, "amg_bgs": {}, "simple": {}}),
+    "fsi_box_ne48": (lambda: inputs.fsi_box(ne=48, seed=2), dict(max_levels=5, coarse_max=1000),
+                     {"bgs_amg": {}, "simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
 }
 
 
 def main():
-    out = {}
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_counts.json")
-    for name, (gen, kw) in WORKLOADS.items():
+    only = sys.argv[1:]
+    out = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            out = json.load(f)
+    for name, (gen, kw, pcs) in WORKLOADS.items():
+        if only and name not in only:
+            continue
         s = gen()
         A = s.scipy_blocks()
         D = precond.assemble(A, s.nfields)
         specs = [amg.FieldSpec.of(f) for f in s.fields]
-        for pc in ("bgs_amg", "amg_bgs", "simple"):
+        for pc, extra in pcs.items():
             t0 = time.time()
-            M = precond.Preconditioner(A, specs, precond.Params(pc, **kw))
+            M = precond.Preconditioner(A, specs, precond.Params(pc, **kw, **extra))
             t1 = time.time()
             r = krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=400)
             t2 = time.time()
             out[f"{name}/{pc}"] = dict(iters=r.iters, relres=r.relres, converged=bool(r.converged),
-                                       setup_s=round(t1 - t0, 2), solve_s=round(t2 - t1, 2), **kw)
+                                       setup_s=round(t1 - t0, 2), solve_s=round(t2 - t1, 2), **kw, **extra)
             print(name, pc, out[f"{name}/{pc}"], flush=True)
     with open(path, "w") as f:
         json.dump(out, f, indent=1, sort_keys=True)

@@ -65,6 +65,48 @@ def test_fullsize_fp32_preconditioner(pc):
     assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
 
 
+_FSI = {}
+
+
+def _fsi():
+    if "s" not in _FSI:
+        s = inputs.fsi_box(ne=48, seed=2)
+        _FSI["s"] = s
+        _FSI["D"] = precond.assemble(s.scipy_blocks(), 4)
+    return _FSI["s"], _FSI["D"]
+
+
+FSI_SIMPLE = dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32p"])
+def test_fullsize_split_box_saddle_simple(prec):
+    s, D = _fsi()
+    ref = _counts()["fsi_box_ne48/simple"]
+    with mfs.Solver(s, precond="simple", precision=prec, **KW, **FSI_SIMPLE) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK
+    assert np.linalg.norm(s.rhs - D @ x) <= 1e-8 * np.linalg.norm(s.rhs)
+    if prec == "fp64":
+        assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    else:
+        assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
+
+
+def test_fullsize_split_box_bgs_fails_like_the_oracle():
+    """BGS(AMG) on the saddle system does not reach 1e-8 in 400 iterations in
+    the oracle (Sec. 4.1: BGS needs dominant diagonal blocks); the GPU must
+    report the same failure with a similar residual."""
+    s, D = _fsi()
+    ref = _counts()["fsi_box_ne48/bgs_amg"]
+    assert not ref["converged"]
+    with mfs.Solver(s, precond="bgs_amg", max_iters=ref["iters"], **KW) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+    assert rc == mfs.ERR_NOT_CONVERGED and info["iters"] == ref["iters"]
+    assert 0.5 * ref["relres"] <= info["true_relres"] <= 2.0 * ref["relres"]
+
+
 def test_fullsize_matvec_sampled_rows():
     s, D = _system()
     rng = np.random.default_rng(9)

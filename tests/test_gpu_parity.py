@@ -37,6 +37,8 @@ def _small(name):
         return inputs.coupled_box_3d(ne=10, nfields=3), dict(max_levels=4, coarse_max=150)
     if name == "3d2":
         return inputs.coupled_box_3d(ne=13, nfields=2), dict(max_levels=3, coarse_max=100)
+    if name == "fsi":
+        return inputs.fsi_box(ne=8), dict(max_levels=3, coarse_max=100)
     raise KeyError(name)
 
 
@@ -66,7 +68,10 @@ CASES = [("2d", "bgs_amg", {}), ("2d", "amg_bgs", {}), ("2d", "simple", {}),
          ("3d", "simple", dict(simple_group=[0, 1, 1])), ("3d", "bgs_amg", dict(bgs_order="fwd")),
          ("3d", "bgs_amg", dict(bgs_order="sym", bgs_sweeps=2)), ("3d2", "amg_bgs", dict(bgs_order="sym")),
          ("3d2", "simple", dict(simple_approx="diag")), ("3d2", "bgs_amg", dict(smoother="jacobi", jacobi_sweeps=2)),
-         ("3d2", "bgs_amg", dict(cheb_degree=3))]
+         ("3d2", "bgs_amg", dict(cheb_degree=3)),
+         ("fsi", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag")),
+         ("fsi", "simple", dict(simple_group=[0, 0, 0, 1])), ("fsi", "bgs_amg", {})]
+FSI = [c for c in CASES if c[0] == "fsi"]
 
 
 @pytest.mark.parametrize("name,pc,extra", CASES)
@@ -82,7 +87,7 @@ def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
             assert err <= APPLY_TOL, err
 
 
-@pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8])
+@pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI)
 def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     s, kw = _small(name)
     okw = {k: v for k, v in extra.items() if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps")}
@@ -98,11 +103,12 @@ def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     assert np.linalg.norm(x - ro.x) <= 1e-6 * np.linalg.norm(ro.x)
 
 
-@pytest.mark.parametrize("name,pc", [("2d", "bgs_amg"), ("3d", "bgs_amg"), ("3d", "amg_bgs"), ("3d", "simple")])
-def test_solve_fp32_preconditioner(name, pc):
+@pytest.mark.parametrize("name,pc,extra", [("2d", "bgs_amg", {}), ("3d", "bgs_amg", {}), ("3d", "amg_bgs", {}),
+                                           ("3d", "simple", {}), ("fsi", "bgs_amg", {})] + FSI[:1])
+def test_solve_fp32_preconditioner(name, pc, extra):
     s, kw = _small(name)
-    ro, D = _oracle_solve(s, kw, pc, {})
-    with mfs.Solver(s, precond=pc, precision="fp32p", **kw) as lib:
+    ro, D = _oracle_solve(s, kw, pc, extra)
+    with mfs.Solver(s, precond=pc, precision="fp32p", **kw, **extra) as lib:
         x, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
         x = x.cpu().numpy()
     true = np.linalg.norm(s.rhs - D @ x) / np.linalg.norm(s.rhs)
