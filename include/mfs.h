@@ -252,7 +252,8 @@ int mfs_kernel_stats(struct mfs_handle *h, double *out, int cap, int reset);
  * kernel variant and size, sorted by summed time: [cls*100000 + sig, rows,
  * launches, ms, algorithmic bytes, algorithmic flops], where for SpMV (cls 0) and smoothing
  * (cls 1) sig = layout*1000 + br*100 + bc*10 + (float64 ? 1 : 0) with layout
- * 0 = SELL-32 / 1 = warp-per-row BSR, and rows = block rows; for the other
+ * 0 = SELL-32, 1 = warp-per-row BSR, 2 = merged coupled rows, 3 = SELL-32 with
+ * 4 slots in flight (the layout autotuner's choices), and rows = block rows; for the other
  * classes sig is a kernel id and rows the vector length.  Returns the number
  * of rows written (cap = length of out).  Cleared by mfs_kernel_stats with
  * reset != 0. */

@@ -33,7 +33,8 @@ struct HookScope {
 };
 
 template <typename T> int sparse_sig(const Sell &A) {
-  return A.kind * 1000 + A.br * 100 + A.bc * 10 + (sizeof(T) == 8 ? 1 : 0);
+  const int layout = A.kind == 0 && A.unroll == 4 ? 3 : A.kind;  // 3: SELL-32 with 4 slots in flight
+  return layout * 1000 + A.br * 100 + A.bc * 10 + (sizeof(T) == 8 ? 1 : 0);
 }
 
 // algorithmic bytes of one pass over a block matrix: values + block-column
@@ -46,7 +47,7 @@ inline unsigned grid_for(int64_t n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
 }
 
-template <int BR, int BC, typename T>
+template <int BR, int BC, typename T, int U>
 __device__ __forceinline__ void sell_row(const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
                                          const int32_t *__restrict__ col, const T *__restrict__ val,
                                          const T *__restrict__ x, int64_t row, T (&acc)[BR]) {
@@ -58,9 +59,8 @@ __device__ __forceinline__ void sell_row(const int32_t *__restrict__ sp, const i
   const T *vp = val + base * (BR * BC * 32) + lane;
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = T(0);
-  // small blocks: more slots in flight to cover the index -> x dependency
-  constexpr int kUnroll = BR * BC <= 3 ? 4 : 2;
-#pragma unroll kUnroll
+  // U slots in flight per thread (chosen per matrix by the layout autotuner)
+#pragma unroll U
   for (int t = 0; t < len; ++t) {
     const int64_t c = __ldg(cp + (int64_t)t * 32);
     T xv[BC];
@@ -144,7 +144,7 @@ k_smooth_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__rest
   }
 }
 
-template <int BR, int BC, typename T>
+template <int BR, int BC, typename T, int U>
 __global__ void __launch_bounds__(kThreads)
 k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
        const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x, T *y,
@@ -152,7 +152,7 @@ k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ 
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= nbr) return;
   T acc[BR];
-  sell_row<BR, BC, T>(sp, rl, col, val, x, row, acc);
+  sell_row<BR, BC, T, U>(sp, rl, col, val, x, row, acc);
   T *yp = y + row * BR;
   if (z != nullptr) {
     const T *zp = z + row * BR;
@@ -203,7 +203,7 @@ k_spmv_rows(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restri
   for (int r = 0; r < BR; ++r) y[row * BR + r] = acc[r];
 }
 
-template <int BR, typename T>
+template <int BR, typename T, int U>
 __global__ void __launch_bounds__(kThreads)
 k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
          const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ dinv,
@@ -212,7 +212,7 @@ k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict_
   const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (row >= nbr) return;
   T acc[BR];
-  sell_row<BR, BR, T>(sp, rl, col, val, x, row, acc);
+  sell_row<BR, BR, T, U>(sp, rl, col, val, x, row, acc);
 #pragma unroll
   for (int r = 0; r < BR; ++r) {
     const int64_t i = row * BR + r;
@@ -239,7 +239,7 @@ __global__ void k_smooth_first(int64_t n, const T *__restrict__ dinv, const T *_
 // factors when they fit (staged == 1), which keeps the warp's sequential
 // steps off global-memory latency.
 template <typename T>
-__global__ void __launch_bounds__(1024)
+__global__ void __launch_bounds__(512)
 k_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ perm,
            const T *__restrict__ b, T *__restrict__ x, int staged) {
   extern __shared__ double sm[];
@@ -257,17 +257,26 @@ k_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ p
   for (int k0 = 0; k0 < n; k0 += 32) {
     const int nb = min(32, n - k0);
     if (warp == 0) {
+      // this lane's row of the 32 x 32 diagonal block, loaded up front
+      double Lr[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) Lr[c] = (c < nb && lane < nb) ? lu[(int64_t)(k0 + c) * n + k0 + lane] : 0.0;
       double yv = lane < nb ? y[k0 + lane] : 0.0;
-      for (int c = 0; c < nb; ++c) {
-        const double yc = __shfl_sync(0xffffffffu, yv, c);
-        if (lane > c && lane < nb) yv -= lu[(int64_t)(k0 + c) * n + k0 + lane] * yc;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        if (c < nb) {
+          const double yc = __shfl_sync(0xffffffffu, yv, c);
+          if (lane > c && lane < nb) yv -= Lr[c] * yc;
+        }
       }
       if (lane < nb) y[k0 + lane] = yv;
     }
     __syncthreads();
     for (int i = k0 + nb + tid; i < n; i += nt) {
       double s = 0.0;
-      for (int c = 0; c < nb; ++c) s += lu[(int64_t)(k0 + c) * n + i] * y[k0 + c];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)  // all 32 loads in flight at once
+        if (c < nb) s += lu[(int64_t)(k0 + c) * n + i] * y[k0 + c];
       y[i] -= s;
     }
     __syncthreads();
@@ -277,18 +286,26 @@ k_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ p
   for (int k0 = last; k0 >= 0; k0 -= 32) {
     const int nb = min(32, n - k0);
     if (warp == 0) {
+      double Ur[32];
+#pragma unroll
+      for (int c = 0; c < 32; ++c) Ur[c] = (c < nb && lane < nb) ? lu[(int64_t)(k0 + c) * n + k0 + lane] : 1.0;
       double yv = lane < nb ? y[k0 + lane] : 0.0;
-      for (int c = nb - 1; c >= 0; --c) {
-        if (lane == c) yv /= lu[(int64_t)(k0 + c) * n + k0 + c];
-        const double yc = __shfl_sync(0xffffffffu, yv, c);
-        if (lane < c) yv -= lu[(int64_t)(k0 + c) * n + k0 + lane] * yc;
+#pragma unroll
+      for (int c = 31; c >= 0; --c) {
+        if (c < nb) {
+          if (lane == c) yv /= Ur[c];
+          const double yc = __shfl_sync(0xffffffffu, yv, c);
+          if (lane < c) yv -= Ur[c] * yc;
+        }
       }
       if (lane < nb) y[k0 + lane] = yv;
     }
     __syncthreads();
     for (int i = tid; i < k0; i += nt) {
       double s = 0.0;
-      for (int c = 0; c < nb; ++c) s += lu[(int64_t)(k0 + c) * n + i] * y[k0 + c];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < nb) s += lu[(int64_t)(k0 + c) * n + i] * y[k0 + c];
       y[i] -= s;
     }
     __syncthreads();
@@ -529,9 +546,15 @@ void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStre
                            A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
     return;
   }
-  MFS_BLOCK_DISPATCH(A.br, A.bc,
-                     (k_spmv<BR_, BC_, T><<<grid_for(A.nbr), kThreads, 0, s>>>(
-                         A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+  if (A.unroll == 4) {
+    MFS_BLOCK_DISPATCH(A.br, A.bc,
+                       (k_spmv<BR_, BC_, T, 4><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+  } else {
+    MFS_BLOCK_DISPATCH(A.br, A.bc,
+                       (k_spmv<BR_, BC_, T, 2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+  }
 }
 
 #define MFS_SQUARE_DISPATCH(BRV, CALL)                                  \
@@ -586,8 +609,13 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
                                   A.nbr, A.sp, A.col, v, dinv, b, x, xout, d, c1, c2)));
     return;
   }
-  MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T><<<grid_for(A.nbr), kThreads, 0, s>>>(
-                                A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+  if (A.unroll == 4) {
+    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 4><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+  } else {
+    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+  }
 }
 
 template <typename T>
@@ -605,7 +633,7 @@ void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   // stage the factors in shared memory when y and LU fit in 200 KB
   const int staged = (size_t)lu.n * (lu.n + 1) * sizeof(double) <= 200 * 1024 ? 1 : 0;
   const size_t smem = (size_t)lu.n * (staged ? lu.n + 1 : 1) * sizeof(double);
-  const int threads = lu.n <= 64 ? 256 : 1024;
+  const int threads = lu.n <= 64 ? 256 : 512;
   k_lu_solve<T><<<1, threads, smem, s>>>(lu.n, lu.lu, lu.perm, b, x, staged);
 }
 

@@ -19,6 +19,7 @@ struct Sell {
                                //    few rows: restriction, coarse levels); then sp is
                                //    the row pointer, col the block columns and the
                                //    values are contiguous per block (br*bc, row-major)
+  int unroll = 2;              // SELL-32: slots of a row in flight per thread (2 or 4)
   int br = 0, bc = 0;
   int64_t nbr = 0, nbc = 0;
   int64_t nslices = 0, nslots = 0;

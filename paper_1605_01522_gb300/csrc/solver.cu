@@ -19,6 +19,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <memory>
 #include <stdexcept>
 #include <string>
@@ -49,13 +51,13 @@ void set_last_error(const char *msg) { g_last_error = msg; }
   } while (0)
 
 struct Arena {
-  std::vector<void *> ptrs;
+  std::vector<std::pair<void *, int64_t>> ptrs;
   int64_t bytes = 0;
   template <typename T> T *alloc(int64_t count) {
     if (count <= 0) return nullptr;
     void *p = nullptr;
     MFS_CUDA(cudaMalloc(&p, (size_t)count * sizeof(T)));
-    ptrs.push_back(p);
+    ptrs.push_back({p, count * (int64_t)sizeof(T)});
     bytes += count * (int64_t)sizeof(T);
     return (T *)p;
   }
@@ -69,17 +71,29 @@ struct Arena {
     if (p) MFS_CUDA(cudaMemset(p, 0, (size_t)count * sizeof(T)));
     return p;
   }
+  void release(const void *p) {
+    if (!p) return;
+    for (size_t k = 0; k < ptrs.size(); ++k)
+      if (ptrs[k].first == p) {
+        cudaFree(ptrs[k].first);
+        bytes -= ptrs[k].second;
+        ptrs.erase(ptrs.begin() + (long)k);
+        return;
+      }
+  }
   ~Arena() {
-    for (void *p : ptrs) cudaFree(p);
+    for (auto &q : ptrs) cudaFree(q.first);
   }
 };
 
-// Layout choice: rows longer than this many blocks on average, or matrices
-// with fewer block rows than this, get one warp per row.
-constexpr double kWarpRowMinAvg = 40.0;
-constexpr int64_t kWarpRowMaxRows = 8192;
+// Layout autotuning: matrices with at least kTuneMinRows block rows are built
+// in both layouts (SELL-32, one thread per block row; plain BSR, one warp per
+// block row), each timed with CUDA events, and the faster is kept.  Smaller
+// matrices are latency bound and take the warp layout.  Decisions are cached
+// per (block shape, rows, blocks, precision) for the life of the process.
+constexpr int64_t kTuneMinRows = 2048;
 
-static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32) {
+static dev::Sell upload_layout(Arena &ar, const HBsr &A, bool want64, bool want32, int kind) {
   dev::Sell S;
   S.br = A.br;
   S.bc = A.bc;
@@ -88,8 +102,7 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   S.nnzb = A.nnzb();
   if (A.nbr == 0) return S;
   const int bs = A.br * A.bc;
-  const double avg = (double)A.nnzb() / (double)A.nbr;
-  if (avg > kWarpRowMinAvg || A.nbr < kWarpRowMaxRows) {
+  if (kind == 1) {
     // plain BSR, one warp per block row
     if (A.nnzb() > INT32_MAX) throw SetupError(MFS_ERR_INVALID, "matrix too large for 32-bit block offsets");
     S.kind = 1;
@@ -139,6 +152,79 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   if (want64) S.v64 = ar.upload(v64);
   if (want32) S.v32 = ar.upload(v32);
   return S;
+}
+
+template <typename T> static float time_spmv(const dev::Sell &S, cudaStream_t st) {
+  T *x = nullptr, *y = nullptr;
+  MFS_CUDA(cudaMallocAsync((void **)&x, (size_t)std::max<int64_t>(1, S.ncols()) * sizeof(T), st));
+  MFS_CUDA(cudaMallocAsync((void **)&y, (size_t)std::max<int64_t>(1, S.nrows()) * sizeof(T), st));
+  MFS_CUDA(cudaMemsetAsync(x, 0, (size_t)S.ncols() * sizeof(T), st));
+  cudaEvent_t e0, e1;
+  MFS_CUDA(cudaEventCreate(&e0));
+  MFS_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rep = 0; rep < 4; ++rep) {
+    MFS_CUDA(cudaEventRecord(e0, st));
+    dev::spmv<T>(S, x, y, T(1), T(0), nullptr, st);
+    MFS_CUDA(cudaEventRecord(e1, st));
+    MFS_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    MFS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (rep > 0) best = std::min(best, ms);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(x, st);
+  cudaFreeAsync(y, st);
+  MFS_CUDA(cudaStreamSynchronize(st));
+  return best;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int64_t, int64_t, int>, int> g_tune;
+
+static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32) {
+  if (A.nbr < kTuneMinRows) return upload_layout(ar, A, want64, want32, 1);
+  const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb(), want32 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      dev::Sell S = upload_layout(ar, A, want64, want32, it->second == 2 ? 1 : 0);
+      if (it->second == 1) S.unroll = 4;
+      return S;
+    }
+  }
+  dev::Sell a = upload_layout(ar, A, want64, want32, 0);
+  dev::Sell b = upload_layout(ar, A, want64, want32, 1);
+  cudaStream_t st;
+  MFS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  MFS_CUDA(cudaStreamSynchronize(0));  // uploads and memsets of the legacy stream
+  // candidates: SELL-32 with 2 or 4 slots in flight, BSR warp per row
+  float t[3];
+  dev::Sell a4 = a;
+  a4.unroll = 4;
+  try {
+    t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
+    t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
+    t[2] = want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st);
+  } catch (...) {
+    cudaStreamDestroy(st);
+    throw;
+  }
+  cudaStreamDestroy(st);
+  const int best = t[0] <= t[1] && t[0] <= t[2] ? 0 : (t[1] <= t[2] ? 1 : 2);
+  dev::Sell &loser = best == 2 ? a : b;
+  ar.release(loser.sp);
+  ar.release(loser.rl);
+  ar.release(loser.col);
+  ar.release(loser.v64);
+  ar.release(loser.v32);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best;
+  }
+  return best == 0 ? a : (best == 1 ? a4 : b);
 }
 
 static dev::DenseLU upload_lu(Arena &ar, const HDenseLU &lu) {
@@ -871,8 +957,7 @@ std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, 
         }
       }
     dev::RowMerged R;
-    R.M = upload_sell(ar, M, true, false);
-    if (R.M.kind != 0) return {};
+    R.M = upload_layout(ar, M, true, false, 0);
     R.nb = nf;
     for (int j = 0; j < nf; ++j) {
       R.b[j] = b[j];

@@ -44,7 +44,7 @@ def kernel_name(key: int) -> str:
         br, rest = divmod(rest, 100)
         bc, f64 = divmod(rest, 10)
         base = "spmv" if cls == 0 else "smooth"
-        layout = {0: "sell", 1: "warp", 2: "rows"}.get(kind, str(kind))
+        layout = {0: "sell", 1: "warp", 2: "rows", 3: "sell4"}.get(kind, str(kind))
         return f"{base}_{layout}<{br}x{bc},{'f64' if f64 else 'f32'}>"
     return _OTHER.get(cls, {}).get(sig, f"class{cls}_id{sig}")
 
