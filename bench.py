@@ -133,6 +133,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def reduce_timing(elapsed, steps, world, dist=None, device=None):
+    """Replicas: every rank solves its own copy of the workload; the job's
+    time is the slowest rank's (all_reduce MAX) and its throughput counts
+    every rank's solves.  Returns (solves per second, slowest elapsed)."""
+    if dist is not None and world > 1:
+        import torch
+        t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return world * steps / elapsed, elapsed
+
+
 def kernel_source_digest(kernel):
     """sha256 of the device source of a kernel variant family (its __global__
     function and the row helper it calls), to tell whether stored ncu
@@ -311,9 +323,7 @@ def run_mfs(args, rank, world):
     elapsed = ev0.elapsed_time(ev1) / 1e3
     if dist:
         dist.barrier()
-        t = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    value, elapsed = reduce_timing(elapsed, args.steps, world, dist, dev)
     detail = lib.kernel_detail()
     stats = lib.kernel_stats(reset=True)
     # true residual, recomputed through the library's FP64 matvec (device)
@@ -366,7 +376,6 @@ def run_mfs(args, rank, world):
                      "traffic": ncu_traffic(r[0], r[1]), "timed": "warm-up solve, every launch timed"}
     stats = stats_all
     launches_total = sum(v[0] for v in stats_all.values()) * args.steps
-    value = world * args.steps / elapsed
     if rank != 0:
         return
     cpu = None
