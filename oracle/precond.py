@@ -18,6 +18,8 @@ method run for k_max sweeps from x^(0) = 0 (Sec. 7.1 uses k_max = 1):
   A~_11 is SIMPLEC's diagonal of absolute row sums of the merged A_11 block
   (read as the sum of absolute entries of each row) or, optionally, diag(A_11).
   S~ = A_22 - A_21 A~_11^-1 A_12 is formed explicitly.
+* monolithic AMG(SIMPLE) (Sec. 4.3): the same V-cycle with a SIMPLE step as
+  level smoother (see MonoAMGSimple).
 * monolithic AMG(BGS) (Sec. 4.3): block-diagonal transfers diag(P_i),
   diag(R_i) from the single-field hierarchies, coarse blocks
   A^{l+1}_ij = R_i A^l_ij P_j, a V-cycle whose level smoother is a BGS sweep
@@ -257,6 +259,62 @@ class MonoAMG:
         return self.cycle(0, list(b))
 
 
+class MonoAMGSimple(MonoAMG):
+    """Monolithic AMG(SIMPLE) (Sec. 4.3): the coupled V-cycle of AMG(BGS) with a
+    SIMPLE step as level smoother.  On level l, with residual r = b - A^l x:
+    predictor  d_1 = one BGS sweep over the predictor fields, each block solve
+               one application of the single-field smoother S^l_i from zero;
+    Schur      d_2 = one application of a Chebyshev smoother on the explicit
+               S~^l = A^l_22 - A^l_21 (A~^l_11)^-1 A^l_12 (its own lambda), from zero,
+               with right-hand side r_2 - A^l_21 d_1;
+    update     d_1 -= (A~^l_11)^-1 A^l_12 d_2;  x += d.
+    A~^l_11 is SIMPLEC / diagonal of the level's merged predictor block; one
+    Schur field."""
+
+    def __init__(self, blocks, specs, prm, nf, g1, g2):
+        super().__init__(blocks, specs, prm, nf)
+        if len(g2) != 1:
+            raise ValueError("AMG(SIMPLE) takes one Schur field")
+        self.g1, self.g2 = g1, g2
+        self.dt, self.S = [], []
+        for l in range(len(self.grp.levels) - 1):
+            dt = simple_dtilde(self.A[l], g1, prm.simple_approx)
+            S = simple_schur(self.A[l], g1, g2, dt)[(0, 0)]
+            fl = amg.FieldLevel(S, specs[g2[0]].b)
+            fl.lam = amg.power_lambda(fl.A, fl.dinv, prm.seed)
+            self.dt.append(dt)
+            self.S.append(fl)
+
+    def smooth(self, l, b, x):
+        lv, A, sp_ = self.grp.levels[l], self.A[l], self.prm.smoother
+        g1, k = self.g1, self.g2[0]
+        for _ in range(self.prm.bgs_sweeps):
+            Ax = coupled_matvec(A, x, self.nf)
+            r = [b[i] - Ax[i] for i in range(self.nf)]
+            d = {}
+            for seq in sweep_orders(self.prm.bgs_order, len(g1)):
+                for jj in seq:
+                    i = g1[jj]
+                    c = r[i].copy()
+                    for j in d:
+                        if j != i and (i, j) in A:
+                            c = c - A[(i, j)] @ d[j]
+                    d[i] = (d[i] if i in d else 0.0) + smooth(lv[i], c - (A[(i, i)] @ d[i] if i in d else 0.0),
+                                                             np.zeros_like(c), sp_)
+            c2 = r[k].copy()
+            for j in g1:
+                if (k, j) in A:
+                    c2 = c2 - A[(k, j)] @ d[j]
+            d2 = smooth(self.S[l], c2, np.zeros_like(c2), sp_)
+            for jj, j in enumerate(g1):
+                if (j, k) in A:
+                    d[j] = d[j] - (A[(j, k)] @ d2) / self.dt[l][jj]
+            for j in g1:
+                x[j] = x[j] + d[j]
+            x[k] = x[k] + d2
+        return x
+
+
 class Preconditioner:
     """z = M^-1 v for the whole coupled vector (field-major concatenation)."""
 
@@ -269,6 +327,13 @@ class Preconditioner:
             self.groups = [self.grp]
         elif prm.precond == "amg_bgs":
             self.op = MonoAMG(blocks, specs, prm, nf)
+            self.grp = self.op.grp
+            self.groups = [self.grp]
+        elif prm.precond == "amg_simple":
+            grp_of = prm.simple_group or [0] * (nf - 1) + [1]
+            g1 = [i for i in range(nf) if grp_of[i] == 0]
+            g2 = [i for i in range(nf) if grp_of[i] == 1]
+            self.op = MonoAMGSimple(blocks, specs, prm, nf, g1, g2)
             self.grp = self.op.grp
             self.groups = [self.grp]
         elif prm.precond == "simple":

@@ -5,15 +5,17 @@ BGS with exact block solves must equal a dense block-triangular solve
 reproduce A^-1 (Sec. 4.2: M_SIMPLE then equals A); AMG(BGS) must reduce to the
 single-field V-cycle for one field and to BGS(AMG)'s block-diagonal V-cycles
 without coupling, and its coarse blocks must equal dense R_i A_ij P_j
-(Sec. 4.3); FGMRES must reach the dense solution and take one iteration
-with an exact preconditioner.
+(Sec. 4.3); AMG(SIMPLE) must reduce to BGS(AMG) without coupling and its
+level smoother, with converged inner solves, must apply M_SIMPLE^-1 (Sec. 4.2
+factorisation on the level); FGMRES must reach the dense solution and take
+one iteration with an exact preconditioner.
 """
 import numpy as np
 import scipy.sparse as sp
 import pytest
 
 from oracle import amg, precond, krylov
-from oracle.cycles import vcycle
+from oracle.cycles import SmootherParams, vcycle
 from paper_1605_01522_gb300 import inputs
 
 
@@ -167,6 +169,52 @@ def test_amg_bgs_coarse_blocks_are_blockwise_galerkin():
     assert np.allclose(_dense(mono.A[1], 3), P.T @ D @ P, atol=1e-12)
 
 
+def test_amg_simple_without_coupling_equals_bgs_amg():
+    """No coupling: S~^l = A^l_22, the predictor is field 1's smoother and the
+    level smoother is the block-diagonal one of BGS(AMG)'s V-cycles."""
+    s, A = _sys2(ne=10)
+    A0 = {k: v for k, v in A.items() if k[0] == k[1]}
+    specs = [amg.FieldSpec.of(f) for f in s.fields]
+    sizes = [f.ndofs for f in s.fields]
+    b = np.random.default_rng(8).standard_normal(sum(sizes))
+    for approx in ("absrowsum", "diag"):
+        za = precond.Preconditioner(A0, specs, precond.Params("amg_simple", max_levels=3, coarse_max=0,
+                                                             simple_approx=approx))(b)
+        zb = precond.Preconditioner(A0, specs, precond.Params("bgs_amg", max_levels=3, coarse_max=0))(b)
+        assert np.allclose(za, zb, rtol=1e-12, atol=1e-13 * np.abs(zb).max())
+
+
+def _chain(n, diag, off):
+    return sp.diags([np.full(n - 1, off), np.full(n, diag), np.full(n - 1, off)], [-1, 0, 1]).tocsr()
+
+
+@pytest.mark.parametrize("approx", ["absrowsum", "diag"])
+def test_amg_simple_level_smoother_applies_simple_factorisation(approx):
+    """Level smoother of AMG(SIMPLE) with converged single-field solves (60
+    Jacobi sweeps on diagonally dominant blocks): d = M_SIMPLE^-1 r with
+    M_SIMPLE = [A11 0; A21 S~][I A~11^-1 A12; 0 I], S~ = A22 - A21 A~11^-1 A12.
+    A12 and A21 are unrelated (not transposes), so swapped or transposed
+    coupling blocks, a wrong sign or a dropped term change the result."""
+    n = 40
+    rng = np.random.default_rng(9)
+    A = {(0, 0): _chain(n, 4.0, -1.0), (1, 1): _chain(n, 5.0, -1.0),
+         (0, 1): sp.random(n, n, density=0.08, random_state=np.random.RandomState(1), format="csr") * 0.6,
+         (1, 0): sp.random(n, n, density=0.08, random_state=np.random.RandomState(2), format="csr") * -0.5}
+    specs = [amg.FieldSpec(1, 1, "const"), amg.FieldSpec(1, 1, "const")]
+    prm = precond.Params("amg_simple", max_levels=2, coarse_max=0, simple_approx=approx,
+                         smoother=SmootherParams("jacobi", omega=1.0, sweeps=60))
+    mono = precond.MonoAMGSimple(A, specs, prm, 2, [0], [1])
+    D = _dense(A, 2)
+    A11, A12, A21, A22 = D[:n, :n], D[:n, n:], D[n:, :n], D[n:, n:]
+    dt = np.abs(A11).sum(1) if approx == "absrowsum" else np.diag(A11)
+    St = A22 - A21 @ np.diag(1 / dt) @ A12
+    M = np.block([[A11, np.zeros((n, n))], [A21, St]]) @ np.block(
+        [[np.eye(n), np.diag(1 / dt) @ A12], [np.zeros((n, n)), np.eye(n)]])
+    r = rng.standard_normal(2 * n)
+    x = mono.smooth(0, [r[:n], r[n:]], [np.zeros(n), np.zeros(n)])
+    assert np.allclose(np.concatenate(x), np.linalg.solve(M, r), rtol=1e-10, atol=1e-10)
+
+
 def test_fgmres_unpreconditioned_reaches_dense_solution():
     rng = np.random.default_rng(8)
     n = 60
@@ -194,7 +242,7 @@ def test_fgmres_exact_preconditioner_one_iteration_and_estimate():
     assert abs(r2.est - r2.relres) <= 1e-6 * r2.relres + 1e-14
 
 
-@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple"])
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple", "amg_simple"])
 def test_preconditioned_solve_iterations_grow_mildly(pc):
     """Trend of Sec. 7 (weak-scaling tables): multilevel block preconditioners
     keep the iteration count nearly flat under refinement."""
