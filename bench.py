@@ -518,7 +518,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mfs", choices=["mfs", "reference"])
-    ap.add_argument("--precond", default="bgs_amg", choices=["bgs_amg", "amg_bgs", "simple"])
+    ap.add_argument("--precond", default="bgs_amg", choices=["bgs_amg", "amg_bgs", "simple", "amg_simple"])
     ap.add_argument("--precision", default="fp32p", choices=["fp32p", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")

@@ -13,7 +13,12 @@
  *                block, explicit approximate Schur complement (Sec. 4.2);
  *   MFS_AMG_BGS  monolithic AMG with block-diagonal transfers, blockwise
  *                Galerkin coarse blocks and block Gauss-Seidel level smoothing
- *                (Sec. 4.3).
+ *                (Sec. 4.3);
+ *   MFS_AMG_SIMPLE the same monolithic V-cycle with a SIMPLE step as level
+ *                smoother (Sec. 4.3): per level, one BGS sweep of the
+ *                single-field smoothers over the predictor fields, one
+ *                smoother application on the explicit level Schur complement
+ *                S~^l (one Schur field), then the SIMPLE update.
  * Every solve-phase step runs in this library's CUDA kernels; there is no CPU
  * fallback.  The AMG setup (strength graph, aggregation, tentative and
  * smoothed prolongators, Galerkin products, power iteration) runs in this
@@ -62,7 +67,7 @@ enum mfs_status {
   MFS_ERR_SETUP = -7           /* aggregation could not coarsen a field */
 };
 
-enum mfs_precond { MFS_BGS_AMG = 0, MFS_SIMPLE = 1, MFS_AMG_BGS = 2 };
+enum mfs_precond { MFS_BGS_AMG = 0, MFS_SIMPLE = 1, MFS_AMG_BGS = 2, MFS_AMG_SIMPLE = 3 };
 enum mfs_bgs_order { MFS_BWD = 0, MFS_FWD = 1, MFS_SYM = 2 };
 enum mfs_nullspace { MFS_NS_CONST = 0, MFS_NS_RBM = 1 };
 enum mfs_precision { MFS_FP64 = 0, MFS_FP32P = 1 };
@@ -229,7 +234,10 @@ int mfs_export_csr(const struct mfs_handle *h, int what, int group, int level, i
 
 /* Export per-level data.  what: 0 = aggregate id per node (int32, -1 for
  * unaggregated nodes), 1 = lambda_max estimate (1 double), 2 = SIMPLE
- * diagonal A~_11 of predictor field i (double, group 0, level 0).
+ * diagonal A~_11 of predictor field i (double, group 0; level 0 for
+ * MFS_SIMPLE, level l for MFS_AMG_SIMPLE).  For MFS_AMG_SIMPLE, group 1
+ * holds the level Schur complements S~^l (export_csr what 0, field 0) and
+ * their lambda estimates.
  * cap = capacity in elements; *count receives the element count. */
 int mfs_export_array(const struct mfs_handle *h, int what, int group, int level, int i,
                      void *buf, int64_t cap, int64_t *count);

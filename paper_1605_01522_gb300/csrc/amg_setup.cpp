@@ -250,6 +250,17 @@ void fill_dinv(HLevelField &fl) {
 
 }  // namespace
 
+double amg_power_lambda(const HBsr &A, const std::vector<double> &dinv, uint64_t seed) {
+  return power_lambda(A, dinv, seed);
+}
+
+std::vector<double> amg_dinv(const HBsr &A) {
+  HLevelField f;
+  f.A = A;
+  fill_dinv(f);
+  return f.dinv;
+}
+
 std::vector<double> bsr_to_dense(const HBsr &A) {
   const int64_t nr = A.nrows(), nc = A.ncols();
   std::vector<double> D((size_t)(nr * nc), 0.0);

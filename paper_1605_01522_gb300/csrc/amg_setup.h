@@ -64,6 +64,10 @@ void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<Fie
                  int max_levels, int64_t coarse_max, uint64_t seed, bool want_off,
                  const BlockMap *fine_off, int verbose = 0);
 HDenseLU dense_lu(int n, std::vector<double> a_rowmajor);
+// lambda_max(D^-1 A) estimate (10 power iterations) and the inverse point
+// diagonal, as used by the setup for every smoothed level
+double amg_power_lambda(const HBsr &A, const std::vector<double> &dinv, uint64_t seed);
+std::vector<double> amg_dinv(const HBsr &A);
 std::vector<double> bsr_to_dense(const HBsr &A);
 
 }  // namespace mfs

@@ -369,6 +369,8 @@ template <typename T> struct Precond {
   std::vector<int> G1, G2;
   std::map<std::pair<int, int>, dev::Sell> cross;
   std::vector<T *> dtinv, sr2, st;
+  std::vector<FL<T>> ms;                // AMG(SIMPLE): level Schur complements S~^l
+  std::vector<std::vector<T *>> ms_dtinv;  // AMG(SIMPLE): [level][predictor field] 1 / A~_11
   cudaStream_t s = nullptr;
 
   // (re)allocate every work vector in `ar` (setup, and each clone)
@@ -377,8 +379,16 @@ template <typename T> struct Precond {
     if (g1.L) alloc_group_work(ar, g1);
     st.clear();
     sr2.clear();
-    for (int j : G1) st.push_back(ar.zeros<T>(fsize[j]));
-    for (int k : G2) sr2.push_back(ar.zeros<T>(fsize[k]));
+    if (kind == MFS_SIMPLE) {
+      for (int j : G1) st.push_back(ar.zeros<T>(fsize[j]));
+      for (int k : G2) sr2.push_back(ar.zeros<T>(fsize[k]));
+    }
+    for (auto &f : ms) {
+      f.t = ar.zeros<T>(f.n);
+      f.d = ar.zeros<T>(f.n);
+      f.c = ar.zeros<T>(f.n);
+      f.e = ar.zeros<T>(f.n);
+    }
   }
 
   // single-field polynomial smoother S^l_i; zero: x enters as 0
@@ -482,7 +492,7 @@ template <typename T> struct Precond {
           MFS_CUDA(cudaMemcpyAsync(x[i], g.lv[l][i].xv, g.lv[l][i].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
       return;
     }
-    mono_smooth(g, l, b, x, true);
+    level_smooth(g, l, b, x, true);
     std::vector<const T *> bc(g.nf);
     std::vector<T *> xc(g.nf);
     for (int i = 0; i < g.nf; ++i) {
@@ -499,7 +509,82 @@ template <typename T> struct Precond {
     }
     mono_cycle(g, l + 1, bc, xc);
     for (int i = 0; i < g.nf; ++i) dev::spmv<T>(g.lv[l][i].P, xc[i], x[i], T(1), T(1), x[i], s);
-    mono_smooth(g, l, b, x, false);
+    level_smooth(g, l, b, x, false);
+  }
+
+  void level_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero) {
+    if (kind == MFS_AMG_SIMPLE) simple_smooth(g, l, b, x, zero);
+    else mono_smooth(g, l, b, x, zero);
+  }
+
+  // AMG(SIMPLE) level smoother: r = b - A x; one BGS sweep of the field
+  // smoothers over the predictor fields (into e); one smoother application on
+  // S~^l (into its e); e_1 -= A~11^-1 A_12 e_2; x += e.
+  void simple_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero) {
+    const int k = G2[0];
+    FL<T> &sk = ms[l];
+    for (int sw = 0; sw < sweeps; ++sw) {
+      std::vector<const T *> r(g.nf);
+      for (int i = 0; i < g.nf; ++i) {
+        if (zero) {
+          r[i] = b[i];
+          continue;
+        }
+        FL<T> &f = g.lv[l][i];
+        dev::spmv<T>(f.A, x[i], f.r, T(-1), T(1), b[i], s);
+        for (int j = 0; j < g.nf; ++j) {
+          if (j == i) continue;
+          const dev::Sell *M = g.block(l, i, j);
+          if (M) dev::spmv<T>(*M, x[j], f.r, T(-1), T(1), f.r, s);
+        }
+        r[i] = f.r;
+      }
+      std::vector<char> done(g.nf, 0);
+      const int n1 = (int)G1.size();
+      for (auto &seq : orders(order, n1))
+        for (int jj : seq) {
+          const int i = G1[jj];
+          FL<T> &f = g.lv[l][i];
+          const T *rhs = r[i];
+          for (int q : G1) {
+            if (q == i || !done[q]) continue;
+            const dev::Sell *M = g.block(l, i, q);
+            if (!M) continue;
+            dev::spmv<T>(*M, g.lv[l][q].e, f.c, T(-1), T(1), rhs, s);
+            rhs = f.c;
+          }
+          if (!done[i]) {
+            smooth(f, rhs, f.e, true);
+            done[i] = 1;
+          } else {  // second visit of a symmetric sweep: correction form
+            smooth(f, rhs, f.e, false);
+          }
+        }
+      const T *rhs2 = r[k];
+      for (int j : G1) {
+        const dev::Sell *M = g.block(l, k, j);
+        if (!M) continue;
+        dev::spmv<T>(*M, g.lv[l][j].e, sk.c, T(-1), T(1), rhs2, s);
+        rhs2 = sk.c;
+      }
+      smooth(sk, rhs2, sk.e, true);
+      for (int jj = 0; jj < n1; ++jj) {
+        const int j = G1[jj];
+        const dev::Sell *M = g.block(l, j, k);
+        if (!M) continue;
+        FL<T> &f = g.lv[l][j];
+        dev::spmv<T>(*M, sk.e, f.c, T(1), T(0), nullptr, s);
+        dev::axpy_diag<T>(f.e, ms_dtinv[l][jj], f.c, f.n, s);
+      }
+      for (int j : G1) {
+        FL<T> &f = g.lv[l][j];
+        if (zero) MFS_CUDA(cudaMemcpyAsync(x[j], f.e, f.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        else dev::axpy<T>(x[j], f.e, T(1), f.n, s);
+      }
+      if (zero) MFS_CUDA(cudaMemcpyAsync(x[k], sk.e, sk.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      else dev::axpy<T>(x[k], sk.e, T(1), sk.n, s);
+      zero = false;
+    }
   }
 
   void apply(const T *in, T *out) {
@@ -511,7 +596,7 @@ template <typename T> struct Precond {
     }
     if (kind == MFS_BGS_AMG) {
       bgs(g0, b, x);
-    } else if (kind == MFS_AMG_BGS) {
+    } else if (kind == MFS_AMG_BGS || kind == MFS_AMG_SIMPLE) {
       mono_cycle(g0, 0, b, x);
     } else {
       std::vector<const T *> b1, b2;
@@ -661,6 +746,7 @@ struct IterGraph {
 struct HostSide {
   HGroup hg0, hg1;
   std::vector<std::vector<double>> dtilde;
+  std::vector<std::vector<std::vector<double>>> mono_dtilde;  // AMG(SIMPLE): [level][predictor field]
   BlockMap schur_off;
   std::vector<HBsr> schur_diag;
   std::vector<int> G1, G2;
@@ -978,24 +1064,80 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
     if (gpu) build_group_gpu(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
     else build_group(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
   };
-  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS) {
+  auto split_groups = [&]() {
+    h->host->G1.clear();
+    h->host->G2.clear();
+    bool any = false;
+    for (int i = 0; i < h->nf; ++i) any |= p.simple_group[i] != 0;
+    for (int i = 0; i < h->nf; ++i) {
+      const bool schur = any ? p.simple_group[i] != 0 : i == h->nf - 1;
+      (schur ? h->host->G2 : h->host->G1).push_back(i);
+    }
+    if (h->host->G1.empty() || h->host->G2.empty())
+      throw SetupError(MFS_ERR_INVALID, "SIMPLE needs a non-empty predictor and Schur group");
+  };
+  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE) {
     std::vector<HBsr> diag;
     BlockMap off;
     for (auto &kv : blocks)
       if (kv.first.first == kv.first.second) diag.push_back(kv.second);
       else off[kv.first] = kv.second;
-    group(h->host->hg0, diag, info, p.precond == MFS_AMG_BGS, &off);
+    group(h->host->hg0, diag, info, p.precond != MFS_BGS_AMG, &off);
+    if (p.precond != MFS_AMG_SIMPLE) return;
+    // AMG(SIMPLE): per smoothed level, A~_11 of the merged predictor rows and
+    // the explicit level Schur complement S~^l with its smoother data
+    split_groups();
+    if (h->host->G2.size() != 1) throw SetupError(MFS_ERR_INVALID, "AMG(SIMPLE) takes one Schur field");
+    const int k = h->host->G2[0];
+    const HGroup &g = h->host->hg0;
+    HGroup &hs = h->host->hg1;
+    hs.nf = 1;
+    hs.lv.assign(std::max(0, g.nlevels() - 1), std::vector<HLevelField>(1));
+    h->host->mono_dtilde.assign(hs.lv.size(), {});
+    for (int l = 0; l + 1 < g.nlevels(); ++l) {
+      auto blk = [&](int i, int j) -> const HBsr * {
+        if (i == j) return &g.lv[l][i].A;
+        auto it = g.off[l].find({i, j});
+        return it == g.off[l].end() ? nullptr : &it->second;
+      };
+      std::vector<std::vector<double>> dts;
+      for (int j : h->host->G1) {
+        std::vector<double> d(g.lv[l][j].A.nrows(), 0.0);
+        if (p.simple_approx == MFS_DIAG) {
+          d = bsr_point_diagonal(g.lv[l][j].A);
+        } else {
+          for (int q : h->host->G1) {
+            const HBsr *M = blk(j, q);
+            if (!M) continue;
+            std::vector<double> sr = bsr_abs_row_sums(*M);
+            for (size_t r = 0; r < d.size(); ++r) d[r] += sr[r];
+          }
+        }
+        for (double v : d)
+          if (v == 0.0) throw SetupError(MFS_ERR_SINGULAR, "zero entry in a level's SIMPLE diagonal approximation");
+        dts.push_back(d);
+      }
+      HBsr S = g.lv[l][k].A;
+      for (size_t jj = 0; jj < h->host->G1.size(); ++jj) {
+        const int j = h->host->G1[jj];
+        const HBsr *a = blk(k, j), *c = blk(j, k);
+        if (!a || !c) continue;
+        HBsr Cs = *c;
+        std::vector<double> inv(dts[jj].size());
+        for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / dts[jj][r];
+        bsr_scale_rows(Cs, inv);
+        HBsr Tm = gpu ? gpu_spgemm(*a, Cs) : bsr_spgemm(*a, Cs);
+        S = bsr_axpby(1.0, S, -1.0, Tm);
+      }
+      HLevelField &f = hs.lv[l][0];
+      f.A = std::move(S);
+      f.dinv = amg_dinv(f.A);
+      f.lam = amg_power_lambda(f.A, f.dinv, p.seed);
+      h->host->mono_dtilde[l] = std::move(dts);
+    }
     return;
   }
-  h->host->G1.clear();
-  h->host->G2.clear();
-  bool any = false;
-  for (int i = 0; i < h->nf; ++i) any |= p.simple_group[i] != 0;
-  for (int i = 0; i < h->nf; ++i) {
-    const bool schur = any ? p.simple_group[i] != 0 : i == h->nf - 1;
-    (schur ? h->host->G2 : h->host->G1).push_back(i);
-  }
-  if (h->host->G1.empty() || h->host->G2.empty()) throw SetupError(MFS_ERR_INVALID, "SIMPLE needs a non-empty predictor and Schur group");
+  split_groups();
   std::map<int, int> l2;
   for (size_t a = 0; a < h->host->G2.size(); ++a) l2[h->host->G2[a]] = (int)a;
   std::vector<HBsr> diag1;
@@ -1082,13 +1224,35 @@ void upload_precond(mfs_handle *h, Arena &mat, Precond<T> &P, const std::map<std
   P.foff = h->foff;
   P.s = h->s;
   auto fine_sell = [&](int i, int j) { return h->A64.at({i, j}); };
-  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS) {
+  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE) {
     std::vector<dev::Sell> d0;
     std::map<std::pair<int, int>, dev::Sell> o0;
     for (int i = 0; i < h->nf; ++i) d0.push_back(fine_sell(i, i));
     for (auto &kv : blocks)
       if (kv.first.first != kv.first.second) o0[kv.first] = fine_sell(kv.first.first, kv.first.second);
-    upload_group(mat, P.g0, hs.hg0, p, d0, o0, p.precond == MFS_AMG_BGS);
+    upload_group(mat, P.g0, hs.hg0, p, d0, o0, p.precond != MFS_BGS_AMG);
+    if (p.precond == MFS_AMG_SIMPLE) {
+      P.G1 = hs.G1;
+      P.G2 = hs.G2;
+      P.ms.assign(hs.hg1.lv.size(), FL<T>());
+      P.ms_dtinv.assign(hs.hg1.lv.size(), {});
+      for (size_t l = 0; l < hs.hg1.lv.size(); ++l) {
+        const HLevelField &hf = hs.hg1.lv[l][0];
+        FL<T> &f = P.ms[l];
+        f.n = hf.A.nrows();
+        f.A = upload_sell(mat, hf.A, !f32, f32);
+        std::vector<double> c1, c2;
+        smoother_coeffs(p, hf.lam, c1, c2);
+        f.c1.assign(c1.begin(), c1.end());
+        f.c2.assign(c2.begin(), c2.end());
+        f.dinv = upload_as<T>(mat, hf.dinv);
+        for (auto &d : hs.mono_dtilde[l]) {
+          std::vector<double> inv(d.size());
+          for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / d[r];
+          P.ms_dtinv[l].push_back(upload_as<T>(mat, inv));
+        }
+      }
+    }
   } else {
     P.G1 = hs.G1;
     P.G2 = hs.G2;
@@ -1178,7 +1342,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
   if (!blocks || !fields || !params || nfields < 1 || nfields > MFS_MAX_FIELDS || nblocks < nfields)
     return fail(MFS_ERR_INVALID, "bad block/field arguments");
   const mfs_params &p = *params;
-  if (p.precond < 0 || p.precond > 2 || p.bgs_order < 0 || p.bgs_order > 2 || p.bgs_sweeps < 1 ||
+  if (p.precond < 0 || p.precond > 3 || p.bgs_order < 0 || p.bgs_order > 2 || p.bgs_sweeps < 1 ||
       p.max_levels < 1 || p.coarse_max < 0 || p.restart < 1 || p.restart > 60 || p.max_iters < 1 ||
       (p.smoother == MFS_CHEBYSHEV && (p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0))) ||
       (p.smoother == MFS_JACOBI && p.jacobi_sweeps < 1) || (p.smoother != MFS_CHEBYSHEV && p.smoother != MFS_JACOBI) ||
@@ -1549,9 +1713,13 @@ int mfs_export_array(const mfs_handle *h, int what, int group, int level, int i,
     *count = 1;
     if (buf && cap >= 1) *(double *)buf = f.lam;
   } else if (what == 2) {
-    if (group != 0 || i >= (int)h->host->dtilde.size()) return fail(MFS_ERR_INVALID, "no SIMPLE diagonal");
-    *count = (int64_t)h->host->dtilde[i].size();
-    if (buf && cap >= *count) std::memcpy(buf, h->host->dtilde[i].data(), h->host->dtilde[i].size() * sizeof(double));
+    const std::vector<std::vector<double>> *src = nullptr;
+    if (group == 0 && h->prm.precond == MFS_SIMPLE && level == 0) src = &h->host->dtilde;
+    if (group == 0 && h->prm.precond == MFS_AMG_SIMPLE && level < (int)h->host->mono_dtilde.size())
+      src = &h->host->mono_dtilde[level];
+    if (!src || i >= (int)src->size()) return fail(MFS_ERR_INVALID, "no SIMPLE diagonal");
+    *count = (int64_t)(*src)[i].size();
+    if (buf && cap >= *count) std::memcpy(buf, (*src)[i].data(), (*src)[i].size() * sizeof(double));
   } else {
     return fail(MFS_ERR_INVALID, "bad export kind");
   }

@@ -16,14 +16,14 @@ from . import build as _build
 
 MAX_FIELDS = 8
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_SINGULAR, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6, -7
-BGS_AMG, SIMPLE, AMG_BGS = 0, 1, 2
+BGS_AMG, SIMPLE, AMG_BGS, AMG_SIMPLE = 0, 1, 2, 3
 BWD, FWD, SYM = 0, 1, 2
 NS_CONST, NS_RBM = 0, 1
 FP64, FP32P = 0, 1
 ABSROWSUM, DIAG = 0, 1
 CHEBYSHEV, JACOBI = 0, 1
 
-PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS}
+PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS, "amg_simple": AMG_SIMPLE}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares

@@ -54,15 +54,22 @@ def oracle_preconditioner(lib, system):
     sizes = [f.ndofs for f in system.fields]
     bsz = [f.b for f in system.fields]
     kind = p.precond
-    if kind in (0, 2):
+    sg = list(p.simple_group)[:nf]
+    if not any(sg):
+        sg = [0] * (nf - 1) + [1]
+    g1 = [i for i in range(nf) if sg[i] == 0]
+    g2 = [i for i in range(nf) if sg[i] == 1]
+    if kind in (0, 2, 3):
         grp = _Grp(_levels(lib, 0, nf, bsz), sp_)
         if kind == 0:
             op = precond.BGS(A, nf, [grp.leaf(i) for i in range(nf)], order, p.bgs_sweeps)
         else:
-            mono = precond.MonoAMG.__new__(precond.MonoAMG)
+            cls = precond.MonoAMG if kind == 2 else precond.MonoAMGSimple
+            mono = cls.__new__(cls)
             mono.nf = nf
             mono.grp = grp
-            mono.prm = precond.Params("amg_bgs", bgs_order=order, bgs_sweeps=p.bgs_sweeps, smoother=sp_)
+            mono.prm = precond.Params("amg_bgs" if kind == 2 else "amg_simple", bgs_order=order,
+                                      bgs_sweeps=p.bgs_sweeps, smoother=sp_)
             mono.A = [dict(A)]
             for l in range(1, len(grp.levels)):
                 d = {}
@@ -70,13 +77,17 @@ def oracle_preconditioner(lib, system):
                     d[(i, j)] = grp.levels[l][i].A if i == j else lib.export_csr("A", 0, l, i, j)
                 mono.A.append(d)
             mono.coarse = amg.DenseLU(precond.assemble(mono.A[-1], nf))
+            if kind == 3:
+                # level Schur complements S~^l (group 1) and A~_11 per level
+                mono.g1, mono.g2 = g1, g2
+                mono.S, mono.dt = [], []
+                for l in range(len(grp.levels) - 1):
+                    fl = amg.FieldLevel(lib.export_csr("A", 1, l, 0, 0), None)
+                    fl.lam = lib.export_array("lambda", 1, l, 0)
+                    mono.S.append(fl)
+                    mono.dt.append([lib.export_array("dtilde", 0, l, jj) for jj in range(len(g1))])
             op = mono
     else:
-        sg = list(p.simple_group)[:nf]
-        if not any(sg):
-            sg = [0] * (nf - 1) + [1]
-        g1 = [i for i in range(nf) if sg[i] == 0]
-        g2 = [i for i in range(nf) if sg[i] == 1]
         grp0 = _Grp(_levels(lib, 0, len(g1), [bsz[i] for i in g1]), sp_)
         grp1 = _Grp(_levels(lib, 1, len(g2), [bsz[i] for i in g2]), sp_)
         sub = precond.sub_blocks(A, g1)

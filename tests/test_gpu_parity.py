@@ -1,7 +1,7 @@
 """CUDA path (through the C ABI) against the FP64 oracle.  Needs a GB300.
 
 * coupled matvec: element-wise against scipy on the same blocks;
-* one preconditioner application (BGS(AMG), SIMPLE, AMG(BGS)), FP64: within
+* one preconditioner application (BGS(AMG), SIMPLE, AMG(BGS), AMG(SIMPLE)), FP64: within
   1e-12 relative (max-norm) of the oracle applied to the library's own
   exported hierarchy - the float64 kernels and the oracle differ only in
   summation order;
@@ -72,9 +72,14 @@ CASES = [("2d", "bgs_amg", {}), ("2d", "amg_bgs", {}), ("2d", "simple", {}),
          ("fsi", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag")),
          ("fsi", "simple", dict(simple_group=[0, 0, 0, 1])), ("fsi", "bgs_amg", {})]
 FSI = [c for c in CASES if c[0] == "fsi"]
+# AMG(SIMPLE): the monolithic V-cycle with the SIMPLE level smoother
+AMG_SIMPLE = [("2d", "amg_simple", {}), ("3d", "amg_simple", {}), ("3d", "amg_simple", dict(bgs_order="sym")),
+              ("3d", "amg_simple", dict(simple_group=[0, 1, 0], simple_approx="diag")),
+              ("3d2", "amg_simple", dict(smoother="jacobi", jacobi_sweeps=2)),
+              ("fsi", "amg_simple", dict(simple_group=[0, 0, 0, 1]))]
 
 
-@pytest.mark.parametrize("name,pc,extra", CASES)
+@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE)
 def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
     s, kw = _small(name)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
@@ -87,7 +92,8 @@ def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
             assert err <= APPLY_TOL, err
 
 
-@pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI)
+@pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI
+                         + AMG_SIMPLE[:4])
 def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     s, kw = _small(name)
     okw = {k: v for k, v in extra.items() if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps")}
@@ -104,7 +110,8 @@ def test_solve_fp64_iterations_match_oracle(name, pc, extra):
 
 
 @pytest.mark.parametrize("name,pc,extra", [("2d", "bgs_amg", {}), ("3d", "bgs_amg", {}), ("3d", "amg_bgs", {}),
-                                           ("3d", "simple", {}), ("fsi", "bgs_amg", {})] + FSI[:1])
+                                           ("3d", "simple", {}), ("fsi", "bgs_amg", {})] + FSI[:1]
+                         + AMG_SIMPLE[1:2])
 def test_solve_fp32_preconditioner(name, pc, extra):
     s, kw = _small(name)
     ro, D = _oracle_solve(s, kw, pc, extra)

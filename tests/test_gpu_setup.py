@@ -75,3 +75,28 @@ def test_gpu_setup_simple_objects():
         assert _rel(g.export_csr("P", 1, l, 0), h.export_csr("P", 1, l, 0)) < TOL
     g.close()
     h.close()
+
+
+@pytest.mark.parametrize("approx", ["absrowsum", "diag"])
+def test_gpu_setup_amg_simple_level_objects(approx):
+    """AMG(SIMPLE): A~_11 and S~^l on every smoothed level, GPU vs host setup,
+    and S~^l against the oracle's level Schur complement."""
+    s = inputs.coupled_box_3d(ne=11, nfields=3)
+    kw = dict(max_levels=4, coarse_max=100, simple_group=[0, 0, 1], simple_approx=approx)
+    g = mfs.Solver(s, precond="amg_simple", setup_device=1, **kw)
+    h = mfs.Solver(s, precond="amg_simple", setup_only=1, **kw)
+    M = precond.Preconditioner(s.scipy_blocks(), [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params("amg_simple", seed=7, **kw))
+    L = g.num_levels(0)
+    assert L == h.num_levels(0) == len(M.op.grp.levels) and g.num_levels(1) == L - 1
+    for l in range(L - 1):
+        for jj in range(2):
+            dg, dh = g.export_array("dtilde", 0, l, jj), h.export_array("dtilde", 0, l, jj)
+            assert np.abs(dg - dh).max() <= 1e-12 * np.abs(dh).max()
+            assert np.abs(dh - M.op.dt[l][jj]).max() <= 1e-12 * np.abs(dh).max()
+        Sg, Sh = g.export_csr("A", 1, l, 0, 0), h.export_csr("A", 1, l, 0, 0)
+        assert _rel(Sg, Sh) < TOL and _rel(Sh, M.op.S[l].A) < TOL
+        lg, lh = g.export_array("lambda", 1, l, 0), h.export_array("lambda", 1, l, 0)
+        assert abs(lg - lh) <= 1e-12 * lh and abs(lh - M.op.S[l].lam) <= 1e-12 * lh
+    g.close()
+    h.close()

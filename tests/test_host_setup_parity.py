@@ -83,6 +83,27 @@ def test_simple_objects_match_oracle(approx):
     lib.close()
 
 
+@pytest.mark.parametrize("approx", ["absrowsum", "diag"])
+@pytest.mark.parametrize("grp", [[0, 0, 1], [1, 0, 0]])
+def test_amg_simple_level_objects_match_oracle(approx, grp):
+    """AMG(SIMPLE): per smoothed level the A~_11 diagonal of the merged
+    predictor rows, the explicit S~^l and its lambda_max."""
+    s, kw = _get("3d")
+    lib = mfs.Solver(s, precond="amg_simple", simple_group=grp, simple_approx=approx, setup_only=1, seed=7, **kw)
+    M = precond.Preconditioner(s.scipy_blocks(), [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params("amg_simple", simple_group=grp, simple_approx=approx, seed=7, **kw))
+    L = len(M.op.grp.levels)
+    assert lib.num_levels(0) == L and lib.num_levels(1) == L - 1
+    for l in range(L - 1):
+        for jj in range(2):
+            assert _rel(lib.export_array("dtilde", 0, l, jj), M.op.dt[l][jj]) < 1e-14
+        assert _rel(lib.export_csr("A", 1, l, 0, 0), M.op.S[l].A) < TOL
+        assert abs(lib.export_array("lambda", 1, l, 0) - M.op.S[l].lam) < 1e-13 * M.op.S[l].lam
+    with pytest.raises(mfs.MfsError):
+        mfs.Solver(s, precond="amg_simple", simple_group=[0, 1, 1], setup_only=1, **kw)
+    lib.close()
+
+
 def test_setup_rejects_bad_input():
     s, kw = _get("2d")
     bad = inputs.BlockSystem(s.fields, {k: v for k, v in s.blocks.items() if k != (1, 1)}, s.rhs)
