@@ -202,7 +202,7 @@ def counts_key(args):
 def precond_extra(args):
     """Preconditioner options of the workload (the split box uses SIMPLE with a
     diagonal A~11 over the predictor fields S, G, Fu and the pressure as Schur field)."""
-    if args.workload == "fsi" and args.precond == "simple":
+    if args.workload == "fsi" and args.precond in ("simple", "amg_simple"):
         return dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
     return {}
 

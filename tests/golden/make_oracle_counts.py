@@ -4,7 +4,7 @@ residuals of the FP64 oracle on the full-size synthetic workloads.
 Calls only the oracle and the seeded input generators (no GPU code).  The
 stored counts pin the CUDA path at full size (iterations within +-1) and
 scale the oracle's timed CPU sample in bench.py.
-Run:  PYTHONPATH=. python tests/golden/make_oracle_counts.py [workload ...]
+Run:  PYTHONPATH=. python tests/golden/make_oracle_counts.py [workload | workload/precond ...]
 """
 import json
 import os
@@ -21,9 +21,10 @@ from paper_1605_01522_gb300 import inputs  # noqa: E402
 WORKLOADS = {
     "coupled_box_3d_ne64_f3": (lambda: inputs.coupled_box_3d(ne=64, nfields=3, seed=1),
                                dict(max_levels=5, coarse_max=1000),
-                               {"bgs_amg": {}, "amg_bgs": {}, "simple": {}}),
+                               {"bgs_amg": {}, "amg_bgs": {}, "simple": {}, "amg_simple": {}}),
     "fsi_box_ne48": (lambda: inputs.fsi_box(ne=48, seed=2), dict(max_levels=5, coarse_max=1000),
-                     {"bgs_amg": {}, "simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
+                     {"bgs_amg": {}, "simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag"),
+                      "amg_simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
 }
 
 
@@ -35,13 +36,15 @@ def main():
         with open(path) as f:
             out = json.load(f)
     for name, (gen, kw, pcs) in WORKLOADS.items():
-        if only and name not in only:
+        pick = [pc for pc in pcs if not only or name in only or f"{name}/{pc}" in only]
+        if not pick:
             continue
         s = gen()
         A = s.scipy_blocks()
         D = precond.assemble(A, s.nfields)
         specs = [amg.FieldSpec.of(f) for f in s.fields]
-        for pc, extra in pcs.items():
+        for pc in pick:
+            extra = pcs[pc]
             t0 = time.time()
             M = precond.Preconditioner(A, specs, precond.Params(pc, **kw, **extra))
             t1 = time.time()

@@ -39,7 +39,7 @@ def _counts():
         return json.load(f)
 
 
-@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple"])
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple", "amg_simple"])
 def test_fullsize_fp64_matches_oracle_counts(pc):
     s, D = _system()
     ref = _counts()[f"coupled_box_3d_ne64_f3/{pc}"]
@@ -52,7 +52,7 @@ def test_fullsize_fp64_matches_oracle_counts(pc):
     assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
 
 
-@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs"])
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "amg_simple"])
 def test_fullsize_fp32_preconditioner(pc):
     s, D = _system()
     ref = _counts()[f"coupled_box_3d_ne64_f3/{pc}"]
@@ -94,14 +94,16 @@ def test_fullsize_split_box_saddle_simple(prec):
         assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
 
 
-def test_fullsize_split_box_bgs_fails_like_the_oracle():
+@pytest.mark.parametrize("pc,extra", [("bgs_amg", {}), ("amg_simple", FSI_SIMPLE)])
+def test_fullsize_split_box_fails_like_the_oracle(pc, extra):
     """BGS(AMG) on the saddle system does not reach 1e-8 in 400 iterations in
-    the oracle (Sec. 4.1: BGS needs dominant diagonal blocks); the GPU must
+    the oracle (Sec. 4.1: BGS needs dominant diagonal blocks), nor does
+    AMG(SIMPLE) with a diagonal A~_11 on the coarse levels; the GPU must
     report the same failure with a similar residual."""
     s, D = _fsi()
-    ref = _counts()["fsi_box_ne48/bgs_amg"]
+    ref = _counts()[f"fsi_box_ne48/{pc}"]
     assert not ref["converged"]
-    with mfs.Solver(s, precond="bgs_amg", max_iters=ref["iters"], **KW) as lib:
+    with mfs.Solver(s, precond=pc, max_iters=ref["iters"], **KW, **extra) as lib:
         x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
     assert rc == mfs.ERR_NOT_CONVERGED and info["iters"] == ref["iters"]
     assert 0.5 * ref["relres"] <= info["true_relres"] <= 2.0 * ref["relres"]
