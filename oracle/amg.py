@@ -204,7 +204,8 @@ class FieldLevel:
     def __init__(self, A, b):
         self.A = A.tocsr()
         self.b = b
-        self.dinv = 1.0 / self.A.diagonal()
+        with np.errstate(divide="ignore"):
+            self.dinv = 1.0 / self.A.diagonal()
         self.lam = None
         self.agg = None
         self.P = None
@@ -228,6 +229,9 @@ def build_group(As, specs, max_levels, coarse_max, seed):
     a new level is made while the level count is below max_levels and the
     group's total dof count exceeds coarse_max.  Returns levels[l][i]."""
     levels = [[FieldLevel(A, s.b) for A, s in zip(As, specs)]]
+    if not all(np.all(np.isfinite(fl.dinv)) for fl in levels[0]):
+        # D^-1 A smoothing (and BGS, Sec. 4.1) needs nonsingular diagonal blocks
+        raise ValueError("zero diagonal entry in a diagonal block")
     while len(levels) < max_levels and sum(fl.A.shape[0] for fl in levels[-1]) > coarse_max:
         fine = len(levels) == 1
         nxt = []

@@ -14,7 +14,12 @@ method run for k_max sweeps from x^(0) = 0 (Sec. 7.1 uses k_max = 1):
 * SIMPLE (Sec. 4.2): the predictor / Schur / update steps of the SIMPLE
   iteration with x^(0) = 0, so the A_22 x_2 term of the Schur right-hand
   side vanishes; fields are merged into a predictor group and a Schur group
-  (Sec. 4.2, merging for N > 2); a multi-field group is solved by BGS(AMG).
+  (Sec. 4.2, merging for N > 2); a multi-field predictor group is solved by
+  one BGS(AMG) sweep or, with simple_pred = "amg_bgs", one monolithic
+  AMG(BGS) V-cycle (SIMPLE(BGS(AMG)) and SIMPLE(AMG(BGS)) of Sec. 6.3); a
+  Schur group at or below coarse_max dofs gets a one-level hierarchy, i.e. the
+  dense LU of S~ (Sec. 6.3 solves the small constraint Schur complement
+  directly).
   A~_11 is SIMPLEC's diagonal of absolute row sums of the merged A_11 block
   (read as the sum of absolute entries of each row) or, optionally, diag(A_11).
   S~ = A_22 - A_21 A~_11^-1 A_12 is formed explicitly.
@@ -41,7 +46,7 @@ class Params:
 
     def __init__(self, precond="bgs_amg", bgs_order="bwd", bgs_sweeps=1, simple_group=None,
                  simple_approx="absrowsum", max_levels=4, coarse_max=1000, seed=7,
-                 smoother=None):
+                 smoother=None, simple_pred="bgs_amg"):
         self.precond = precond
         self.bgs_order = bgs_order
         self.bgs_sweeps = bgs_sweeps
@@ -51,6 +56,7 @@ class Params:
         self.coarse_max = coarse_max
         self.seed = seed
         self.smoother = smoother or SmootherParams()
+        self.simple_pred = simple_pred
 
 
 def split(v, sizes):
@@ -340,7 +346,11 @@ class Preconditioner:
             grp_of = prm.simple_group or [0] * (nf - 1) + [1]
             g1 = [i for i in range(nf) if grp_of[i] == 0]
             g2 = [i for i in range(nf) if grp_of[i] == 1]
-            pred, grp1 = bgs_amg_over(sub_blocks(blocks, g1), [specs[i] for i in g1], prm, len(g1))
+            if prm.simple_pred == "amg_bgs":
+                pred = MonoAMG(sub_blocks(blocks, g1), [specs[i] for i in g1], prm, len(g1))
+                grp1 = pred.grp
+            else:
+                pred, grp1 = bgs_amg_over(sub_blocks(blocks, g1), [specs[i] for i in g1], prm, len(g1))
             dt = simple_dtilde(blocks, g1, prm.simple_approx)
             S = simple_schur(blocks, g1, g2, dt)
             sspecs = [amg.FieldSpec(specs[k].b, specs[k].dim, "const", None, specs[k].theta) for k in g2]

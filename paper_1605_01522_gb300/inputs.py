@@ -22,6 +22,11 @@ whose meshes are not available:
   elasticity (3 dof/node), heat (1 dof/node) and an optional scalar diffusion
   field whose diffusivity is log-uniform in [1e-3, 1e3] per element.  The
   heat-diffusion pair is coupled by alpha*M and 1e-3*M.
+* ``constrained_box``    - the coupled box plus a field of m Lagrange multipliers
+  (stand-in for the lung model's volume constraints, Sec. 6.3): each enforces
+  the mean normal displacement over one patch of the free face; the
+  multiplier-multiplier block is zero (saddle point with a zero diagonal
+  block).
 
 Layout of a block: node-level block-CSR (BSR) with int32 ``rowptr`` / ``colind``
 and float64 ``vals`` of shape (nnzb, br, bc), row-major inside a block.
@@ -36,7 +41,7 @@ import itertools
 import numpy as np
 
 __all__ = [
-    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d", "fsi_box",
+    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d", "constrained_box", "fsi_box",
     "batch_sizes_log_uniform", "batch_workload", "system_rhs",
 ]
 
@@ -366,6 +371,75 @@ def coupled_box_3d(ne=64, nfields=3, alpha=1e-2, beta=1e-3, E=1.0, nu=0.3, k=1.0
     return BlockSystem(fields, blocks, _seeded_rhs(fields, seed, dnodes),
                        name=f"coupled_box_3d_ne{ne}_f{nfields}",
                        meta=dict(ne=ne, nfields=nfields, alpha=alpha, seed=seed))
+
+
+def constrained_box(ne=64, nfields=3, patches=(2, 2), seed=5, **kw):
+    """coupled_box_3d plus a last field C of m = patches[0]*patches[1]
+    Lagrange multipliers.  The free face x = 1 is cut into a grid of patches
+    over (y, z); multiplier k enforces the mean x-displacement of patch k,
+    with weights w_i = (int_{patch} N_i) / |patch| (Q1 face integrals, so the
+    weights of a patch sum to 1): A_C0 holds w as 1 x 3 blocks [w_i, 0, 0],
+    A_0C = A_C0^T (the multipliers act as uniform pressures on the patches)
+    and A_CC is an all-zero (empty) block.  Fields 1.. of the box do not couple
+    to C.  The right-hand side is redrawn with this seed over all fields."""
+    base = coupled_box_3d(ne=ne, nfields=nfields, seed=seed, **kw)
+    g = _Grid(ne, 3)
+    py, pz = patches
+    m = py * pz
+    face = np.nonzero(g.ijk[:, 0] == ne)[0]
+    wts = np.zeros((m, g.nnodes))
+    # face cells (j, k) in y, z; each adds a quarter of its area to its four nodes
+    for cj in range(ne):
+        for ck in range(ne):
+            k = min(cj * py // ne, py - 1) + py * min(ck * pz // ne, pz - 1)
+            for dj in (0, 1):
+                for dk in (0, 1):
+                    node = ne + (cj + dj) * g.stride[1] + (ck + dk) * g.stride[2]
+                    wts[k, node] += 0.25
+    wts /= wts.sum(1, keepdims=True)
+    rows_c, cols_c, vals_c = [], [], []
+    for k in range(m):
+        nz = np.nonzero(wts[k])[0]
+        rows_c.append(len(nz))
+        cols_c.append(nz)
+        v = np.zeros((len(nz), 1, 3))
+        v[:, 0, 0] = wts[k, nz]
+        vals_c.append(v)
+    rp = np.zeros(m + 1, np.int64)
+    np.cumsum(rows_c, out=rp[1:])
+    A_c0 = BSR(1, 3, m, g.nnodes, rp.astype(np.int32), np.concatenate(cols_c).astype(np.int32),
+               np.concatenate(vals_c))
+    # transpose: row i of A_0C has one block per patch containing node i
+    cnt = (wts > 0).sum(0)
+    rp2 = np.zeros(g.nnodes + 1, np.int64)
+    np.cumsum(cnt, out=rp2[1:])
+    col2 = np.zeros(rp2[-1], np.int32)
+    val2 = np.zeros((rp2[-1], 3, 1))
+    fill = rp2[:-1].copy()
+    for k in range(m):
+        nz = np.nonzero(wts[k])[0]
+        col2[fill[nz]] = k
+        val2[fill[nz], 0, 0] = wts[k, nz]
+        fill[nz] += 1
+    A_0c = BSR(3, 1, g.nnodes, m, rp2.astype(np.int32), col2, val2)
+    nf = nfields + 1
+    blocks = dict(base.blocks)
+    blocks[(0, nf - 1)] = A_0c
+    blocks[(nf - 1, 0)] = A_c0
+    blocks[(nf - 1, nf - 1)] = BSR(1, 1, m, m, np.zeros(m + 1, np.int32), np.zeros(0, np.int32),
+                                   np.zeros((0, 1, 1)))
+    centres = np.array([[1.0, (kj + 0.5) / py, (kk + 0.5) / pz] for kk in range(pz) for kj in range(py)])
+    fields = list(base.fields) + [Field("constraint", 1, m, 3, centres, "const", 0.0)]
+    dnodes = base.fields[0].dirichlet_nodes
+    rhs = np.random.default_rng(seed).standard_normal(sum(f.ndofs for f in fields))
+    off = 0
+    for f in fields[:-1]:
+        d = (dnodes[:, None] * f.b + np.arange(f.b)[None, :]).ravel()
+        rhs[off + d] = 0.0
+        off += f.ndofs
+    assert not np.intersect1d(face, dnodes).size
+    return BlockSystem(fields, blocks, rhs, name=f"constrained_box_ne{ne}_f{nfields}_m{m}",
+                       meta=dict(ne=ne, nfields=nfields, patches=patches, seed=seed))
 
 
 def q1_flow_matrices(h):

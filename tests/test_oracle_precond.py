@@ -5,7 +5,9 @@ BGS with exact block solves must equal a dense block-triangular solve
 reproduce A^-1 (Sec. 4.2: M_SIMPLE then equals A); AMG(BGS) must reduce to the
 single-field V-cycle for one field and to BGS(AMG)'s block-diagonal V-cycles
 without coupling, and its coarse blocks must equal dense R_i A_ij P_j
-(Sec. 4.3); AMG(SIMPLE) must reduce to BGS(AMG) without coupling and its
+(Sec. 4.3); SIMPLE(AMG(BGS)) must reduce to SIMPLE(BGS(AMG)) for one or
+uncoupled predictor fields, and the constraint saddle's Schur group must be
+a direct solve (Sec. 6.3); AMG(SIMPLE) must reduce to BGS(AMG) without coupling and its
 level smoother, with converged inner solves, must apply M_SIMPLE^-1 (Sec. 4.2
 factorisation on the level); FGMRES must reach the dense solution and take
 one iteration with an exact preconditioner.
@@ -26,6 +28,11 @@ def _sys2(ne=6, alpha=1e-1, beta=5e-2):
 
 def _sys3(ne=3):
     s = inputs.coupled_box_3d(ne=ne, nfields=3, alpha=0.2, beta=0.1)
+    return s, {k: v.to_scipy() for k, v in s.blocks.items()}
+
+
+def _cons(ne=3):
+    s = inputs.constrained_box(ne=ne, nfields=3, alpha=0.2, beta=0.1)
     return s, {k: v.to_scipy() for k, v in s.blocks.items()}
 
 
@@ -76,7 +83,8 @@ def test_bgs_exact_blocks_zero_coupling_is_exact():
     assert r.iters == 1 and r.relres < 1e-12
 
 
-@pytest.mark.parametrize("maker,groups", [(_sys2, [0, 1]), (_sys3, [0, 0, 1]), (_sys3, [0, 1, 1])])
+@pytest.mark.parametrize("maker,groups", [(_sys2, [0, 1]), (_sys3, [0, 0, 1]), (_sys3, [0, 1, 1]),
+                                          (_cons, [0, 0, 0, 1])])
 def test_simple_with_exact_a11_reproduces_inverse(maker, groups):
     s, A = maker()
     nf = s.nfields
@@ -213,6 +221,51 @@ def test_amg_simple_level_smoother_applies_simple_factorisation(approx):
     r = rng.standard_normal(2 * n)
     x = mono.smooth(0, [r[:n], r[n:]], [np.zeros(n), np.zeros(n)])
     assert np.allclose(np.concatenate(x), np.linalg.solve(M, r), rtol=1e-10, atol=1e-10)
+
+
+def test_constrained_saddle_structure_and_direct_schur():
+    """Constraint field of the lung-like box (Sec. 6.3): zero diagonal block,
+    A_0C = A_C0^T with unit patch weights; BGS-type setups must refuse the zero
+    diagonal; SIMPLE's Schur group (4 dofs <= coarse_max) is one level, so its
+    solve is the dense solve with S~ = -A_C0 A~_00^-1 A_0C."""
+    s, A = _cons(ne=4)
+    specs = [amg.FieldSpec.of(f) for f in s.fields]
+    assert A[(3, 3)].nnz == 0 and abs(A[(0, 3)] - A[(3, 0)].T).max() == 0
+    assert np.allclose(np.asarray(A[(3, 0)].sum(1)).ravel(), 1.0)
+    for pc in ("bgs_amg", "amg_bgs", "amg_simple"):
+        with pytest.raises(ValueError):
+            precond.Preconditioner(A, specs, precond.Params(pc, max_levels=3, coarse_max=20))
+    M = precond.Preconditioner(A, specs, precond.Params("simple", max_levels=3, coarse_max=20))
+    assert len(M.groups[1].levels) == 1
+    S = M.schur_blocks[(0, 0)].toarray()
+    D = _dense(A, 4)
+    n1 = sum(f.ndofs for f in s.fields[:3])
+    dt = np.abs(D[:n1, :n1]).sum(1)
+    assert np.allclose(S, -D[n1:, :n1] @ np.diag(1 / dt) @ D[:n1, n1:], rtol=1e-12, atol=0)
+    assert np.all(np.linalg.eigvalsh(0.5 * (S + S.T)) < 0)
+    r = np.random.default_rng(10).standard_normal(S.shape[0])
+    leaf = M.groups[1].leaf(0)
+    assert np.allclose(leaf(r), np.linalg.solve(S, r), rtol=1e-12, atol=1e-12 * np.abs(np.linalg.solve(S, r)).max())
+
+
+def test_simple_amg_bgs_predictor_reductions():
+    """SIMPLE(AMG(BGS)) equals SIMPLE(BGS(AMG)) when the predictor is one field
+    (the monolithic V-cycle of one field is the single-field V-cycle) and when
+    the predictor fields do not couple (AMG(BGS) without coupling is BGS(AMG))."""
+    s, A = _sys3(ne=5)
+    specs = [amg.FieldSpec.of(f) for f in s.fields]
+    kw = dict(max_levels=3, coarse_max=40)
+    b = np.random.default_rng(11).standard_normal(sum(f.ndofs for f in s.fields))
+    for groups, blocks in (([0, 1, 1], A),
+                           ([0, 0, 1], {k: v for k, v in A.items() if set(k) != {0, 1}})):
+        za = precond.Preconditioner(blocks, specs, precond.Params("simple", simple_group=groups,
+                                                                  simple_pred="amg_bgs", **kw))(b)
+        zb = precond.Preconditioner(blocks, specs, precond.Params("simple", simple_group=groups, **kw))(b)
+        assert np.allclose(za, zb, rtol=1e-12, atol=1e-13 * np.abs(zb).max())
+    # with coupling inside the predictor group the two differ
+    za = precond.Preconditioner(A, specs, precond.Params("simple", simple_group=[0, 0, 1], simple_pred="amg_bgs", **kw))(b)
+    zb = precond.Preconditioner(A, specs, precond.Params("simple", simple_group=[0, 0, 1], **kw))(b)
+    assert not np.allclose(za, zb, rtol=1e-6)
 
 
 def test_fgmres_unpreconditioned_reaches_dense_solution():
