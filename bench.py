@@ -41,17 +41,26 @@ CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_eve
 
 
 def workload_config(args, s, extra=None):
-    what = (f"3-field 3D coupled box {NE}^3 Q1 ({s.ndofs} dofs: elasticity+heat+diffusion)"
-            if args.workload != "fsi" else
-            f"4-field split-box saddle 48^3 Q1 ({s.ndofs} dofs: structure | mesh + PSPG Stokes u, p)")
+    if args.workload == "fsi":
+        what = f"4-field split-box saddle 48^3 Q1 ({s.ndofs} dofs: structure | mesh + PSPG Stokes u, p)"
+    elif args.workload == "cons":
+        what = (f"constrained 3-field box {NE}^3 Q1 + 4 patch-mean Lagrange multipliers ({s.ndofs} dofs, "
+                f"zero multiplier block)")
+    else:
+        what = f"3-field 3D coupled box {NE}^3 Q1 ({s.ndofs} dofs: elasticity+heat+diffusion)"
+    pname = args.precond.upper()
+    if args.precond == "simple" and args.simple_pred == "amg_bgs":
+        pname = "SIMPLE(AMG(BGS))"
     cfg = {
-        "workload": f"{what}, {args.precond.upper()} preconditioner in {args.precision.upper()}, FGMRES(50), rtol 1e-8",
+        "workload": f"{what}, {pname} preconditioner in {args.precision.upper()}, FGMRES(50), rtol 1e-8",
         "ndofs": s.ndofs,
         "precond": args.precond,
         "precision": args.precision,
         "l2": "inputs larger than L2 (matrices ~2 GB per solve pass)",
         "parallelism": "replicas" if args.gpus > 1 else "1 GPU",
     }
+    if args.precond == "simple":
+        cfg["simple_pred"] = args.simple_pred
     cfg.update(extra or {})
     return cfg
 
@@ -192,19 +201,27 @@ def make_system(args=None):
     from paper_1605_01522_gb300 import inputs
     if args is not None and args.workload == "fsi":
         return inputs.fsi_box(ne=48, seed=2)
+    if args is not None and args.workload == "cons":
+        return inputs.constrained_box(ne=NE, nfields=3, seed=5)
     return inputs.coupled_box_3d(ne=NE, nfields=3, seed=1)
 
 
 def counts_key(args):
-    return ("fsi_box_ne48" if args.workload == "fsi" else WORKLOAD) + "/" + args.precond
+    name = {"fsi": "fsi_box_ne48", "cons": f"constrained_box_ne{NE}_f3_m4"}.get(args.workload, WORKLOAD)
+    pc = args.precond + ("+amg_bgs" if args.precond == "simple" and args.simple_pred == "amg_bgs" else "")
+    return name + "/" + pc
 
 
 def precond_extra(args):
     """Preconditioner options of the workload (the split box uses SIMPLE with a
-    diagonal A~11 over the predictor fields S, G, Fu and the pressure as Schur field)."""
+    diagonal A~11 over the predictor fields S, G, Fu and the pressure as Schur field;
+    --simple-pred picks SIMPLE's predictor solver)."""
+    extra = {}
     if args.workload == "fsi" and args.precond in ("simple", "amg_simple"):
-        return dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
-    return {}
+        extra = dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
+    if args.precond == "simple" and args.simple_pred != "bgs_amg":
+        extra["simple_pred"] = args.simple_pred
+    return extra
 
 
 def oracle_counts():
@@ -524,9 +541,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--ne", type=int, default=NE, help="mesh edge (64 = the benchmark workload)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "fsi", "batch", "serve"],
+    ap.add_argument("--workload", default="box", choices=["box", "fsi", "cons", "batch", "serve"],
                     help="box: the 64^3 three-field system (headline); fsi: the 48^3 split-box saddle; "
+                         "cons: the box with 4 Lagrange-multiplier constraints (zero diagonal block); "
                          "batch: 256 independent systems; serve: Poisson request stream")
+    ap.add_argument("--simple-pred", default="bgs_amg", choices=["bgs_amg", "amg_bgs"],
+                    help="SIMPLE's predictor solver: BGS(AMG) sweep or AMG(BGS) V-cycle")
     ap.add_argument("--nsys", type=int, default=256)
     ap.add_argument("--threads", type=int, default=16)
     ap.add_argument("--requests", type=int, default=1000)

@@ -10,7 +10,13 @@
  *                per diagonal block (Sec. 4.1);
  *   MFS_SIMPLE   n-field SIMPLE(AMG): fields merged into a predictor group and a
  *                Schur group, SIMPLEC / diagonal approximation of the predictor
- *                block, explicit approximate Schur complement (Sec. 4.2);
+ *                block, explicit approximate Schur complement (Sec. 4.2); a
+ *                multi-field predictor group is solved by one BGS(AMG) sweep
+ *                or, with simple_pred = MFS_PRED_AMG_BGS, by one monolithic
+ *                AMG(BGS) V-cycle (SIMPLE(BGS(AMG)) / SIMPLE(AMG(BGS)) of
+ *                Sec. 6.3); a Schur group at or below coarse_max dofs is
+ *                solved directly by the dense LU of S~ (Sec. 6.3: a
+ *                constraint block with a zero diagonal block);
  *   MFS_AMG_BGS  monolithic AMG with block-diagonal transfers, blockwise
  *                Galerkin coarse blocks and block Gauss-Seidel level smoothing
  *                (Sec. 4.3);
@@ -73,6 +79,7 @@ enum mfs_nullspace { MFS_NS_CONST = 0, MFS_NS_RBM = 1 };
 enum mfs_precision { MFS_FP64 = 0, MFS_FP32P = 1 };
 enum mfs_simple_approx { MFS_ABSROWSUM = 0, MFS_DIAG = 1 };
 enum mfs_smoother { MFS_CHEBYSHEV = 0, MFS_JACOBI = 1 };
+enum mfs_simple_pred { MFS_PRED_BGS_AMG = 0, MFS_PRED_AMG_BGS = 1 };
 
 /* One nonzero block A_ij as node-level block-CSR (BSR): nbrows x nbcols node
  * blocks of br x bc scalars (br = dofs per node of field i, bc = of field j),
@@ -127,6 +134,8 @@ typedef struct {
                                         one captured CUDA graph per GMRES iteration */
   int setup_device;                  /* 1 (default): AMG setup on the GPU; 0: on the host
                                         (C++/OpenMP); both compute the same hierarchy */
+  int simple_pred;                   /* enum mfs_simple_pred: solver of SIMPLE's predictor
+                                        group (default MFS_PRED_BGS_AMG) */
 } mfs_params;
 
 typedef struct {

@@ -606,8 +606,9 @@ template <typename T> struct Precond {
         x1.push_back(x[j]);
       }
       for (int k : G2) x2.push_back(x[k]);
-      // predictor
-      if (G1.size() == 1) vcycle(g0, 0, 0, b1[0], x1[0]);
+      // predictor: one V-cycle, one BGS(AMG) sweep or one AMG(BGS) V-cycle
+      if (g0.mono) mono_cycle(g0, 0, b1, x1);
+      else if (G1.size() == 1) vcycle(g0, 0, 0, b1[0], x1[0]);
       else bgs(g0, b1, x1);
       // Schur right-hand side b_2 - A_21 dx_1
       for (size_t kk = 0; kk < G2.size(); ++kk) {
@@ -1142,11 +1143,22 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
   for (size_t a = 0; a < h->host->G2.size(); ++a) l2[h->host->G2[a]] = (int)a;
   std::vector<HBsr> diag1;
   std::vector<FieldInfo> info1;
+  std::map<int, int> l1;
   for (int j : h->host->G1) {
+    l1[j] = (int)diag1.size();
     diag1.push_back(blocks.at({j, j}));
     info1.push_back(info[j]);
   }
-  group(h->host->hg0, diag1, info1, false, nullptr);
+  // SIMPLE(AMG(BGS)): the predictor group gets a monolithic hierarchy with
+  // blockwise Galerkin coupling blocks
+  const bool mono_pred = p.simple_pred == MFS_PRED_AMG_BGS;
+  BlockMap off1;
+  if (mono_pred)
+    for (auto &kv : blocks) {
+      const int i = kv.first.first, j = kv.first.second;
+      if (i != j && l1.count(i) && l1.count(j)) off1[{l1[i], l1[j]}] = kv.second;
+    }
+  group(h->host->hg0, diag1, info1, mono_pred, mono_pred ? &off1 : nullptr);
   // A~_11: SIMPLEC sums of absolute entries over the merged predictor rows, or the diagonal
   h->host->dtilde.clear();
   for (int j : h->host->G1) {
@@ -1267,7 +1279,7 @@ void upload_precond(mfs_handle *h, Arena &mat, Precond<T> &P, const std::map<std
       if (i != j && l1.count(i) && l1.count(j)) o0[{l1[i], l1[j]}] = fine_sell(i, j);
       if ((l1.count(i) && l2.count(j)) || (l2.count(i) && l1.count(j))) P.cross[kv.first] = fine_sell(i, j);
     }
-    upload_group(mat, P.g0, hs.hg0, p, d0, o0, false);
+    upload_group(mat, P.g0, hs.hg0, p, d0, o0, p.simple_pred == MFS_PRED_AMG_BGS);
     std::vector<dev::Sell> sd0;
     std::map<std::pair<int, int>, dev::Sell> so0;
     for (auto &M : hs.schur_diag) sd0.push_back(upload_sell(mat, M, !f32, f32));
@@ -1346,7 +1358,8 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       p.max_levels < 1 || p.coarse_max < 0 || p.restart < 1 || p.restart > 60 || p.max_iters < 1 ||
       (p.smoother == MFS_CHEBYSHEV && (p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0))) ||
       (p.smoother == MFS_JACOBI && p.jacobi_sweeps < 1) || (p.smoother != MFS_CHEBYSHEV && p.smoother != MFS_JACOBI) ||
-      (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1)
+      (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
+      (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS))
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;

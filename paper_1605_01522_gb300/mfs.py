@@ -22,6 +22,7 @@ NS_CONST, NS_RBM = 0, 1
 FP64, FP32P = 0, 1
 ABSROWSUM, DIAG = 0, 1
 CHEBYSHEV, JACOBI = 0, 1
+PRED_BGS_AMG, PRED_AMG_BGS = 0, 1
 
 PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS, "amg_simple": AMG_SIMPLE}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
@@ -70,7 +71,8 @@ class Params(C.Structure):
                 ("jacobi_omega", C.c_double), ("jacobi_sweeps", C.c_int), ("restart", C.c_int),
                 ("max_iters", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
-                ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int)]
+                ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int),
+                ("simple_pred", C.c_int)]
 
 
 class Info(C.Structure):
@@ -186,6 +188,8 @@ def default_params(**kw) -> Params:
             v = {"absrowsum": ABSROWSUM, "diag": DIAG}[v]
         elif k == "smoother" and isinstance(v, str):
             v = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI}[v]
+        elif k == "simple_pred" and isinstance(v, str):
+            v = {"bgs_amg": PRED_BGS_AMG, "amg_bgs": PRED_AMG_BGS}[v]
         if k == "simple_group":
             arr = (C.c_int * MAX_FIELDS)(*([0] * MAX_FIELDS))
             for i, g in enumerate(v):

@@ -22,6 +22,10 @@ WORKLOADS = {
     "coupled_box_3d_ne64_f3": (lambda: inputs.coupled_box_3d(ne=64, nfields=3, seed=1),
                                dict(max_levels=5, coarse_max=1000),
                                {"bgs_amg": {}, "amg_bgs": {}, "simple": {}, "amg_simple": {}}),
+    # labels "<precond>+<predictor>" select SIMPLE's predictor solver
+    "constrained_box_ne64_f3_m4": (lambda: inputs.constrained_box(ne=64, nfields=3, seed=5),
+                                   dict(max_levels=5, coarse_max=1000),
+                                   {"simple": {}, "simple+amg_bgs": dict(simple_pred="amg_bgs")}),
     "fsi_box_ne48": (lambda: inputs.fsi_box(ne=48, seed=2), dict(max_levels=5, coarse_max=1000),
                      {"bgs_amg": {}, "simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag"),
                       "amg_simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
@@ -46,7 +50,7 @@ def main():
         for pc in pick:
             extra = pcs[pc]
             t0 = time.time()
-            M = precond.Preconditioner(A, specs, precond.Params(pc, **kw, **extra))
+            M = precond.Preconditioner(A, specs, precond.Params(pc.split("+")[0], **kw, **extra))
             t1 = time.time()
             r = krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=400)
             t2 = time.time()

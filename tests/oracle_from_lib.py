@@ -59,24 +59,29 @@ def oracle_preconditioner(lib, system):
         sg = [0] * (nf - 1) + [1]
     g1 = [i for i in range(nf) if sg[i] == 0]
     g2 = [i for i in range(nf) if sg[i] == 1]
+
+    def monolithic(cls, name, Afine, nfg, grp):
+        # AMG(BGS)-type hierarchy of group 0 from the exported blockwise Galerkin blocks
+        mono = cls.__new__(cls)
+        mono.nf = nfg
+        mono.grp = grp
+        mono.prm = precond.Params(name, bgs_order=order, bgs_sweeps=p.bgs_sweeps, smoother=sp_)
+        mono.A = [dict(Afine)]
+        for l in range(1, len(grp.levels)):
+            d = {}
+            for (i, j) in Afine:
+                d[(i, j)] = grp.levels[l][i].A if i == j else lib.export_csr("A", 0, l, i, j)
+            mono.A.append(d)
+        mono.coarse = amg.DenseLU(precond.assemble(mono.A[-1], nfg))
+        return mono
+
     if kind in (0, 2, 3):
         grp = _Grp(_levels(lib, 0, nf, bsz), sp_)
         if kind == 0:
             op = precond.BGS(A, nf, [grp.leaf(i) for i in range(nf)], order, p.bgs_sweeps)
         else:
-            cls = precond.MonoAMG if kind == 2 else precond.MonoAMGSimple
-            mono = cls.__new__(cls)
-            mono.nf = nf
-            mono.grp = grp
-            mono.prm = precond.Params("amg_bgs" if kind == 2 else "amg_simple", bgs_order=order,
-                                      bgs_sweeps=p.bgs_sweeps, smoother=sp_)
-            mono.A = [dict(A)]
-            for l in range(1, len(grp.levels)):
-                d = {}
-                for (i, j) in A:
-                    d[(i, j)] = grp.levels[l][i].A if i == j else lib.export_csr("A", 0, l, i, j)
-                mono.A.append(d)
-            mono.coarse = amg.DenseLU(precond.assemble(mono.A[-1], nf))
+            mono = monolithic(precond.MonoAMG if kind == 2 else precond.MonoAMGSimple,
+                              "amg_bgs" if kind == 2 else "amg_simple", A, nf, grp)
             if kind == 3:
                 # level Schur complements S~^l (group 1) and A~_11 per level
                 mono.g1, mono.g2 = g1, g2
@@ -91,7 +96,9 @@ def oracle_preconditioner(lib, system):
         grp0 = _Grp(_levels(lib, 0, len(g1), [bsz[i] for i in g1]), sp_)
         grp1 = _Grp(_levels(lib, 1, len(g2), [bsz[i] for i in g2]), sp_)
         sub = precond.sub_blocks(A, g1)
-        if len(g1) == 1:
+        if p.simple_pred == 1:
+            pred = monolithic(precond.MonoAMG, "amg_bgs", sub, len(g1), grp0)
+        elif len(g1) == 1:
             leaf = grp0.leaf(0)
             pred = lambda b: [leaf(b[0])]
         else:

@@ -39,6 +39,8 @@ def _small(name):
         return inputs.coupled_box_3d(ne=13, nfields=2), dict(max_levels=3, coarse_max=100)
     if name == "fsi":
         return inputs.fsi_box(ne=8), dict(max_levels=3, coarse_max=100)
+    if name == "cons":
+        return inputs.constrained_box(ne=9), dict(max_levels=3, coarse_max=100)
     raise KeyError(name)
 
 
@@ -77,9 +79,15 @@ AMG_SIMPLE = [("2d", "amg_simple", {}), ("3d", "amg_simple", {}), ("3d", "amg_si
               ("3d", "amg_simple", dict(simple_group=[0, 1, 0], simple_approx="diag")),
               ("3d2", "amg_simple", dict(smoother="jacobi", jacobi_sweeps=2)),
               ("fsi", "amg_simple", dict(simple_group=[0, 0, 0, 1]))]
+# SIMPLE(BGS(AMG)) / SIMPLE(AMG(BGS)) (Sec. 6.3), incl. the constrained box whose
+# multiplier block is zero and whose Schur group is solved by dense LU
+NESTED = [("cons", "simple", {}), ("cons", "simple", dict(simple_pred="amg_bgs")),
+          ("cons", "simple", dict(simple_pred="amg_bgs", simple_approx="diag", bgs_order="sym")),
+          ("3d", "simple", dict(simple_pred="amg_bgs", simple_group=[0, 0, 1])),
+          ("fsi", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag", simple_pred="amg_bgs"))]
 
 
-@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE)
+@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED)
 def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
     s, kw = _small(name)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
@@ -93,10 +101,11 @@ def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
 
 
 @pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI
-                         + AMG_SIMPLE[:4])
+                         + AMG_SIMPLE[:4] + NESTED)
 def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     s, kw = _small(name)
-    okw = {k: v for k, v in extra.items() if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps")}
+    okw = {k: v for k, v in extra.items()
+           if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps", "simple_pred")}
     ro, D = _oracle_solve(s, kw, pc, okw)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
         x, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
@@ -111,7 +120,7 @@ def test_solve_fp64_iterations_match_oracle(name, pc, extra):
 
 @pytest.mark.parametrize("name,pc,extra", [("2d", "bgs_amg", {}), ("3d", "bgs_amg", {}), ("3d", "amg_bgs", {}),
                                            ("3d", "simple", {}), ("fsi", "bgs_amg", {})] + FSI[:1]
-                         + AMG_SIMPLE[1:2])
+                         + AMG_SIMPLE[1:2] + NESTED[:2])
 def test_solve_fp32_preconditioner(name, pc, extra):
     s, kw = _small(name)
     ro, D = _oracle_solve(s, kw, pc, extra)
@@ -168,3 +177,18 @@ def test_dot_matches_host():
             assert abs(d - float(np.dot(x, y))) <= 1e-13 * np.abs(x).max() * np.abs(y).max() * s.ndofs ** 0.5
         with pytest.raises(mfs.MfsError):
             lib.dot(x, y)  # host vectors are rejected
+
+
+def test_zero_diagonal_block_is_refused():
+    """The constrained box's multiplier block is zero: every preconditioner
+    that smooths with D^-1 on that field (BGS(AMG), AMG(BGS), AMG(SIMPLE))
+    must be refused by the GPU setup, as the oracle refuses it."""
+    s, kw = _small("cons")
+    for pc in ("bgs_amg", "amg_bgs", "amg_simple"):
+        with pytest.raises(mfs.MfsError) as e:
+            mfs.Solver(s, precond=pc, **kw)
+        assert e.value.code == mfs.ERR_SINGULAR
+    # the handle-free failure leaves the device usable
+    with mfs.Solver(s, precond="simple", **kw) as lib:
+        _, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
+        assert rc == mfs.OK

@@ -100,3 +100,19 @@ def test_gpu_setup_amg_simple_level_objects(approx):
         assert abs(lg - lh) <= 1e-12 * lh and abs(lh - M.op.S[l].lam) <= 1e-12 * lh
     g.close()
     h.close()
+
+
+def test_gpu_setup_constrained_box_nested_simple():
+    """SIMPLE(AMG(BGS)) on the constrained box: the GPU setup's predictor
+    hierarchy (with coupling blocks) and one-level Schur group equal the host's."""
+    s = inputs.constrained_box(ne=12)
+    kw = dict(max_levels=4, coarse_max=100, simple_pred="amg_bgs")
+    g = mfs.Solver(s, precond="simple", setup_device=1, **kw)
+    h = mfs.Solver(s, precond="simple", setup_only=1, **kw)
+    assert g.num_levels(0) == h.num_levels(0) and g.num_levels(1) == h.num_levels(1) == 1
+    assert _rel(g.export_csr("A", 1, 0, 0, 0), h.export_csr("A", 1, 0, 0, 0)) < TOL
+    for l in range(1, g.num_levels(0)):
+        for (i, j) in [(0, 1), (1, 0), (0, 2), (2, 0), (1, 2), (2, 1)]:
+            assert _rel(g.export_csr("A", 0, l, i, j), h.export_csr("A", 0, l, i, j)) < TOL
+    g.close()
+    h.close()

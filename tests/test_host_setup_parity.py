@@ -104,6 +104,32 @@ def test_amg_simple_level_objects_match_oracle(approx, grp):
     lib.close()
 
 
+@pytest.mark.parametrize("pred", ["bgs_amg", "amg_bgs"])
+def test_constrained_box_simple_objects_match_oracle(pred):
+    """Lung-like constrained box: S~ (4 x 4, from a zero multiplier block) in a
+    one-level Schur group, and for SIMPLE(AMG(BGS)) the predictor group's
+    blockwise Galerkin coupling blocks on every coarse level."""
+    s = inputs.constrained_box(ne=8)
+    kw = dict(max_levels=3, coarse_max=100, simple_pred=pred)
+    lib = mfs.Solver(s, precond="simple", setup_only=1, **kw)
+    M = precond.Preconditioner(s.scipy_blocks(), [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params("simple", **kw))
+    assert lib.num_levels(1) == len(M.groups[1].levels) == 1
+    assert _rel(lib.export_csr("A", 1, 0, 0, 0), M.schur_blocks[(0, 0)]) < TOL
+    L = lib.num_levels(0)
+    assert L == len(M.groups[0].levels) == 3
+    if pred == "amg_bgs":
+        for l in range(1, L):
+            for (i, j), Mij in M.op.pred.A[l].items():
+                if i != j:
+                    assert _rel(lib.export_csr("A", 0, l, i, j), Mij) < TOL
+    lib.close()
+    for pc in ("bgs_amg", "amg_bgs", "amg_simple"):
+        with pytest.raises(mfs.MfsError) as e:
+            mfs.Solver(s, precond=pc, setup_only=1, **kw)
+        assert e.value.code == mfs.ERR_SINGULAR
+
+
 def test_setup_rejects_bad_input():
     s, kw = _get("2d")
     bad = inputs.BlockSystem(s.fields, {k: v for k, v in s.blocks.items() if k != (1, 1)}, s.rhs)
@@ -112,3 +138,5 @@ def test_setup_rejects_bad_input():
     assert e.value.code == mfs.ERR_INVALID
     with pytest.raises(mfs.MfsError):
         mfs.Solver(s, setup_only=1, restart=0)
+    with pytest.raises(mfs.MfsError):
+        mfs.Solver(s, setup_only=1, precond="simple", simple_pred=2)
