@@ -121,3 +121,35 @@ def test_fullsize_matvec_sampled_rows():
         lo, hi = D.indptr[r], D.indptr[r + 1]
         ref = float(np.dot(D.data[lo:hi], xv[D.indices[lo:hi]]))
         assert abs(y[r] - ref) <= 1e-12 * (np.abs(D.data[lo:hi]).sum() * np.abs(xv).max())
+
+
+_CONS = {}
+
+
+def _cons():
+    if "s" not in _CONS:
+        s = inputs.constrained_box(ne=64, nfields=3, seed=5)
+        _CONS["s"] = s
+        _CONS["D"] = precond.assemble(s.scipy_blocks(), 4)
+    return _CONS["s"], _CONS["D"]
+
+
+@pytest.mark.parametrize("pred", ["bgs_amg", "amg_bgs"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32p"])
+def test_fullsize_constrained_box_nested_simple(pred, prec):
+    """Lung-like constrained box (zero multiplier block, Schur group solved by
+    dense LU): SIMPLE(BGS(AMG)) and SIMPLE(AMG(BGS)) against the oracle's
+    stored counts (39 each)."""
+    s, D = _cons()
+    key = "constrained_box_ne64_f3_m4/simple" + ("+amg_bgs" if pred == "amg_bgs" else "")
+    ref = _counts()[key]
+    with mfs.Solver(s, precond="simple", simple_pred=pred, precision=prec, **KW) as lib:
+        assert lib.num_levels(1) == 1
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK
+    assert np.linalg.norm(s.rhs - D @ x) <= 1e-8 * np.linalg.norm(s.rhs)
+    if prec == "fp64":
+        assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    else:
+        assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
