@@ -9,6 +9,15 @@ TEST INFRASTRUCTURE (oracle).
   2003).  The paper's own smoother (Sec. 7.1: additive Schwarz with damped
   Gauss-Seidel) is replaced by this one.
 * damped Jacobi x <- x + omega D^-1 (b - A x), the optional alternative.
+* multicolour damped Gauss-Seidel, the GPU analogue of the paper's DD(GS(omega))
+  (Sec. 7.1, omega = 0.79): nodes are coloured greedily (node_colors) so that
+  no two coupled nodes share a colour; a forward sweep visits the colours in
+  increasing order and inside a node its dofs in increasing order, setting
+  x_p <- x_p + omega (b_p - sum_q a_pq x_q) / a_pp with the latest values,
+  which is SOR(omega) in that ordering; nodes of one colour never couple, so
+  they update together.  Pre-smoothing sweeps forward, post-smoothing
+  backward (colours and dofs in decreasing order), so the V-cycle stays
+  symmetric for symmetric blocks.
 * V-cycle: Algorithm 1 - pre-smooth, restrict the residual, recurse with a
   zero initial guess, prolongate the correction, post-smooth; direct solve on
   the coarsest level.  The coarse operators come from the setup (the
@@ -55,12 +64,67 @@ def jacobi(A, dinv, b, x, omega, sweeps):
     return x
 
 
-def smooth(fl, b, x, sp_):
-    """Apply the single-field level smoother S^l_i of field-level `fl`."""
+# a block (i, j) couples nodes i != j when one of its entries exceeds this
+# fraction of the largest entry of node i's rows (rounding-level Galerkin
+# entries do not count)
+COUPLING_REL = 1e-12
+
+
+def node_colors(A, b):
+    """Greedy node colouring of the point matrix A with b dofs per node: node
+    i (in increasing order) takes the smallest colour not taken by a
+    lower-numbered node it couples with (either direction)."""
+    A = A.tocsr()
+    n = A.shape[0] // b
+    rowmax = np.zeros(n)
+    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
+    np.maximum.at(rowmax, rows // b, np.abs(A.data))
+    nbr = [set() for _ in range(n)]
+    for p in range(A.shape[0]):
+        i = p // b
+        for k in range(A.indptr[p], A.indptr[p + 1]):
+            j = A.indices[k] // b
+            if j != i and abs(A.data[k]) > COUPLING_REL * rowmax[i]:
+                nbr[i].add(j)
+                nbr[j].add(i)
+    color = np.full(n, -1, np.int64)
+    for i in range(n):
+        taken = {color[j] for j in nbr[i] if j < i}
+        c = 0
+        while c in taken:
+            c += 1
+        color[i] = c
+    return color
+
+
+def gauss_seidel(fl, b, x, omega, sweeps, backward=False):
+    """Multicolour damped Gauss-Seidel sweeps (see the module header)."""
+    if getattr(fl, "colors", None) is None:
+        fl.colors = node_colors(fl.A, fl.b)
+    A, nb = fl.A, fl.b
+    d = fl.A.diagonal()
+    ncol = int(fl.colors.max()) + 1 if len(fl.colors) else 0
+    x = x.copy()
+    cols = range(ncol - 1, -1, -1) if backward else range(ncol)
+    dofs = range(nb - 1, -1, -1) if backward else range(nb)
+    for _ in range(sweeps):
+        for c in cols:
+            nodes = np.nonzero(fl.colors == c)[0]
+            for r in dofs:
+                p = nodes * nb + r
+                x[p] = x[p] + omega * (b[p] - A[p] @ x) / d[p]
+    return x
+
+
+def smooth(fl, b, x, sp_, post=False):
+    """Apply the single-field level smoother S^l_i of field-level `fl`
+    (`post`: the application after the coarse correction)."""
     if sp_.kind == "chebyshev":
         return chebyshev(fl.A, fl.dinv, fl.lam, b, x, sp_.degree, sp_.ratio, sp_.boost)
     if sp_.kind == "jacobi":
         return jacobi(fl.A, fl.dinv, b, x, sp_.omega, sp_.sweeps)
+    if sp_.kind == "gs":
+        return gauss_seidel(fl, b, x, sp_.omega, sp_.sweeps, backward=post)
     raise ValueError(sp_.kind)
 
 
@@ -74,5 +138,5 @@ def vcycle(levels, i, coarse_solver, b, sp_, l=0):
     bc = fl.R @ (b - fl.A @ x)
     xc = vcycle(levels, i, coarse_solver, bc, sp_, l + 1)
     x = x + fl.P @ xc
-    x = smooth(fl, b, x, sp_)
+    x = smooth(fl, b, x, sp_, post=True)
     return x

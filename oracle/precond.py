@@ -38,7 +38,7 @@ import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import amg
-from .cycles import SmootherParams, smooth, vcycle
+from .cycles import SmootherParams, gauss_seidel, smooth, vcycle
 
 
 class Params:
@@ -100,6 +100,22 @@ class DirectLeaf:
 
     def __call__(self, b):
         return self.lu.solve(b)
+
+
+class GSLeaf:
+    """Block solver of the single-level BGS(GS): Gauss-Seidel sweeps from zero
+    (forward colour order) on the fine diagonal block."""
+
+    def __init__(self, A, b, sp_):
+        if sp_.kind != "gs":
+            raise ValueError("BGS(GS) needs the Gauss-Seidel smoother")
+        self.fl = amg.FieldLevel(A, b)
+        if not np.all(np.isfinite(self.fl.dinv)):
+            raise ValueError("zero diagonal entry in a diagonal block")
+        self.sp = sp_
+
+    def __call__(self, b):
+        return gauss_seidel(self.fl, b, np.zeros_like(b), self.sp.omega, self.sp.sweeps)
 
 
 class BGS:
@@ -236,7 +252,7 @@ class MonoAMG:
         self.coarse = amg.DenseLU(assemble(self.A[-1], nf))
         self.prm = prm
 
-    def smooth(self, l, b, x):
+    def smooth(self, l, b, x, post=False):
         lv, A = self.grp.levels[l], self.A[l]
         for _ in range(self.prm.bgs_sweeps):
             for seq in sweep_orders(self.prm.bgs_order, self.nf):
@@ -245,7 +261,7 @@ class MonoAMG:
                     for j in range(self.nf):
                         if j != i and (i, j) in A:
                             c = c - A[(i, j)] @ x[j]
-                    x[i] = smooth(lv[i], c, x[i], self.prm.smoother)
+                    x[i] = smooth(lv[i], c, x[i], self.prm.smoother, post)
         return x
 
     def cycle(self, l, b):
@@ -259,7 +275,7 @@ class MonoAMG:
         bc = [lv[l][i].R @ (b[i] - Ax[i]) for i in range(self.nf)]
         xc = self.cycle(l + 1, bc)
         x = [x[i] + lv[l][i].P @ xc[i] for i in range(self.nf)]
-        return self.smooth(l, b, x)
+        return self.smooth(l, b, x, post=True)
 
     def __call__(self, b):
         return self.cycle(0, list(b))
@@ -291,7 +307,7 @@ class MonoAMGSimple(MonoAMG):
             self.dt.append(dt)
             self.S.append(fl)
 
-    def smooth(self, l, b, x):
+    def smooth(self, l, b, x, post=False):
         lv, A, sp_ = self.grp.levels[l], self.A[l], self.prm.smoother
         g1, k = self.g1, self.g2[0]
         for _ in range(self.prm.bgs_sweeps):
@@ -306,12 +322,12 @@ class MonoAMGSimple(MonoAMG):
                         if j != i and (i, j) in A:
                             c = c - A[(i, j)] @ d[j]
                     d[i] = (d[i] if i in d else 0.0) + smooth(lv[i], c - (A[(i, i)] @ d[i] if i in d else 0.0),
-                                                             np.zeros_like(c), sp_)
+                                                             np.zeros_like(c), sp_, post)
             c2 = r[k].copy()
             for j in g1:
                 if (k, j) in A:
                     c2 = c2 - A[(k, j)] @ d[j]
-            d2 = smooth(self.S[l], c2, np.zeros_like(c2), sp_)
+            d2 = smooth(self.S[l], c2, np.zeros_like(c2), sp_, post)
             for jj, j in enumerate(g1):
                 if (j, k) in A:
                     d[j] = d[j] - (A[(j, k)] @ d2) / self.dt[l][jj]
@@ -342,6 +358,12 @@ class Preconditioner:
             self.op = MonoAMGSimple(blocks, specs, prm, nf, g1, g2)
             self.grp = self.op.grp
             self.groups = [self.grp]
+        elif prm.precond == "bgs_gs":
+            # single-level BGS(DD(GS)) of Sec. 7.1 on one subdomain: each block
+            # solve is prm.smoother's Gauss-Seidel sweeps from zero on A_ii
+            leaves = [GSLeaf(blocks[(i, i)], specs[i].b, prm.smoother) for i in range(nf)]
+            self.op = BGS(blocks, nf, leaves, prm.bgs_order, prm.bgs_sweeps)
+            self.groups = []
         elif prm.precond == "simple":
             grp_of = prm.simple_group or [0] * (nf - 1) + [1]
             g1 = [i for i in range(nf) if grp_of[i] == 0]
