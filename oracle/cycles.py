@@ -74,22 +74,20 @@ def node_colors(A, b):
     """Greedy node colouring of the point matrix A with b dofs per node: node
     i (in increasing order) takes the smallest colour not taken by a
     lower-numbered node it couples with (either direction)."""
-    A = A.tocsr()
+    C = A.tocoo()
     n = A.shape[0] // b
+    ri, ci = C.row.astype(np.int64) // b, C.col.astype(np.int64) // b
     rowmax = np.zeros(n)
-    rows = np.repeat(np.arange(A.shape[0]), np.diff(A.indptr))
-    np.maximum.at(rowmax, rows // b, np.abs(A.data))
-    nbr = [set() for _ in range(n)]
-    for p in range(A.shape[0]):
-        i = p // b
-        for k in range(A.indptr[p], A.indptr[p + 1]):
-            j = A.indices[k] // b
-            if j != i and abs(A.data[k]) > COUPLING_REL * rowmax[i]:
-                nbr[i].add(j)
-                nbr[j].add(i)
+    np.maximum.at(rowmax, ri, np.abs(C.data))
+    keep = (ri != ci) & (np.abs(C.data) > COUPLING_REL * rowmax[ri])
+    # symmetrised coupling graph as sorted unique neighbour lists
+    e = np.unique(np.concatenate([ri[keep] * n + ci[keep], ci[keep] * n + ri[keep]]))
+    src, dst = e // n, e % n
+    ptr = np.searchsorted(src, np.arange(n + 1))
     color = np.full(n, -1, np.int64)
     for i in range(n):
-        taken = {color[j] for j in nbr[i] if j < i}
+        nb = dst[ptr[i]:ptr[i + 1]]
+        taken = set(color[nb[nb < i]].tolist())
         c = 0
         while c in taken:
             c += 1

@@ -226,3 +226,11 @@ def test_single_level_bgs_gs_is_not_scalable():
     assert its["bgs_gs"][-1] >= 3 * its["bgs_gs"][0]
     assert its["bgs_amg"][-1] <= 2 * its["bgs_amg"][0] + 2
     assert its["bgs_amg"][-1] < its["bgs_gs"][-1]
+
+
+def test_node_colors_chain_beyond_int32_pairs():
+    """A 60,000-node chain (node pairs beyond 2^31): colours alternate 0, 1."""
+    n = 60000
+    A = sp.diags([np.full(n - 1, -1.0), np.full(n, 4.0), np.full(n - 1, -1.0)], [-1, 0, 1]).tocsr()
+    col = node_colors(A, 1)
+    assert np.array_equal(col, np.arange(n) % 2)
