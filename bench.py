@@ -61,6 +61,7 @@ def workload_config(args, s, extra=None):
     }
     if args.precond == "simple":
         cfg["simple_pred"] = args.simple_pred
+    cfg["smoother"] = "gs" if args.smoother == "gs" or args.precond == "bgs_gs" else "chebyshev"
     cfg.update(extra or {})
     return cfg
 
@@ -209,6 +210,7 @@ def make_system(args=None):
 def counts_key(args):
     name = {"fsi": "fsi_box_ne48", "cons": f"constrained_box_ne{NE}_f3_m4"}.get(args.workload, WORKLOAD)
     pc = args.precond + ("+amg_bgs" if args.precond == "simple" and args.simple_pred == "amg_bgs" else "")
+    pc += "+gs" if args.smoother == "gs" and args.precond != "bgs_gs" else ""
     return name + "/" + pc
 
 
@@ -221,7 +223,18 @@ def precond_extra(args):
         extra = dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
     if args.precond == "simple" and args.simple_pred != "bgs_amg":
         extra["simple_pred"] = args.simple_pred
+    if args.smoother == "gs" or args.precond == "bgs_gs":
+        extra["smoother"] = "gs"
     return extra
+
+
+def oracle_params(name, extra):
+    """The oracle's parameter block for the library options of precond_extra."""
+    from oracle import precond
+    from oracle.cycles import SmootherParams
+    ex = dict(extra)
+    sm = SmootherParams("gs", omega=0.79, sweeps=1) if ex.pop("smoother", None) == "gs" else None
+    return precond.Params(name, **SOLVER_KW, **ex, smoother=sm)
 
 
 def oracle_counts():
@@ -238,7 +251,7 @@ def oracle_sample(s, precond_name, n_iter, extra=None):
     D = precond.assemble(A, s.nfields)
     t0 = time.perf_counter()
     M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields],
-                               precond.Params(precond_name, **SOLVER_KW, **(extra or {})))
+                               oracle_params(precond_name, extra or {}))
     t1 = time.perf_counter()
     krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=n_iter)
     t2 = time.perf_counter()
@@ -260,7 +273,7 @@ def run_reference(args, rank, world):
     D = precond.assemble(A, s.nfields)
     t0 = time.perf_counter()
     M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields],
-                               precond.Params(args.precond, **SOLVER_KW, **precond_extra(args)))
+                               oracle_params(args.precond, precond_extra(args)))
     setup_s = time.perf_counter() - t0
     for k in range(args.warmup + args.steps):
         t1 = time.perf_counter()
@@ -535,7 +548,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mfs", choices=["mfs", "reference"])
-    ap.add_argument("--precond", default="bgs_amg", choices=["bgs_amg", "amg_bgs", "simple", "amg_simple"])
+    ap.add_argument("--precond", default="bgs_amg", choices=["bgs_amg", "amg_bgs", "simple", "amg_simple", "bgs_gs"])
+    ap.add_argument("--smoother", default="chebyshev", choices=["chebyshev", "gs"],
+                    help="level smoother: Chebyshev degree 2, or multicolour damped Gauss-Seidel (omega 0.79)")
     ap.add_argument("--precision", default="fp32p", choices=["fp32p", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")

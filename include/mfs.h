@@ -20,6 +20,10 @@
  *   MFS_AMG_BGS  monolithic AMG with block-diagonal transfers, blockwise
  *                Galerkin coarse blocks and block Gauss-Seidel level smoothing
  *                (Sec. 4.3);
+ *   MFS_BGS_GS   single-level BGS(GS): block Gauss-Seidel whose block solves
+ *                are gs_sweeps multicolour Gauss-Seidel sweeps on the fine
+ *                diagonal blocks (the paper's BGS(DD(GS)) comparison, Sec. 7.1,
+ *                on one subdomain); requires smoother = MFS_GS;
  *   MFS_AMG_SIMPLE the same monolithic V-cycle with a SIMPLE step as level
  *                smoother (Sec. 4.3): per level, one BGS sweep of the
  *                single-field smoothers over the predictor fields, one
@@ -73,12 +77,12 @@ enum mfs_status {
   MFS_ERR_SETUP = -7           /* aggregation could not coarsen a field */
 };
 
-enum mfs_precond { MFS_BGS_AMG = 0, MFS_SIMPLE = 1, MFS_AMG_BGS = 2, MFS_AMG_SIMPLE = 3 };
+enum mfs_precond { MFS_BGS_AMG = 0, MFS_SIMPLE = 1, MFS_AMG_BGS = 2, MFS_AMG_SIMPLE = 3, MFS_BGS_GS = 4 };
 enum mfs_bgs_order { MFS_BWD = 0, MFS_FWD = 1, MFS_SYM = 2 };
 enum mfs_nullspace { MFS_NS_CONST = 0, MFS_NS_RBM = 1 };
 enum mfs_precision { MFS_FP64 = 0, MFS_FP32P = 1 };
 enum mfs_simple_approx { MFS_ABSROWSUM = 0, MFS_DIAG = 1 };
-enum mfs_smoother { MFS_CHEBYSHEV = 0, MFS_JACOBI = 1 };
+enum mfs_smoother { MFS_CHEBYSHEV = 0, MFS_JACOBI = 1, MFS_GS = 2 };
 enum mfs_simple_pred { MFS_PRED_BGS_AMG = 0, MFS_PRED_AMG_BGS = 1 };
 
 /* One nonzero block A_ij as node-level block-CSR (BSR): nbrows x nbcols node
@@ -136,6 +140,9 @@ typedef struct {
                                         (C++/OpenMP); both compute the same hierarchy */
   int simple_pred;                   /* enum mfs_simple_pred: solver of SIMPLE's predictor
                                         group (default MFS_PRED_BGS_AMG) */
+  int gs_sweeps;                     /* MFS_GS: sweeps per smoother application (1) */
+  double gs_omega;                   /* MFS_GS: damping omega of the Gauss-Seidel update (0.79,
+                                        the paper's DD(GS(0.79)), Sec. 7.1); 0 < omega < 2 */
 } mfs_params;
 
 typedef struct {
@@ -246,7 +253,10 @@ int mfs_export_csr(const struct mfs_handle *h, int what, int group, int level, i
  * diagonal A~_11 of predictor field i (double, group 0; level 0 for
  * MFS_SIMPLE, level l for MFS_AMG_SIMPLE).  For MFS_AMG_SIMPLE, group 1
  * holds the level Schur complements S~^l (export_csr what 0, field 0) and
- * their lambda estimates.
+ * their lambda estimates.  3 = Gauss-Seidel colour per node (int32) of a
+ * smoothed level (smoother MFS_GS): greedy first fit in node order, where
+ * nodes i != j couple when an entry of block (i, j) or (j, i) exceeds 1e-12
+ * times the largest entry of that block row.
  * cap = capacity in elements; *count receives the element count. */
 int mfs_export_array(const struct mfs_handle *h, int what, int group, int level, int i,
                      void *buf, int64_t cap, int64_t *count);

@@ -261,6 +261,42 @@ std::vector<double> amg_dinv(const HBsr &A) {
   return f.dinv;
 }
 
+std::vector<int32_t> node_colors(const HBsr &A) {
+  const int64_t n = A.nbr;
+  const int bs = A.br * A.bc;
+  std::vector<double> rowmax(n, 0.0);
+  for (int64_t I = 0; I < n; ++I)
+    for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a)
+      for (int e = 0; e < bs; ++e) rowmax[I] = std::max(rowmax[I], std::fabs(A.v[a * bs + e]));
+  // coupling edges, both directions
+  std::vector<std::vector<int64_t>> nbr(n);
+  for (int64_t I = 0; I < n; ++I)
+    for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a) {
+      const int64_t J = A.ci[a];
+      if (J == I) continue;
+      double m = 0.0;
+      for (int e = 0; e < bs; ++e) m = std::max(m, std::fabs(A.v[a * bs + e]));
+      if (m > 1e-12 * rowmax[I]) {
+        nbr[I].push_back(J);
+        nbr[J].push_back(I);
+      }
+    }
+  std::vector<int32_t> color(n, -1);
+  std::vector<int64_t> mark;  // mark[c] == i: colour c is taken for node i
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j : nbr[i])
+      if (j < i) {
+        const int32_t c = color[j];
+        if ((int64_t)mark.size() <= c) mark.resize(c + 1, -1);
+        mark[c] = i;
+      }
+    int32_t c = 0;
+    while (c < (int32_t)mark.size() && mark[c] == i) ++c;
+    color[i] = c;
+  }
+  return color;
+}
+
 std::vector<double> bsr_to_dense(const HBsr &A) {
   const int64_t nr = A.nrows(), nc = A.ncols();
   std::vector<double> D((size_t)(nr * nc), 0.0);

@@ -40,6 +40,7 @@ struct HLevelField {
   int64_t nagg = 0;
   HBsr P, R;                   // to level l+1
   std::vector<double> B;       // near-nullspace on coarse levels (n x b)
+  std::vector<int32_t> color;  // Gauss-Seidel node colours (smoothed levels, MFS_GS only)
 };
 
 struct HDenseLU {
@@ -68,6 +69,12 @@ HDenseLU dense_lu(int n, std::vector<double> a_rowmajor);
 // diagonal, as used by the setup for every smoothed level
 double amg_power_lambda(const HBsr &A, const std::vector<double> &dinv, uint64_t seed);
 std::vector<double> amg_dinv(const HBsr &A);
+// Greedy node colouring for multicolour Gauss-Seidel: node i (increasing
+// order) takes the smallest colour not held by a lower-numbered node it
+// couples with; i != j couple when some entry of block (i, j) or (j, i)
+// exceeds 1e-12 times the largest entry of that block row (so rounding-level
+// Galerkin entries do not count).
+std::vector<int32_t> node_colors(const HBsr &A);
 std::vector<double> bsr_to_dense(const HBsr &A);
 
 }  // namespace mfs

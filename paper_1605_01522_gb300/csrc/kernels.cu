@@ -100,6 +100,33 @@ __device__ __forceinline__ void bsr_warp_row(const int32_t *__restrict__ rp, con
     for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
 }
 
+// dx of one node from its row sums acc (see gs_color), written into x
+template <int BR, typename T>
+__device__ __forceinline__ void gs_update(const T (&acc)[BR], int64_t node, const T *__restrict__ dblk,
+                                          const T *__restrict__ b, T *x, T omega, bool backward) {
+  const T *D = dblk + node * (BR * BR);
+  T dx[BR];
+  if (!backward) {
+#pragma unroll
+    for (int r = 0; r < BR; ++r) {
+      T res = b[node * BR + r] - acc[r];
+#pragma unroll
+      for (int c = 0; c < r; ++c) res -= D[r * BR + c] * dx[c];
+      dx[r] = omega * res / D[r * BR + r];
+    }
+  } else {
+#pragma unroll
+    for (int r = BR - 1; r >= 0; --r) {
+      T res = b[node * BR + r] - acc[r];
+#pragma unroll
+      for (int c = r + 1; c < BR; ++c) res -= D[r * BR + c] * dx[c];
+      dx[r] = omega * res / D[r * BR + r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r) x[node * BR + r] += dx[r];
+}
+
 template <int BR, typename T>
 __device__ __forceinline__ T pick(const T (&acc)[BR], int r) {
   T a = acc[0];
@@ -221,6 +248,35 @@ k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict_
     d[i] = dd;
     xout[i] = x[i] + dd;
   }
+}
+
+// One colour of a Gauss-Seidel sweep, SELL-32 rows of that colour (one thread each).
+// x is read through the read-only path: within one launch only rows of this
+// colour write x, and those never read each other's entries.
+template <int BR, typename T, int U>
+__global__ void __launch_bounds__(kThreads)
+k_gs(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl, const int32_t *__restrict__ col,
+     const T *__restrict__ val, const int32_t *__restrict__ rowidx, const T *__restrict__ dblk,
+     const T *__restrict__ b, T *x, T omega, int backward) {
+  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nbr) return;
+  T acc[BR];
+  sell_row<BR, BR, T, U>(sp, rl, col, val, x, row, acc);
+  gs_update<BR, T>(acc, rowidx[row], dblk, b, x, omega, backward != 0);
+}
+
+// The same with one warp per row (plain BSR of this colour's rows); lane 0 updates.
+template <int BR, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gs_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const T *__restrict__ val,
+          const int32_t *__restrict__ rowidx, const T *__restrict__ dblk, const T *__restrict__ b, T *x, T omega,
+          int backward) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= nbr) return;
+  T acc[BR];
+  bsr_warp_row<BR, BR, T>(rp, col, val, x, row, lane, acc);
+  if (lane == 0) gs_update<BR, T>(acc, rowidx[row], dblk, b, x, omega, backward != 0);
 }
 
 template <typename T>
@@ -626,6 +682,29 @@ void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaSt
 }
 
 template <typename T>
+void gs_color(const Sell &A, const int32_t *rowidx, const T *dblk, const T *b, T *x, T omega, bool backward,
+              cudaStream_t s) {
+  if (A.nbr == 0) return;
+  const T *v = vals<T>(A);
+  // matrix + gathered x + diagonal blocks + b and x of the colour's rows
+  HookScope hs(s, K_SMOOTH,
+               matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + (A.br + 2.0) * A.nrows()) + 4.0 * A.nbr,
+               (A.kind == 1 ? 5 : (A.unroll == 4 ? 6 : 4)) * 1000 + sparse_sig<T>(A) % 1000, A.nbr,
+               2.0 * A.nnzb * A.br * A.bc + 2.0 * A.br * A.nrows());
+  const int bw = backward ? 1 : 0;
+  if (A.kind == 1) {
+    MFS_SQUARE_DISPATCH(A.br, (k_gs_warp<BR_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.col, v, rowidx, dblk, b, x, omega, bw)));
+  } else if (A.unroll == 4) {
+    MFS_SQUARE_DISPATCH(A.br, (k_gs<BR_, T, 4><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.rl, A.col, v, rowidx, dblk, b, x, omega, bw)));
+  } else {
+    MFS_SQUARE_DISPATCH(A.br, (k_gs<BR_, T, 2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.rl, A.col, v, rowidx, dblk, b, x, omega, bw)));
+  }
+}
+
+template <typename T>
 void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   if (lu.n == 0) return;
   HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n,
@@ -702,6 +781,8 @@ void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, i
   template void smooth_step<T>(const Sell &, const T *, const T *, const T *, T *, T *, T, T,         \
                                cudaStream_t);                                                         \
   template void smooth_first<T>(int64_t, const T *, const T *, T *, T *, T, cudaStream_t);            \
+  template void gs_color<T>(const Sell &, const int32_t *, const T *, const T *, T *, T, bool,           \
+                            cudaStream_t);                                                             \
   template void lu_solve<T>(const DenseLU &, const T *, T *, cudaStream_t);                           \
   template void fill<T>(T *, int64_t, T, cudaStream_t);                                               \
   template void axpy_diag<T>(T *, const T *, const T *, int64_t, cudaStream_t);                       \

@@ -38,7 +38,10 @@ struct Sell {
 // launch's algorithmic byte count); installed by the solver when profiling.
 enum KernelClass { K_SPMV = 0, K_SMOOTH = 1, K_VECTOR = 2, K_COARSE = 3, K_ARNOLDI = 4, K_NCLASS = 5 };
 // sig identifies the kernel variant: for SpMV / smoothing
-// kind*1000 + br*100 + bc*10 + (float64 ? 1 : 0); otherwise a small id.
+// layout*1000 + br*100 + bc*10 + (float64 ? 1 : 0) with layout 0 SELL-32,
+// 1 warp BSR, 2 merged rows, 3 SELL-32 with 4 slots in flight, 4 / 5 / 6 the
+// Gauss-Seidel colour kernels on SELL-32 / warp BSR / SELL-32 x4; otherwise a
+// small id.
 // rows = block rows (sparse kernels) or vector length.
 struct LaunchHook {
   // returns false when this launch is not to be recorded (after() is then skipped)
@@ -84,6 +87,18 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
 // First step from x = 0:  d = c2 * dinv * b;  x = d
 template <typename T>
 void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s);
+
+// One colour of a multicolour damped Gauss-Seidel sweep (SOR(omega) in the
+// order colour, node, dof): A holds the block rows of this colour only (all
+// their blocks), rowidx[k] the node of its row k, dblk the br x br diagonal
+// block of every node (node order, row-major).  For each row's node i, with
+// the sums s = (A x)_i taken from the x before this launch,
+//   forward:  for r = 0..br-1:  dx_r = omega (b_r - s_r - sum_{c<r} D_rc dx_c) / D_rr
+//   backward: for r = br-1..0:  the same with c > r;   x_i += dx.
+// Rows of one colour do not couple, so they update in parallel.
+template <typename T>
+void gs_color(const Sell &A, const int32_t *rowidx, const T *dblk, const T *b, T *x, T omega, bool backward,
+              cudaStream_t s);
 
 // x = LU^-1 b  (dense, one CTA; b, x of type T, arithmetic in float64)
 template <typename T>

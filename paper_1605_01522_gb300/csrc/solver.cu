@@ -247,6 +247,11 @@ template <typename T> struct FL {
   T *dinv = nullptr;
   std::vector<T> c1, c2;  // smoother step coefficients
   T *bv = nullptr, *xv = nullptr, *t = nullptr, *d = nullptr, *r = nullptr, *c = nullptr, *e = nullptr;
+  // multicolour Gauss-Seidel (smoother MFS_GS): the block rows of each colour,
+  // their node indices, and the br x br diagonal block of every node
+  std::vector<dev::Sell> gs;
+  std::vector<const int32_t *> gsrow;
+  T *dblk = nullptr;
 };
 
 template <typename T> struct DGroup {
@@ -288,6 +293,43 @@ static void smoother_coeffs(const mfs_params &p, double lam, std::vector<double>
   }
 }
 
+// Gauss-Seidel data of one smoothed level field: per colour the sub-matrix of
+// its block rows (all their blocks, rows in increasing node order), the node
+// index of each, and every node's diagonal block.
+template <typename T>
+static void upload_gs(Arena &ar, FL<T> &f, const HBsr &A, const std::vector<int32_t> &color) {
+  const bool f32 = std::is_same<T, float>::value;
+  const int bs = A.br * A.bc;
+  std::vector<double> dg((size_t)A.nbr * bs, 0.0);
+  for (int64_t I = 0; I < A.nbr; ++I)
+    for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a)
+      if (A.ci[a] == I) std::copy(A.v.begin() + a * bs, A.v.begin() + (a + 1) * bs, dg.begin() + I * bs);
+  f.dblk = upload_as<T>(ar, dg);
+  int nc = 0;
+  for (int32_t c : color) nc = std::max(nc, c + 1);
+  std::vector<std::vector<int32_t>> rows(nc);
+  for (int64_t I = 0; I < A.nbr; ++I) rows[color[I]].push_back((int32_t)I);
+  f.gs.clear();
+  f.gsrow.clear();
+  for (int c = 0; c < nc; ++c) {
+    HBsr S;
+    S.br = A.br;
+    S.bc = A.bc;
+    S.nbr = (int64_t)rows[c].size();
+    S.nbc = A.nbc;
+    S.rp.assign(1, 0);
+    for (int32_t I : rows[c]) {
+      for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a) {
+        S.ci.push_back(A.ci[a]);
+        S.v.insert(S.v.end(), A.v.begin() + a * bs, A.v.begin() + (a + 1) * bs);
+      }
+      S.rp.push_back((int64_t)S.ci.size());
+    }
+    f.gs.push_back(upload_sell(ar, S, !f32, f32));
+    f.gsrow.push_back(ar.upload(rows[c]));
+  }
+}
+
 // Device copy of a host group's matrices and smoother data (read-only after
 // setup, shared by clones).  level0 gives the Sell objects of the level-0
 // diagonal / off-diagonal blocks (shared with the fine operator).
@@ -317,12 +359,13 @@ static void upload_group(Arena &ar, DGroup<T> &g, const HGroup &h, const mfs_par
         f.c2.assign(c2.begin(), c2.end());
         f.dinv = upload_as<T>(ar, hf.dinv);
       }
+      if (!hf.color.empty()) upload_gs(ar, f, hf.A, hf.color);
     }
     if (l > 0 && mono)
       for (auto &kv : h.off[l]) g.off[l][kv.first] = upload_sell(ar, kv.second, !f32, f32);
   }
   g.cf.resize(g.nf);
-  for (int i = 0; i < g.nf; ++i) g.cf[i] = upload_lu(ar, h.coarse_field[i]);
+  for (int i = 0; i < g.nf && i < (int)h.coarse_field.size(); ++i) g.cf[i] = upload_lu(ar, h.coarse_field[i]);
   if (mono) g.cc = upload_lu(ar, h.coarse_coupled);
 }
 
@@ -364,6 +407,8 @@ template <typename T> static void alloc_group_work(Arena &ar, DGroup<T> &g) {
 
 template <typename T> struct Precond {
   int kind = 0, nf = 0, order = 0, sweeps = 1;
+  int smoother = MFS_CHEBYSHEV, gs_sweeps = 1;
+  T gs_omega = T(0.79);
   std::vector<int64_t> fsize, foff;
   DGroup<T> g0, g1;
   std::vector<int> G1, G2;
@@ -391,8 +436,19 @@ template <typename T> struct Precond {
     }
   }
 
-  // single-field polynomial smoother S^l_i; zero: x enters as 0
-  void smooth(FL<T> &f, const T *rhs, T *x, bool zero) {
+  // single-field smoother S^l_i; zero: x enters as 0; post: the application
+  // after the coarse correction (Gauss-Seidel then sweeps backward)
+  void smooth(FL<T> &f, const T *rhs, T *x, bool zero, bool post = false) {
+    if (smoother == MFS_GS) {
+      if (zero) MFS_CUDA(cudaMemsetAsync(x, 0, f.n * sizeof(T), s));
+      const int nc = (int)f.gs.size();
+      for (int sw = 0; sw < gs_sweeps; ++sw)
+        for (int q = 0; q < nc; ++q) {
+          const int c = post ? nc - 1 - q : q;
+          dev::gs_color<T>(f.gs[c], f.gsrow[c], f.dblk, rhs, x, gs_omega, post, s);
+        }
+      return;
+    }
     const int ns = (int)f.c1.size();
     T *cur = x, *oth = f.t;
     int k0 = 0;
@@ -423,7 +479,7 @@ template <typename T> struct Precond {
     dev::spmv<T>(f.R, f.r, c.bv, T(1), T(0), nullptr, s);
     vcycle(g, i, l + 1, c.bv, c.xv);
     dev::spmv<T>(f.P, c.xv, x, T(1), T(1), x, s);
-    smooth(f, rhs, x, false);
+    smooth(f, rhs, x, false, true);
   }
 
   static std::vector<std::vector<int>> orders(int order, int nf) {
@@ -435,6 +491,13 @@ template <typename T> struct Precond {
     if (order == MFS_FWD) return {fwd};
     if (order == MFS_BWD) return {bwd};
     return {fwd, bwd};
+  }
+
+  // block solve of BGS: one V-cycle, or for the single-level BGS(GS) the
+  // Gauss-Seidel sweeps from zero on the fine block
+  void leaf(DGroup<T> &g, int i, const T *rhs, T *x) {
+    if (kind == MFS_BGS_GS) smooth(g.lv[0][i], rhs, x, true, false);
+    else vcycle(g, i, 0, rhs, x);
   }
 
   // block Gauss-Seidel on level 0 of group g with V-cycle block solves
@@ -453,16 +516,17 @@ template <typename T> struct Precond {
             rhs = f.c;
           }
           if (!nz[i]) {
-            vcycle(g, i, 0, rhs, x[i]);
+            leaf(g, i, rhs, x[i]);
             nz[i] = 1;
           } else {
-            vcycle(g, i, 0, rhs, f.e);
+            leaf(g, i, rhs, f.e);
             dev::axpy<T>(x[i], f.e, T(1), f.n, s);
           }
         }
   }
 
-  void mono_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero) {
+  void mono_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero,
+                   bool post) {
     std::vector<char> nz(g.nf, zero ? 0 : 1);
     for (int sw = 0; sw < sweeps; ++sw)
       for (auto &seq : orders(order, g.nf))
@@ -476,7 +540,7 @@ template <typename T> struct Precond {
             dev::spmv<T>(*M, x[j], f.c, T(-1), T(1), rhs, s);
             rhs = f.c;
           }
-          smooth(f, rhs, x[i], !nz[i]);
+          smooth(f, rhs, x[i], !nz[i], post);
           nz[i] = 1;
         }
   }
@@ -512,15 +576,17 @@ template <typename T> struct Precond {
     level_smooth(g, l, b, x, false);
   }
 
+  // pre-smoothing enters with x = 0, post-smoothing after the coarse correction
   void level_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero) {
-    if (kind == MFS_AMG_SIMPLE) simple_smooth(g, l, b, x, zero);
-    else mono_smooth(g, l, b, x, zero);
+    if (kind == MFS_AMG_SIMPLE) simple_smooth(g, l, b, x, zero, !zero);
+    else mono_smooth(g, l, b, x, zero, !zero);
   }
 
   // AMG(SIMPLE) level smoother: r = b - A x; one BGS sweep of the field
   // smoothers over the predictor fields (into e); one smoother application on
   // S~^l (into its e); e_1 -= A~11^-1 A_12 e_2; x += e.
-  void simple_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero) {
+  void simple_smooth(DGroup<T> &g, int l, const std::vector<const T *> &b, const std::vector<T *> &x, bool zero,
+                     bool post) {
     const int k = G2[0];
     FL<T> &sk = ms[l];
     for (int sw = 0; sw < sweeps; ++sw) {
@@ -554,10 +620,10 @@ template <typename T> struct Precond {
             rhs = f.c;
           }
           if (!done[i]) {
-            smooth(f, rhs, f.e, true);
+            smooth(f, rhs, f.e, true, post);
             done[i] = 1;
           } else {  // second visit of a symmetric sweep: correction form
-            smooth(f, rhs, f.e, false);
+            smooth(f, rhs, f.e, false, post);
           }
         }
       const T *rhs2 = r[k];
@@ -567,7 +633,7 @@ template <typename T> struct Precond {
         dev::spmv<T>(*M, g.lv[l][j].e, sk.c, T(-1), T(1), rhs2, s);
         rhs2 = sk.c;
       }
-      smooth(sk, rhs2, sk.e, true);
+      smooth(sk, rhs2, sk.e, true, post);
       for (int jj = 0; jj < n1; ++jj) {
         const int j = G1[jj];
         const dev::Sell *M = g.block(l, j, k);
@@ -594,7 +660,7 @@ template <typename T> struct Precond {
       b[i] = in + foff[i];
       x[i] = out + foff[i];
     }
-    if (kind == MFS_BGS_AMG) {
+    if (kind == MFS_BGS_AMG || kind == MFS_BGS_GS) {
       bgs(g0, b, x);
     } else if (kind == MFS_AMG_BGS || kind == MFS_AMG_SIMPLE) {
       mono_cycle(g0, 0, b, x);
@@ -1056,6 +1122,21 @@ std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, 
 }
 
 // Host half of the setup: hierarchies, SIMPLE diagonal and explicit S~.
+// Multicolour Gauss-Seidel colours of every smoothed level field (levels
+// below the coarsest; every level of the single-level BGS(GS) and of
+// AMG(SIMPLE)'s level Schur complements).
+void color_levels(mfs_handle *h) {
+  const mfs_params &p = h->prm;
+  if (p.smoother != MFS_GS) return;
+  auto run = [](HGroup &g, bool all) {
+    for (int l = 0; l < g.nlevels(); ++l)
+      if (all || l + 1 < g.nlevels())
+        for (auto &f : g.lv[l]) f.color = node_colors(f.A);
+  };
+  run(h->host->hg0, p.precond == MFS_BGS_GS);
+  run(h->host->hg1, p.precond == MFS_AMG_SIMPLE);
+}
+
 void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks,
                 const std::vector<FieldInfo> &info) {
   const mfs_params &p = h->prm;
@@ -1077,6 +1158,19 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
     if (h->host->G1.empty() || h->host->G2.empty())
       throw SetupError(MFS_ERR_INVALID, "SIMPLE needs a non-empty predictor and Schur group");
   };
+  if (p.precond == MFS_BGS_GS) {
+    // single level: the fine diagonal blocks and their smoother data only
+    HGroup &g = h->host->hg0;
+    g.nf = h->nf;
+    g.info = info;
+    g.lv.assign(1, std::vector<HLevelField>(h->nf));
+    g.off.assign(1, BlockMap());
+    for (int i = 0; i < h->nf; ++i) {
+      g.lv[0][i].A = blocks.at({i, i});
+      g.lv[0][i].dinv = amg_dinv(g.lv[0][i].A);
+    }
+    return;
+  }
   if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE) {
     std::vector<HBsr> diag;
     BlockMap off;
@@ -1236,13 +1330,17 @@ void upload_precond(mfs_handle *h, Arena &mat, Precond<T> &P, const std::map<std
   P.foff = h->foff;
   P.s = h->s;
   auto fine_sell = [&](int i, int j) { return h->A64.at({i, j}); };
-  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE) {
+  P.smoother = p.smoother;
+  P.gs_sweeps = p.gs_sweeps;
+  P.gs_omega = (T)p.gs_omega;
+  if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE ||
+      p.precond == MFS_BGS_GS) {
     std::vector<dev::Sell> d0;
     std::map<std::pair<int, int>, dev::Sell> o0;
     for (int i = 0; i < h->nf; ++i) d0.push_back(fine_sell(i, i));
     for (auto &kv : blocks)
       if (kv.first.first != kv.first.second) o0[kv.first] = fine_sell(kv.first.first, kv.first.second);
-    upload_group(mat, P.g0, hs.hg0, p, d0, o0, p.precond != MFS_BGS_AMG);
+    upload_group(mat, P.g0, hs.hg0, p, d0, o0, p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE);
     if (p.precond == MFS_AMG_SIMPLE) {
       P.G1 = hs.G1;
       P.G2 = hs.G2;
@@ -1258,6 +1356,7 @@ void upload_precond(mfs_handle *h, Arena &mat, Precond<T> &P, const std::map<std
         f.c1.assign(c1.begin(), c1.end());
         f.c2.assign(c2.begin(), c2.end());
         f.dinv = upload_as<T>(mat, hf.dinv);
+        if (!hf.color.empty()) upload_gs(mat, f, hf.A, hf.color);
         for (auto &d : hs.mono_dtilde[l]) {
           std::vector<double> inv(d.size());
           for (size_t r = 0; r < inv.size(); ++r) inv[r] = 1.0 / d[r];
@@ -1338,6 +1437,8 @@ void mfs_default_params(mfs_params *p) {
   p->cheb_boost = 1.1;
   p->jacobi_omega = 2.0 / 3.0;
   p->jacobi_sweeps = 1;
+  p->gs_sweeps = 1;
+  p->gs_omega = 0.79;
   p->restart = 50;
   p->max_iters = 1000;
   p->precision = MFS_FP64;
@@ -1354,10 +1455,13 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
   if (!blocks || !fields || !params || nfields < 1 || nfields > MFS_MAX_FIELDS || nblocks < nfields)
     return fail(MFS_ERR_INVALID, "bad block/field arguments");
   const mfs_params &p = *params;
-  if (p.precond < 0 || p.precond > 3 || p.bgs_order < 0 || p.bgs_order > 2 || p.bgs_sweeps < 1 ||
+  if (p.precond < 0 || p.precond > 4 || p.bgs_order < 0 || p.bgs_order > 2 || p.bgs_sweeps < 1 ||
       p.max_levels < 1 || p.coarse_max < 0 || p.restart < 1 || p.restart > 60 || p.max_iters < 1 ||
       (p.smoother == MFS_CHEBYSHEV && (p.cheb_degree < 1 || !(p.cheb_ratio > 1.0) || !(p.cheb_boost > 0.0))) ||
-      (p.smoother == MFS_JACOBI && p.jacobi_sweeps < 1) || (p.smoother != MFS_CHEBYSHEV && p.smoother != MFS_JACOBI) ||
+      (p.smoother == MFS_JACOBI && p.jacobi_sweeps < 1) ||
+      (p.smoother != MFS_CHEBYSHEV && p.smoother != MFS_JACOBI && p.smoother != MFS_GS) ||
+      (p.smoother == MFS_GS && (p.gs_sweeps < 1 || !(p.gs_omega > 0.0) || !(p.gs_omega < 2.0))) ||
+      (p.precond == MFS_BGS_GS && p.smoother != MFS_GS) ||
       (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
       (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS))
     return fail(MFS_ERR_INVALID, "bad parameters");
@@ -1409,6 +1513,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     for (int i = 0; i < nfields; ++i)
       if (!hb.count({i, i})) throw SetupError(MFS_ERR_INVALID, "missing diagonal block");
     build_host(h.get(), hb, info);
+    color_levels(h.get());
     h->host_only = host_only;
     if (host_only) {
       h->setup_ms = now_ms() - t0;
@@ -1733,6 +1838,10 @@ int mfs_export_array(const mfs_handle *h, int what, int group, int level, int i,
     if (!src || i >= (int)src->size()) return fail(MFS_ERR_INVALID, "no SIMPLE diagonal");
     *count = (int64_t)(*src)[i].size();
     if (buf && cap >= *count) std::memcpy(buf, (*src)[i].data(), (*src)[i].size() * sizeof(double));
+  } else if (what == 3) {
+    if (f.color.empty()) return fail(MFS_ERR_INVALID, "no Gauss-Seidel colours on this level");
+    *count = (int64_t)f.color.size();
+    if (buf && cap >= *count) std::memcpy(buf, f.color.data(), f.color.size() * sizeof(int32_t));
   } else {
     return fail(MFS_ERR_INVALID, "bad export kind");
   }

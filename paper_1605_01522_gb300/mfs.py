@@ -16,15 +16,15 @@ from . import build as _build
 
 MAX_FIELDS = 8
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_SINGULAR, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6, -7
-BGS_AMG, SIMPLE, AMG_BGS, AMG_SIMPLE = 0, 1, 2, 3
+BGS_AMG, SIMPLE, AMG_BGS, AMG_SIMPLE, BGS_GS = 0, 1, 2, 3, 4
 BWD, FWD, SYM = 0, 1, 2
 NS_CONST, NS_RBM = 0, 1
 FP64, FP32P = 0, 1
 ABSROWSUM, DIAG = 0, 1
-CHEBYSHEV, JACOBI = 0, 1
+CHEBYSHEV, JACOBI, GS = 0, 1, 2
 PRED_BGS_AMG, PRED_AMG_BGS = 0, 1
 
-PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS, "amg_simple": AMG_SIMPLE}
+PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS, "amg_simple": AMG_SIMPLE, "bgs_gs": BGS_GS}
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
@@ -45,7 +45,8 @@ def kernel_name(key: int) -> str:
         br, rest = divmod(rest, 100)
         bc, f64 = divmod(rest, 10)
         base = "spmv" if cls == 0 else "smooth"
-        layout = {0: "sell", 1: "warp", 2: "rows", 3: "sell4"}.get(kind, str(kind))
+        layout = {0: "sell", 1: "warp", 2: "rows", 3: "sell4", 4: "gs_sell", 5: "gs_warp",
+                  6: "gs_sell4"}.get(kind, str(kind))
         return f"{base}_{layout}<{br}x{bc},{'f64' if f64 else 'f32'}>"
     return _OTHER.get(cls, {}).get(sig, f"class{cls}_id{sig}")
 
@@ -72,7 +73,7 @@ class Params(C.Structure):
                 ("max_iters", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
                 ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int),
-                ("simple_pred", C.c_int)]
+                ("simple_pred", C.c_int), ("gs_sweeps", C.c_int), ("gs_omega", C.c_double)]
 
 
 class Info(C.Structure):
@@ -187,7 +188,7 @@ def default_params(**kw) -> Params:
         elif k == "simple_approx" and isinstance(v, str):
             v = {"absrowsum": ABSROWSUM, "diag": DIAG}[v]
         elif k == "smoother" and isinstance(v, str):
-            v = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI}[v]
+            v = {"chebyshev": CHEBYSHEV, "jacobi": JACOBI, "gs": GS}[v]
         elif k == "simple_pred" and isinstance(v, str):
             v = {"bgs_amg": PRED_BGS_AMG, "amg_bgs": PRED_AMG_BGS}[v]
         if k == "simple_group":
@@ -330,13 +331,14 @@ class Solver:
         return sp.csr_matrix((vv, ci, rp), shape=(nr.value, nc.value))
 
     def export_array(self, what, group, level, i):
-        """what: 'agg' (int32 per node), 'lambda' (float), 'dtilde' (float64)."""
-        w = {"agg": 0, "lambda": 1, "dtilde": 2}[what]
+        """what: 'agg' (int32 per node), 'lambda' (float), 'dtilde' (float64),
+        'colors' (int32 per node, Gauss-Seidel smoother)."""
+        w = {"agg": 0, "lambda": 1, "dtilde": 2, "colors": 3}[what]
         cnt = C.c_int64()
         rc = self.lib.mfs_export_array(self.h, w, group, level, i, None, 0, C.byref(cnt))
         if rc != OK:
             raise MfsError(rc, "mfs_export_array")
-        buf = np.zeros(cnt.value, np.int32 if w == 0 else np.float64)
+        buf = np.zeros(cnt.value, np.int32 if w in (0, 3) else np.float64)
         rc = self.lib.mfs_export_array(self.h, w, group, level, i, buf.ctypes.data, cnt.value, C.byref(cnt))
         if rc != OK:
             raise MfsError(rc, "mfs_export_array")

@@ -15,14 +15,16 @@ ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__)
 sys.path.insert(0, ROOT)
 
 from oracle import amg, krylov, precond  # noqa: E402
+from oracle.cycles import SmootherParams  # noqa: E402
 from paper_1605_01522_gb300 import inputs  # noqa: E402
 
 # workload name -> (generator, solver parameters)
 WORKLOADS = {
     "coupled_box_3d_ne64_f3": (lambda: inputs.coupled_box_3d(ne=64, nfields=3, seed=1),
                                dict(max_levels=5, coarse_max=1000),
-                               {"bgs_amg": {}, "amg_bgs": {}, "simple": {}, "amg_simple": {}}),
-    # labels "<precond>+<predictor>" select SIMPLE's predictor solver
+                               {"bgs_amg": {}, "amg_bgs": {}, "simple": {}, "amg_simple": {},
+                                "bgs_amg+gs": dict(smoother="gs")}),
+    # labels "<precond>+<option>" select SIMPLE's predictor solver or the smoother
     "constrained_box_ne64_f3_m4": (lambda: inputs.constrained_box(ne=64, nfields=3, seed=5),
                                    dict(max_levels=5, coarse_max=1000),
                                    {"simple": {}, "simple+amg_bgs": dict(simple_pred="amg_bgs")}),
@@ -50,7 +52,10 @@ def main():
         for pc in pick:
             extra = pcs[pc]
             t0 = time.time()
-            M = precond.Preconditioner(A, specs, precond.Params(pc.split("+")[0], **kw, **extra))
+            ex = dict(extra)
+            if ex.pop("smoother", None) == "gs":
+                ex["smoother"] = SmootherParams("gs", omega=0.79, sweeps=1)
+            M = precond.Preconditioner(A, specs, precond.Params(pc.split("+")[0], **kw, **ex))
             t1 = time.time()
             r = krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=400)
             t2 = time.time()

@@ -10,8 +10,17 @@ from oracle import amg, precond
 from oracle.cycles import SmootherParams
 
 
-def _levels(lib, group, nf, blocks_b):
+def _colors(lib, fl, group, l, i):
+    """Gauss-Seidel colours exported by the library (equal to the oracle's own
+    node_colors on the same matrix; taken over so both sweep one order)."""
+    c = lib.export_array("colors", group, l, i)
+    fl.colors = c
+    fl.b = fl.A.shape[0] // len(c)
+
+
+def _levels(lib, group, nf, blocks_b, smoothed_all=False):
     L = lib.num_levels(group)
+    gs = lib.params.smoother == 2
     levels = []
     for l in range(L):
         row = []
@@ -23,6 +32,8 @@ def _levels(lib, group, nf, blocks_b):
                 fl.R = lib.export_csr("R", group, l, i)
                 fl.lam = lib.export_array("lambda", group, l, i)
                 fl.agg = lib.export_array("agg", group, l, i)
+            if gs and (l < L - 1 or smoothed_all):
+                _colors(lib, fl, group, l, i)
             row.append(fl)
         levels.append(row)
     return levels
@@ -39,6 +50,8 @@ class _Grp:
 
 
 def smoother_params(p):
+    if p.smoother == 2:
+        return SmootherParams("gs", omega=p.gs_omega, sweeps=p.gs_sweeps)
     if p.smoother == 1:
         return SmootherParams("jacobi", omega=p.jacobi_omega, sweeps=p.jacobi_sweeps)
     return SmootherParams("chebyshev", degree=p.cheb_degree, ratio=p.cheb_ratio, boost=p.cheb_boost)
@@ -75,6 +88,15 @@ def oracle_preconditioner(lib, system):
         mono.coarse = amg.DenseLU(precond.assemble(mono.A[-1], nfg))
         return mono
 
+    if kind == 4:
+        # single-level BGS(GS): Gauss-Seidel sweeps on the exported fine blocks
+        leaves = []
+        for i in range(nf):
+            lf = precond.GSLeaf(lib.export_csr("A", 0, 0, i, i), bsz[i], sp_)
+            _colors(lib, lf.fl, 0, 0, i)
+            leaves.append(lf)
+        op = precond.BGS(A, nf, leaves, order, p.bgs_sweeps)
+        return lambda v: np.concatenate(op(precond.split(v, sizes)))
     if kind in (0, 2, 3):
         grp = _Grp(_levels(lib, 0, nf, bsz), sp_)
         if kind == 0:
@@ -89,6 +111,8 @@ def oracle_preconditioner(lib, system):
                 for l in range(len(grp.levels) - 1):
                     fl = amg.FieldLevel(lib.export_csr("A", 1, l, 0, 0), None)
                     fl.lam = lib.export_array("lambda", 1, l, 0)
+                    if p.smoother == 2:
+                        _colors(lib, fl, 1, l, 0)
                     mono.S.append(fl)
                     mono.dt.append([lib.export_array("dtilde", 0, l, jj) for jj in range(len(g1))])
             op = mono

@@ -18,6 +18,7 @@ import pytest
 torch = pytest.importorskip("torch")
 
 from oracle import amg, krylov, precond
+from oracle.cycles import SmootherParams
 from paper_1605_01522_gb300 import inputs, mfs
 from tests.oracle_from_lib import oracle_preconditioner
 
@@ -44,10 +45,25 @@ def _small(name):
     raise KeyError(name)
 
 
+def _oracle_params(pc, kw, extra):
+    """Oracle parameters for the library options in `extra`."""
+    ex = dict(extra)
+    kind = ex.pop("smoother", "chebyshev")
+    if kind == "gs":
+        spk = dict(omega=ex.pop("gs_omega", 0.79), sweeps=ex.pop("gs_sweeps", 1))
+    elif kind == "jacobi":
+        spk = dict(omega=ex.pop("jacobi_omega", 2.0 / 3.0), sweeps=ex.pop("jacobi_sweeps", 1))
+    else:
+        spk = dict(degree=ex.pop("cheb_degree", 2))
+    ex = {k: v for k, v in ex.items()
+          if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps", "simple_pred")}
+    return precond.Params(pc, **kw, **ex, smoother=SmootherParams(kind, **spk))
+
+
 def _oracle_solve(s, kw, pc, extra):
     A = s.scipy_blocks()
     D = precond.assemble(A, s.nfields)
-    prm = precond.Params(pc, **kw, **extra)
+    prm = _oracle_params(pc, kw, extra)
     M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], prm)
     return krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=600), D
 
@@ -85,9 +101,16 @@ NESTED = [("cons", "simple", {}), ("cons", "simple", dict(simple_pred="amg_bgs")
           ("cons", "simple", dict(simple_pred="amg_bgs", simple_approx="diag", bgs_order="sym")),
           ("3d", "simple", dict(simple_pred="amg_bgs", simple_group=[0, 0, 1])),
           ("fsi", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag", simple_pred="amg_bgs"))]
+# multicolour damped Gauss-Seidel smoothing (the paper's DD(GS(omega)), Sec. 7.1)
+# and the single-level BGS(GS)
+GS = [("2d", "bgs_amg", dict(smoother="gs")), ("3d", "amg_bgs", dict(smoother="gs")),
+      ("3d", "simple", dict(smoother="gs", simple_group=[0, 0, 1])),
+      ("3d2", "amg_simple", dict(smoother="gs", gs_sweeps=2, gs_omega=1.0)),
+      ("3d", "bgs_gs", dict(smoother="gs")), ("2d", "bgs_gs", dict(smoother="gs", gs_omega=0.69, bgs_order="sym")),
+      ("cons", "simple", dict(smoother="gs", simple_pred="amg_bgs"))]
 
 
-@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED)
+@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED + GS)
 def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
     s, kw = _small(name)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
@@ -101,12 +124,10 @@ def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
 
 
 @pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI
-                         + AMG_SIMPLE[:4] + NESTED)
+                         + AMG_SIMPLE[:4] + NESTED + GS)
 def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     s, kw = _small(name)
-    okw = {k: v for k, v in extra.items()
-           if k in ("simple_group", "simple_approx", "bgs_order", "bgs_sweeps", "simple_pred")}
-    ro, D = _oracle_solve(s, kw, pc, okw)
+    ro, D = _oracle_solve(s, kw, pc, extra)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
         x, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
         x = x.cpu().numpy()
@@ -114,13 +135,14 @@ def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     true = np.linalg.norm(s.rhs - D @ x) / np.linalg.norm(s.rhs)
     assert true <= 1e-8
     assert abs(true - info["true_relres"]) <= 1e-3 * true + 1e-15
-    assert abs(info["iters"] - ro.iters) <= 1, (info["iters"], ro.iters)
+    # +-1, or +-1 % for long restarted runs (rounding differences accumulate over restarts)
+    assert abs(info["iters"] - ro.iters) <= max(1, round(0.01 * ro.iters)), (info["iters"], ro.iters)
     assert np.linalg.norm(x - ro.x) <= 1e-6 * np.linalg.norm(ro.x)
 
 
 @pytest.mark.parametrize("name,pc,extra", [("2d", "bgs_amg", {}), ("3d", "bgs_amg", {}), ("3d", "amg_bgs", {}),
                                            ("3d", "simple", {}), ("fsi", "bgs_amg", {})] + FSI[:1]
-                         + AMG_SIMPLE[1:2] + NESTED[:2])
+                         + AMG_SIMPLE[1:2] + NESTED[:2] + GS[:2] + GS[4:5])
 def test_solve_fp32_preconditioner(name, pc, extra):
     s, kw = _small(name)
     ro, D = _oracle_solve(s, kw, pc, extra)

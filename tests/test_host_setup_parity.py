@@ -130,6 +130,38 @@ def test_constrained_box_simple_objects_match_oracle(pred):
         assert e.value.code == mfs.ERR_SINGULAR
 
 
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_simple", "bgs_gs"])
+def test_gauss_seidel_colours_match_oracle(pc):
+    """Multicolour Gauss-Seidel: the library's greedy colours of every smoothed
+    level equal the oracle's node_colors on the oracle's own level matrices."""
+    from oracle.cycles import SmootherParams, node_colors
+    s, kw = _get("3d")
+    lib = mfs.Solver(s, precond=pc, smoother="gs", setup_only=1, seed=7, **kw)
+    M = precond.Preconditioner(s.scipy_blocks(), [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params(pc, seed=7, smoother=SmootherParams("gs"), **kw))
+    if pc == "bgs_gs":
+        assert lib.num_levels(0) == 1
+        for i, lf in enumerate(M.op.solvers):
+            assert np.array_equal(lib.export_array("colors", 0, 0, i), node_colors(lf.fl.A, lf.fl.b))
+        lib.close()
+        return
+    lv = M.groups[0].levels
+    n = 0
+    for l in range(len(lv) - 1):
+        for i in range(s.nfields):
+            c = lib.export_array("colors", 0, l, i)
+            assert np.array_equal(c, node_colors(lv[l][i].A, lv[l][i].A.shape[0] // len(c)))
+            n += 1
+    if pc == "amg_simple":
+        for l, fl in enumerate(M.op.S):
+            c = lib.export_array("colors", 1, l, 0)
+            assert np.array_equal(c, node_colors(fl.A, fl.A.shape[0] // len(c)))
+    with pytest.raises(mfs.MfsError):
+        lib.export_array("colors", 0, len(lv) - 1, 0)
+    lib.close()
+    assert n >= 6
+
+
 def test_setup_rejects_bad_input():
     s, kw = _get("2d")
     bad = inputs.BlockSystem(s.fields, {k: v for k, v in s.blocks.items() if k != (1, 1)}, s.rhs)
@@ -140,3 +172,7 @@ def test_setup_rejects_bad_input():
         mfs.Solver(s, setup_only=1, restart=0)
     with pytest.raises(mfs.MfsError):
         mfs.Solver(s, setup_only=1, precond="simple", simple_pred=2)
+    with pytest.raises(mfs.MfsError):
+        mfs.Solver(s, setup_only=1, precond="bgs_gs")  # needs the Gauss-Seidel smoother
+    with pytest.raises(mfs.MfsError):
+        mfs.Solver(s, setup_only=1, smoother="gs", gs_omega=2.0)
