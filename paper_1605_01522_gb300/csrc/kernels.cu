@@ -13,6 +13,7 @@ namespace dev {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kGsCtaThreads = 1024;  // threads of the one-CTA Gauss-Seidel kernel for small levels
 LaunchHook *g_hook = nullptr;
 
 struct HookScope {
@@ -100,7 +101,7 @@ __device__ __forceinline__ void bsr_warp_row(const int32_t *__restrict__ rp, con
     for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
 }
 
-// dx of one node from its row sums acc (see gs_color), written into x
+// dx of one node from its row sums acc (see gs_sweeps), written into x
 template <int BR, typename T>
 __device__ __forceinline__ void gs_update(const T (&acc)[BR], int64_t node, const T *__restrict__ dblk,
                                           const T *__restrict__ b, T *x, T omega, bool backward) {
@@ -250,33 +251,96 @@ k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict_
   }
 }
 
-// One colour of a Gauss-Seidel sweep, SELL-32 rows of that colour (one thread each).
-// x is read through the read-only path: within one launch only rows of this
-// colour write x, and those never read each other's entries.
-template <int BR, typename T, int U>
-__global__ void __launch_bounds__(kThreads)
-k_gs(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl, const int32_t *__restrict__ col,
-     const T *__restrict__ val, const int32_t *__restrict__ rowidx, const T *__restrict__ dblk,
-     const T *__restrict__ b, T *x, T omega, int backward) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nbr) return;
-  T acc[BR];
-  sell_row<BR, BR, T, U>(sp, rl, col, val, x, row, acc);
-  gs_update<BR, T>(acc, rowidx[row], dblk, b, x, omega, backward != 0);
+// G lanes per row of a plain BSR matrix: the lanes of a group stride over the
+// row's blocks, then a fixed xor-butterfly inside the group sums them.  x goes
+// through the read-only path: in a one-colour launch only rows of that colour
+// write x, and they never read each other's entries (earlier colours wrote in
+// earlier launches).
+template <int BR, int G, typename T>
+__device__ __forceinline__ void gs_group_row(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                             const T *__restrict__ val, const T *x, int64_t row, bool active,
+                                             int gl, T (&acc)[BR]) {
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+  const int lo = active ? rp[row] : 0, hi = active ? rp[row + 1] : 0;
+  for (int k = lo + gl; k < hi; k += G) {
+    const int64_t c = __ldg(col + k);
+    T xv[BR];
+#pragma unroll
+    for (int q = 0; q < BR; ++q) xv[q] = __ldg(x + c * BR + q);
+    const T *v = val + (int64_t)k * (BR * BR);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BR; ++q) acc[r] += __ldg(v + r * BR + q) * xv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
 }
 
-// The same with one warp per row (plain BSR of this colour's rows); lane 0 updates.
-template <int BR, typename T>
+// One colour: reordered rows [r0, r1), G lanes per row.
+template <int BR, typename T, int G>
 __global__ void __launch_bounds__(kThreads)
-k_gs_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col, const T *__restrict__ val,
-          const int32_t *__restrict__ rowidx, const T *__restrict__ dblk, const T *__restrict__ b, T *x, T omega,
-          int backward) {
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (row >= nbr) return;
+k_gs_color(int64_t r0, int64_t r1, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+           const T *__restrict__ val, const int32_t *__restrict__ rowidx, const T *__restrict__ dblk,
+           const T *__restrict__ b, T *x, T omega, int backward) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t row = r0 + t / G;
+  const int gl = (int)(t % G);
+  const bool active = row < r1;
   T acc[BR];
-  bsr_warp_row<BR, BR, T>(rp, col, val, x, row, lane, acc);
-  if (lane == 0) gs_update<BR, T>(acc, rowidx[row], dblk, b, x, omega, backward != 0);
+  gs_group_row<BR, G, T>(rp, col, val, x, row, active, gl, acc);
+  if (active && gl == 0) gs_update<BR, T>(acc, rowidx[row], dblk, b, x, omega, backward != 0);
+}
+
+// All colours and sweeps of a small level in one CTA: x lives in shared
+// memory for the whole launch (loaded first, written back last), so the
+// colour-to-colour dependency goes through shared memory and __syncthreads;
+// groups of G lanes stride over the rows of a colour.  Every thread reaches
+// every barrier (uniform loops, no early exit).
+template <int BR, typename T, int G>
+__global__ void __launch_bounds__(kGsCtaThreads)
+k_gs_small(int nc, int64_t n, const int32_t *__restrict__ coff, const int32_t *__restrict__ rp,
+           const int32_t *__restrict__ col, const T *__restrict__ val, const int32_t *__restrict__ rowidx,
+           const T *__restrict__ dblk, const T *__restrict__ b, T *__restrict__ x, T omega, int sweeps,
+           int backward) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int tid = threadIdx.x;
+  for (int64_t k = tid; k < n * BR; k += blockDim.x) xs[k] = x[k];
+  __syncthreads();
+  const int ngroups = blockDim.x / G;
+  const int gid = tid / G, gl = tid % G;
+  for (int sw = 0; sw < sweeps; ++sw)
+    for (int q = 0; q < nc; ++q) {
+      const int c = backward ? nc - 1 - q : q;
+      const int lo = coff[c], hi = coff[c + 1];
+      for (int base = lo; base < hi; base += ngroups) {
+        const int row = base + gid;
+        const bool active = row < hi;
+        T acc[BR];
+#pragma unroll
+        for (int r = 0; r < BR; ++r) acc[r] = T(0);
+        const int k0 = active ? rp[row] : 0, k1 = active ? rp[row + 1] : 0;
+        for (int k = k0 + gl; k < k1; k += G) {
+          const int64_t cc = __ldg(col + k);
+          const T *v = val + (int64_t)k * (BR * BR);
+#pragma unroll
+          for (int r = 0; r < BR; ++r)
+#pragma unroll
+            for (int qq = 0; qq < BR; ++qq) acc[r] += __ldg(v + r * BR + qq) * xs[cc * BR + qq];
+        }
+#pragma unroll
+        for (int r = 0; r < BR; ++r)
+#pragma unroll
+          for (int o = G / 2; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+        if (active && gl == 0) gs_update<BR, T>(acc, rowidx[row], dblk, b, xs, omega, backward != 0);
+      }
+      __syncthreads();
+    }
+  for (int64_t k = tid; k < n * BR; k += blockDim.x) x[k] = xs[k];
 }
 
 template <typename T>
@@ -681,27 +745,47 @@ void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaSt
   k_smooth_first<T><<<ew_grid(n), kThreads, 0, s>>>(n, dinv, b, x, d, c2);
 }
 
+#define MFS_GS_G_DISPATCH(GV, CALL)                              \
+  switch (GV) {                                                  \
+    case 4: { constexpr int G_ = 4; CALL; } break;               \
+    case 8: { constexpr int G_ = 8; CALL; } break;               \
+    case 16: { constexpr int G_ = 16; CALL; } break;             \
+    default: { constexpr int G_ = 32; CALL; } break;             \
+  }
+
 template <typename T>
-void gs_color(const Sell &A, const int32_t *rowidx, const T *dblk, const T *b, T *x, T omega, bool backward,
-              cudaStream_t s) {
+void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int sweeps, bool backward,
+               cudaStream_t s) {
+  const Sell &A = g.M;
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
-  // matrix + gathered x + diagonal blocks + b and x of the colour's rows
-  HookScope hs(s, K_SMOOTH,
-               matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + (A.br + 2.0) * A.nrows()) + 4.0 * A.nbr,
-               (A.kind == 1 ? 5 : (A.unroll == 4 ? 6 : 4)) * 1000 + sparse_sig<T>(A) % 1000, A.nbr,
-               2.0 * A.nnzb * A.br * A.bc + 2.0 * A.br * A.nrows());
   const int bw = backward ? 1 : 0;
-  if (A.kind == 1) {
-    MFS_SQUARE_DISPATCH(A.br, (k_gs_warp<BR_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.col, v, rowidx, dblk, b, x, omega, bw)));
-  } else if (A.unroll == 4) {
-    MFS_SQUARE_DISPATCH(A.br, (k_gs<BR_, T, 4><<<grid_for(A.nbr), kThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.rl, A.col, v, rowidx, dblk, b, x, omega, bw)));
-  } else {
-    MFS_SQUARE_DISPATCH(A.br, (k_gs<BR_, T, 2><<<grid_for(A.nbr), kThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.rl, A.col, v, rowidx, dblk, b, x, omega, bw)));
+  const int sig = (A.kind == 1 ? 5 : 4) * 1000 + sparse_sig<T>(A) % 1000;
+  if (!g.small) {
+    const int nc = g.ncolors();
+    for (int sw = 0; sw < sweeps; ++sw)
+      for (int q = 0; q < nc; ++q) {
+        const int c = backward ? nc - 1 - q : q;
+        const int64_t r0 = g.hoff[c], r1 = g.hoff[c + 1], nr = r1 - r0;
+        // this colour's blocks + gathered x + diagonal blocks + b and x of its rows
+        HookScope hs(s, K_SMOOTH,
+                     (double)g.cnnzb[c] * (A.br * A.bc * sizeof(T) + sizeof(int32_t)) +
+                         (double)sizeof(T) * (g.cnnzb[c] * A.bc + (A.br + 2.0) * A.br * nr) + 8.0 * nr,
+                     sig, nr, 2.0 * g.cnnzb[c] * A.br * A.bc + 2.0 * A.br * A.br * nr);
+        MFS_GS_G_DISPATCH(g.G, MFS_SQUARE_DISPATCH(A.br, (k_gs_color<BR_, T, G_><<<grid_for(nr * G_), kThreads, 0, s>>>(
+                                                             r0, r1, A.sp, A.col, v, g.rowidx, dblk, b, x, omega, bw))));
+      }
+    return;
   }
+  HookScope hs(s, K_SMOOTH,
+               sweeps * (matrix_bytes<T>(A) + (double)sizeof(T) * ((A.br + 2.0) * A.nrows())) +
+                   2.0 * sizeof(T) * A.nrows(),
+               sig, A.nbr, sweeps * (2.0 * A.nnzb * A.br * A.bc + 2.0 * A.br * A.nrows()));
+  const int nc = g.ncolors();
+  const size_t shm = (size_t)A.nrows() * sizeof(T);
+  MFS_GS_G_DISPATCH(g.G, MFS_SQUARE_DISPATCH(A.br, (k_gs_small<BR_, T, G_><<<1, kGsCtaThreads, shm, s>>>(
+                                                       nc, A.nbr, g.coff, A.sp, A.col, v, g.rowidx, dblk, b, x,
+                                                       omega, sweeps, bw))));
 }
 
 template <typename T>
@@ -781,8 +865,7 @@ void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, i
   template void smooth_step<T>(const Sell &, const T *, const T *, const T *, T *, T *, T, T,         \
                                cudaStream_t);                                                         \
   template void smooth_first<T>(int64_t, const T *, const T *, T *, T *, T, cudaStream_t);            \
-  template void gs_color<T>(const Sell &, const int32_t *, const T *, const T *, T *, T, bool,           \
-                            cudaStream_t);                                                             \
+  template void gs_sweeps<T>(const GsLevel &, const T *, const T *, T *, T, int, bool, cudaStream_t);   \
   template void lu_solve<T>(const DenseLU &, const T *, T *, cudaStream_t);                           \
   template void fill<T>(T *, int64_t, T, cudaStream_t);                                               \
   template void axpy_diag<T>(T *, const T *, const T *, int64_t, cudaStream_t);                       \

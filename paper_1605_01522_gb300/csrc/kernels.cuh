@@ -10,6 +10,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <vector>
+
 namespace mfs {
 namespace dev {
 
@@ -88,17 +90,32 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
 template <typename T>
 void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s);
 
-// One colour of a multicolour damped Gauss-Seidel sweep (SOR(omega) in the
-// order colour, node, dof): A holds the block rows of this colour only (all
-// their blocks), rowidx[k] the node of its row k, dblk the br x br diagonal
-// block of every node (node order, row-major).  For each row's node i, with
-// the sums s = (A x)_i taken from the x before this launch,
+// Multicolour damped Gauss-Seidel (SOR(omega) in the order colour, node,
+// dof) on one level field.  M holds the field's block rows reordered by
+// colour as plain BSR (kind 1, all blocks of each row); rowidx[k] is the node
+// of reordered row k; colour c owns rows [hoff[c], hoff[c+1]) (coff is the
+// device copy); dblk (caller's precision) the br x br diagonal block of every
+// node, node order, row-major.  For each row's node i, with the sums
+// s = (A x)_i taken from the x before its colour,
 //   forward:  for r = 0..br-1:  dx_r = omega (b_r - s_r - sum_{c<r} D_rc dx_c) / D_rr
-//   backward: for r = br-1..0:  the same with c > r;   x_i += dx.
-// Rows of one colour do not couple, so they update in parallel.
+//   backward: for r = br-1..0:  the same with c > r;   x_i += dx;
+// a forward sweep visits colours 0..nc-1, a backward one nc-1..0.  Rows of a
+// colour do not couple, so they update in parallel; G lanes share a row.
+// Large levels launch one kernel per colour; small ones (x fits in 48 KB of
+// shared memory) run all colours and sweeps in one single-CTA launch.
+struct GsLevel {
+  Sell M;
+  const int32_t *rowidx = nullptr;
+  const int32_t *coff = nullptr;
+  std::vector<int64_t> hoff;   // nc + 1 colour row offsets
+  std::vector<int64_t> cnnzb;  // blocks per colour (algorithmic bytes)
+  int G = 32;                  // lanes per row: 4, 8, 16 or 32
+  bool small = false;          // one single-CTA launch for all colours (x in shared memory)
+  int ncolors() const { return (int)hoff.size() - 1; }
+};
 template <typename T>
-void gs_color(const Sell &A, const int32_t *rowidx, const T *dblk, const T *b, T *x, T omega, bool backward,
-              cudaStream_t s);
+void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int sweeps, bool backward,
+               cudaStream_t s);
 
 // x = LU^-1 b  (dense, one CTA; b, x of type T, arithmetic in float64)
 template <typename T>

@@ -247,10 +247,9 @@ template <typename T> struct FL {
   T *dinv = nullptr;
   std::vector<T> c1, c2;  // smoother step coefficients
   T *bv = nullptr, *xv = nullptr, *t = nullptr, *d = nullptr, *r = nullptr, *c = nullptr, *e = nullptr;
-  // multicolour Gauss-Seidel (smoother MFS_GS): the block rows of each colour,
-  // their node indices, and the br x br diagonal block of every node
-  std::vector<dev::Sell> gs;
-  std::vector<const int32_t *> gsrow;
+  // multicolour Gauss-Seidel (smoother MFS_GS): the block rows in colour
+  // order and the br x br diagonal block of every node
+  dev::GsLevel gs;
   T *dblk = nullptr;
 };
 
@@ -293,9 +292,12 @@ static void smoother_coeffs(const mfs_params &p, double lam, std::vector<double>
   }
 }
 
-// Gauss-Seidel data of one smoothed level field: per colour the sub-matrix of
-// its block rows (all their blocks, rows in increasing node order), the node
-// index of each, and every node's diagonal block.
+// Gauss-Seidel data of one smoothed level field: its block rows reordered by
+// colour (increasing node order inside a colour) as plain BSR, the node of
+// each, the colour offsets, and every node's diagonal block.  Lanes per row
+// follow the average row length; levels whose vector fits in 48 KB run all
+// colours in one single-CTA launch with x in shared memory.
+constexpr int64_t kGsSmallBytes = 48 * 1024;
 template <typename T>
 static void upload_gs(Arena &ar, FL<T> &f, const HBsr &A, const std::vector<int32_t> &color) {
   const bool f32 = std::is_same<T, float>::value;
@@ -309,25 +311,36 @@ static void upload_gs(Arena &ar, FL<T> &f, const HBsr &A, const std::vector<int3
   for (int32_t c : color) nc = std::max(nc, c + 1);
   std::vector<std::vector<int32_t>> rows(nc);
   for (int64_t I = 0; I < A.nbr; ++I) rows[color[I]].push_back((int32_t)I);
-  f.gs.clear();
-  f.gsrow.clear();
+  HBsr S;
+  S.br = A.br;
+  S.bc = A.bc;
+  S.nbr = A.nbr;
+  S.nbc = A.nbc;
+  S.rp.assign(1, 0);
+  std::vector<int32_t> order, coff(1, 0);
+  dev::GsLevel &g = f.gs;
+  g.hoff.assign(1, 0);
+  g.cnnzb.clear();
   for (int c = 0; c < nc; ++c) {
-    HBsr S;
-    S.br = A.br;
-    S.bc = A.bc;
-    S.nbr = (int64_t)rows[c].size();
-    S.nbc = A.nbc;
-    S.rp.assign(1, 0);
+    const int64_t nz0 = (int64_t)S.ci.size();
     for (int32_t I : rows[c]) {
       for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a) {
         S.ci.push_back(A.ci[a]);
         S.v.insert(S.v.end(), A.v.begin() + a * bs, A.v.begin() + (a + 1) * bs);
       }
       S.rp.push_back((int64_t)S.ci.size());
+      order.push_back(I);
     }
-    f.gs.push_back(upload_sell(ar, S, !f32, f32));
-    f.gsrow.push_back(ar.upload(rows[c]));
+    g.hoff.push_back((int64_t)order.size());
+    coff.push_back((int32_t)order.size());
+    g.cnnzb.push_back((int64_t)S.ci.size() - nz0);
   }
+  g.M = upload_layout(ar, S, !f32, f32, 1);
+  g.rowidx = ar.upload(order);
+  g.coff = ar.upload(coff);
+  const double avg = A.nbr ? (double)A.nnzb() / (double)A.nbr : 0.0;
+  g.G = avg <= 12 ? 4 : avg <= 40 ? 8 : avg <= 100 ? 16 : 32;
+  g.small = A.nrows() * (int64_t)sizeof(T) <= kGsSmallBytes;
 }
 
 // Device copy of a host group's matrices and smoother data (read-only after
@@ -441,12 +454,7 @@ template <typename T> struct Precond {
   void smooth(FL<T> &f, const T *rhs, T *x, bool zero, bool post = false) {
     if (smoother == MFS_GS) {
       if (zero) MFS_CUDA(cudaMemsetAsync(x, 0, f.n * sizeof(T), s));
-      const int nc = (int)f.gs.size();
-      for (int sw = 0; sw < gs_sweeps; ++sw)
-        for (int q = 0; q < nc; ++q) {
-          const int c = post ? nc - 1 - q : q;
-          dev::gs_color<T>(f.gs[c], f.gsrow[c], f.dblk, rhs, x, gs_omega, post, s);
-        }
+      dev::gs_sweeps<T>(f.gs, f.dblk, rhs, x, gs_omega, gs_sweeps, post, s);
       return;
     }
     const int ns = (int)f.c1.size();

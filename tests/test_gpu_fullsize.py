@@ -153,3 +153,20 @@ def test_fullsize_constrained_box_nested_simple(pred, prec):
         assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
     else:
         assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32p"])
+def test_fullsize_gauss_seidel_smoother(prec):
+    """BGS(AMG) with the multicolour damped Gauss-Seidel smoother (omega 0.79,
+    the paper's DD(GS(0.79)) analogue) on the 64^3 box: 48 oracle iterations."""
+    s, D = _system()
+    ref = _counts()["coupled_box_3d_ne64_f3/bgs_amg+gs"]
+    with mfs.Solver(s, precond="bgs_amg", smoother="gs", precision=prec, **KW) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK
+    assert np.linalg.norm(s.rhs - D @ x) <= 1e-8 * np.linalg.norm(s.rhs)
+    if prec == "fp64":
+        assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
+    else:
+        assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
