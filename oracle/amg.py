@@ -25,6 +25,12 @@ steps below are the readings this project fixes:
    vector, lambda = ||D^-1 A v|| with ||v|| = 1.
 5. P = (I - omega D^-1 A) P_tent, omega = 4 / (3 lambda_max).
 6. R = P^T, A_c = R A P.
+
+Fields marked Petrov-Galerkin (the paper's fluid field, Sec. 7.2, citing Sala &
+Tuminaro 2008) replace steps 5-6 by pg_transfers: local damping parameters
+per coarse dof chosen to minimise ||A p_j|| in the D^-1 norm, moved to the
+rows by a minimum so that the near nullspace is kept, R built the same way
+from A^T, and A_c = R A P with R != P^T.
 """
 from __future__ import annotations
 
@@ -216,12 +222,55 @@ class FieldLevel:
 class FieldSpec:
     """What the setup needs to know about a field (mirrors the C-ABI field map)."""
 
-    def __init__(self, b, dim, kind, coords=None, theta=0.0):
+    def __init__(self, b, dim, kind, coords=None, theta=0.0, pg=False):
         self.b, self.dim, self.kind, self.coords, self.theta = b, dim, kind, coords, theta
+        self.pg = pg
 
     @classmethod
     def of(cls, f):
-        return cls(f.b, f.dim, f.nullspace, f.coords, f.theta)
+        return cls(f.b, f.dim, f.nullspace, f.coords, f.theta, getattr(f, "petrov_galerkin", False))
+
+
+# a scalar column counts in the row minimum of the damping parameters when its
+# entry of D^-1 A P_tent exceeds this fraction of the largest entry (rounding-
+# level entries, e.g. inside an aggregate where A annihilates the constant, do not)
+PG_PATTERN_REL = 1e-12
+
+
+def pg_damping(A, dinv, Pt):
+    """Row damping parameters of the Petrov-Galerkin prolongator smoothing:
+    Q = D^-1 A P_tent; per coarse dof j, omega_j minimises
+    f_j(w) = || A (p_j - w q_j) ||^2_{D^-1}  (p_j, q_j: column j of P_tent, Q),
+    i.e. omega_j = <A q_j, q_j> / <A q_j, D^-1 A q_j>, set to 0 when not
+    positive; row i takes the minimum of omega_j over the columns j with
+    |Q_ij| > PG_PATTERN_REL * max |Q| (0 for a row without such columns).
+    Returns (Q, row omegas, column omegas)."""
+    Q = (sp.diags(dinv) @ (A @ Pt)).tocsr()
+    AQ = (A @ Q).tocsr()
+    num = np.asarray(AQ.multiply(Q).sum(axis=0)).ravel()
+    den = np.asarray(AQ.multiply(AQ).multiply(dinv[:, None]).sum(axis=0)).ravel()
+    wcol = np.zeros(Q.shape[1])
+    ok = (den > 0) & (num > 0)
+    wcol[ok] = num[ok] / den[ok]
+    thr = PG_PATTERN_REL * (np.abs(Q.data).max() if Q.nnz else 0.0)
+    wrow = np.zeros(Q.shape[0])
+    for i in range(Q.shape[0]):
+        lo, hi = Q.indptr[i], Q.indptr[i + 1]
+        cols = Q.indices[lo:hi][np.abs(Q.data[lo:hi]) > thr]
+        if len(cols):
+            wrow[i] = wcol[cols].min()
+    return Q, wrow, wcol
+
+
+def pg_transfers(A, dinv, Pt):
+    """P = P_tent - diag(omega) D^-1 A P_tent and R = (P_tent - diag(omega')
+    D^-1 A^T P_tent)^T with the row parameters of pg_damping for A and A^T."""
+    Q, w, _ = pg_damping(A, dinv, Pt)
+    P = (Pt - sp.diags(w) @ Q).tocsr()
+    At = A.T.tocsr()
+    Qt, wt, _ = pg_damping(At, dinv, Pt)
+    R = (Pt - sp.diags(wt) @ Qt).T.tocsr()
+    return P, R
 
 
 def build_group(As, specs, max_levels, coarse_max, seed):
@@ -247,9 +296,13 @@ def build_group(As, specs, max_levels, coarse_max, seed):
             else:
                 k = fl.b
                 Pt, Bc = tentative_prolongator(agg, nagg, fl.b, k, B=fl.B)
-            omega = 4.0 / (3.0 * fl.lam)
-            P = (Pt - omega * sp.diags(fl.dinv) @ (fl.A @ Pt)).tocsr()
-            fl.agg, fl.P, fl.R = agg, P, P.T.tocsr()
+            if s.pg:
+                P, R = pg_transfers(fl.A, fl.dinv, Pt)
+            else:
+                omega = 4.0 / (3.0 * fl.lam)
+                P = (Pt - omega * sp.diags(fl.dinv) @ (fl.A @ Pt)).tocsr()
+                R = P.T.tocsr()
+            fl.agg, fl.P, fl.R = agg, P, R
             c = FieldLevel(fl.R @ fl.A @ P, k)
             c.B = Bc
             nxt.append(c)

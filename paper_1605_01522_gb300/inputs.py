@@ -82,6 +82,7 @@ class Field:
     nullspace: str         # "const" (per-component constants) or "rbm" (rigid-body modes)
     theta: float = 0.0     # strength-of-connection threshold used for this field
     dirichlet_nodes: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
+    petrov_galerkin: bool = False  # non-symmetric block: Petrov-Galerkin transfers (R != P^T)
 
     @property
     def ndofs(self) -> int:
@@ -460,6 +461,19 @@ def q1_flow_matrices(h):
     return G, Dz
 
 
+def q1_convection_matrix(h, wind):
+    """3D Q1 cell convection matrix C[a, b] = int N_a (wind . grad N_b)."""
+    pts, wts = _gauss_2pt()
+    C = np.zeros((8, 8))
+    w3 = np.asarray(wind, float)
+    for idx in itertools.product(range(2), repeat=3):
+        xi = np.array([pts[i] for i in idx])
+        w = np.prod([wts[i] for i in idx]) * h ** 3
+        N, dN = _shape_at(3, xi)
+        C += w * np.outer(N, (dN / h) @ w3)
+    return C
+
+
 def _vector_cell(K, b):
     """Cell matrix acting componentwise on b-vectors: (K kron I_b) in dof order a*b + c."""
     return np.kron(K, np.eye(b))
@@ -512,7 +526,7 @@ def _dirichlet_fields(blocks, dmasks):
             m.vals[diag] = np.eye(m.br)
 
 
-def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2):
+def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2, wind=None):
     """Fluid / structure / mesh-motion-like saddle system on the unit cube split
     at z = 0.5 (stand-in for the FSI block system of Sec. 6.2).  Fields:
       0 S  elasticity (3 dof/node, E, clamped top face) on the upper half;
@@ -523,7 +537,11 @@ def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2):
       3 Fp pressure (PSPG: -tau L, tau = h^2/(12 nu), p = 0 on the bottom face).
     Couplings: Fu-Fp discrete divergence and gradient; S-Fu and G-Fu interface
     penalties gamma * M_Gamma on the z = 0.5 plane (-M off the diagonal, +M on
-    it); Fu <- G volume block eta * int N dN/dz.  S-G, S-Fp, G-Fp are zero."""
+    it); Fu <- G volume block eta * int N dN/dz.  S-G, S-Fp, G-Fp are zero.
+    With `wind` (a constant 3-vector) the velocity block becomes the Oseen
+    operator nu * L + int N (wind . grad N) per component, non-symmetric, and
+    the velocity field is marked for Petrov-Galerkin transfers (the paper's
+    fluid field, Sec. 7.2)."""
     h = 1.0 / ne
     nz = ne // 2
     up = _Grid(ne, 3, shape=(ne, ne, ne - nz), h=h, origin=(0.0, 0.0, nz * h))
@@ -534,7 +552,8 @@ def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2):
     blocks = {
         (0, 0): up.bsr(up.assemble(Ke, 3, 3), 3, 3),
         (1, 1): lo.bsr(lo.assemble(_vector_cell(Kl, 3), 3, 3), 3, 3),
-        (2, 2): lo.bsr(lo.assemble(nu * _vector_cell(Kl, 3), 3, 3), 3, 3),
+        (2, 2): lo.bsr(lo.assemble(_vector_cell(nu * Kl + (q1_convection_matrix(h, wind) if wind is not None
+                                                           else 0.0), 3), 3, 3), 3, 3),
         (3, 3): lo.bsr(lo.assemble(-tau * Kl, 1, 1), 1, 1),
         (2, 3): lo.bsr(lo.assemble(Gd, 3, 1), 3, 1),
         (3, 2): lo.bsr(lo.assemble(Gd.T.copy(), 1, 3), 1, 3),
@@ -564,7 +583,8 @@ def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2):
     fields = [
         Field("structure", 3, up.nnodes, 3, up.coords, "rbm", 0.0, np.nonzero(dS)[0]),
         Field("mesh", 3, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dG)[0]),
-        Field("fluid_velocity", 3, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dF)[0]),
+        Field("fluid_velocity", 3, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dF)[0],
+              petrov_galerkin=wind is not None),
         Field("fluid_pressure", 1, lo.nnodes, 3, lo.coords, "const", 0.0, np.nonzero(dP)[0]),
     ]
     rng = np.random.default_rng(seed)
@@ -574,7 +594,8 @@ def fsi_box(ne=48, nu=1e-2, E=1e3, poisson=0.3, gamma=1.0, eta=1e-3, seed=2):
         d = (f.dirichlet_nodes[:, None] * f.b + np.arange(f.b)[None, :]).ravel()
         rhs[off + d] = 0.0
         off += f.ndofs
-    return BlockSystem(fields, blocks, rhs, name=f"fsi_box_ne{ne}", meta=dict(ne=ne, nu=nu, seed=seed))
+    name = f"fsi_box_ne{ne}" if wind is None else f"oseen_fsi_box_ne{ne}"
+    return BlockSystem(fields, blocks, rhs, name=name, meta=dict(ne=ne, nu=nu, seed=seed, wind=wind))
 
 
 def batch_sizes_log_uniform(nsys=256, lo=12, hi=48, seed=3):
