@@ -43,6 +43,9 @@ CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_eve
 def workload_config(args, s, extra=None):
     if args.workload == "fsi":
         what = f"4-field split-box saddle 48^3 Q1 ({s.ndofs} dofs: structure | mesh + PSPG Stokes u, p)"
+    elif args.workload == "oseen":
+        what = (f"4-field split-box saddle 48^3 Q1 with an Oseen velocity block, wind (0.2, 0.1, 0) ({s.ndofs} dofs), "
+                f"velocity transfers {'R = P^T' if args.no_pg else 'Petrov-Galerkin'}")
     elif args.workload == "cons":
         what = (f"constrained 3-field box {NE}^3 Q1 + 4 patch-mean Lagrange multipliers ({s.ndofs} dofs, "
                 f"zero multiplier block)")
@@ -204,13 +207,20 @@ def make_system(args=None):
         return inputs.fsi_box(ne=48, seed=2)
     if args is not None and args.workload == "cons":
         return inputs.constrained_box(ne=NE, nfields=3, seed=5)
+    if args is not None and args.workload == "oseen":
+        s = inputs.fsi_box(ne=48, seed=2, wind=(0.2, 0.1, 0.0))
+        if args.no_pg:
+            s.fields[2].petrov_galerkin = False
+        return s
     return inputs.coupled_box_3d(ne=NE, nfields=3, seed=1)
 
 
 def counts_key(args):
-    name = {"fsi": "fsi_box_ne48", "cons": f"constrained_box_ne{NE}_f3_m4"}.get(args.workload, WORKLOAD)
+    name = {"fsi": "fsi_box_ne48", "cons": f"constrained_box_ne{NE}_f3_m4",
+            "oseen": "oseen_fsi_box_ne48"}.get(args.workload, WORKLOAD)
     pc = args.precond + ("+amg_bgs" if args.precond == "simple" and args.simple_pred == "amg_bgs" else "")
     pc += "+gs" if args.smoother == "gs" and args.precond != "bgs_gs" else ""
+    pc += "+sa" if args.workload == "oseen" and args.no_pg else ""
     return name + "/" + pc
 
 
@@ -219,7 +229,7 @@ def precond_extra(args):
     diagonal A~11 over the predictor fields S, G, Fu and the pressure as Schur field;
     --simple-pred picks SIMPLE's predictor solver)."""
     extra = {}
-    if args.workload == "fsi" and args.precond in ("simple", "amg_simple"):
+    if args.workload in ("fsi", "oseen") and args.precond in ("simple", "amg_simple"):
         extra = dict(simple_group=[0, 0, 0, 1], simple_approx="diag")
     if args.precond == "simple" and args.simple_pred != "bgs_amg":
         extra["simple_pred"] = args.simple_pred
@@ -556,9 +566,11 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--ne", type=int, default=NE, help="mesh edge (64 = the benchmark workload)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--workload", default="box", choices=["box", "fsi", "cons", "batch", "serve"],
+    ap.add_argument("--no-pg", action="store_true", help="oseen workload: R = P^T on the velocity field")
+    ap.add_argument("--workload", default="box", choices=["box", "fsi", "cons", "oseen", "batch", "serve"],
                     help="box: the 64^3 three-field system (headline); fsi: the 48^3 split-box saddle; "
                          "cons: the box with 4 Lagrange-multiplier constraints (zero diagonal block); "
+                         "oseen: the split box with a non-symmetric Oseen velocity block (Petrov-Galerkin AMG); "
                          "batch: 256 independent systems; serve: Poisson request stream")
     ap.add_argument("--simple-pred", default="bgs_amg", choices=["bgs_amg", "amg_bgs"],
                     help="SIMPLE's predictor solver: BGS(AMG) sweep or AMG(BGS) V-cycle")

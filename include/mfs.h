@@ -100,7 +100,11 @@ typedef struct {
 
 /* One physical field.  coords (host, nnodes * dim, may be NULL for
  * MFS_NS_CONST) give the rigid-body modes of an MFS_NS_RBM field
- * (requires dofs_per_node == dim). */
+ * (requires dofs_per_node == dim).  petrov_galerkin = 1 marks a
+ * non-symmetric diagonal block (the paper's fluid field, Sec. 7.2): its
+ * hierarchy takes Petrov-Galerkin transfers after Sala & Tuminaro (2008),
+ * R != P^T (local damping parameters minimising ||A p_j|| in the D^-1 norm,
+ * moved to the rows by a minimum; R from the same construction on A^T). */
 typedef struct {
   int64_t nnodes;
   int dofs_per_node;
@@ -108,6 +112,7 @@ typedef struct {
   const double *coords;
   int nullspace;          /* enum mfs_nullspace */
   double strength_theta;  /* strength-of-connection threshold, >= 0 */
+  int petrov_galerkin;    /* 0: smoothed aggregation, R = P^T; 1: Petrov-Galerkin */
 } mfs_field;
 
 typedef struct {

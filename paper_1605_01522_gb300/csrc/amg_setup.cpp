@@ -261,6 +261,61 @@ std::vector<double> amg_dinv(const HBsr &A) {
   return f.dinv;
 }
 
+// Row damping parameters of the Petrov-Galerkin smoothing of Pt by A (see
+// pg_transfers); returns Q = D^-1 A Pt scaled by them (row i times omega_i).
+static HBsr pg_damped(const HBsr &A, const std::vector<double> &dinv, const HBsr &Pt) {
+  HBsr Q = bsr_spgemm(A, Pt);
+  bsr_scale_rows(Q, dinv);
+  const HBsr AQ = bsr_spgemm(A, Q);
+  const int br = Q.br, bc = Q.bc;
+  const int64_t nc = Q.ncols();
+  std::vector<double> num(nc, 0.0), den(nc, 0.0);
+  double qmax = 0.0;
+  for (double v : Q.v) qmax = std::max(qmax, std::fabs(v));
+  // column sums in row order: <A q_j, q_j> over Q's blocks, <A q_j, D^-1 A q_j> over AQ's
+  for (int64_t I = 0; I < AQ.nbr; ++I) {
+    int64_t q = Q.rp[I];
+    for (int64_t a = AQ.rp[I]; a < AQ.rp[I + 1]; ++a) {
+      const int64_t J = AQ.ci[a];
+      const double *w = AQ.blk(a);
+      while (q < Q.rp[I + 1] && Q.ci[q] < J) ++q;
+      const bool inq = q < Q.rp[I + 1] && Q.ci[q] == J;
+      for (int r = 0; r < br; ++r)
+        for (int c = 0; c < bc; ++c) {
+          const double x = w[r * bc + c];
+          den[J * bc + c] += x * x * dinv[I * br + r];
+          if (inq) num[J * bc + c] += x * Q.blk(q)[r * bc + c];
+        }
+    }
+  }
+  std::vector<double> wcol(nc, 0.0);
+  for (int64_t j = 0; j < nc; ++j)
+    if (den[j] > 0.0 && num[j] > 0.0) wcol[j] = num[j] / den[j];
+  const double thr = 1e-12 * qmax;
+  std::vector<double> wrow(Q.nrows(), 0.0);
+  for (int64_t I = 0; I < Q.nbr; ++I)
+    for (int r = 0; r < br; ++r) {
+      double m = 0.0;
+      bool any = false;
+      for (int64_t a = Q.rp[I]; a < Q.rp[I + 1]; ++a)
+        for (int c = 0; c < bc; ++c)
+          if (std::fabs(Q.blk(a)[r * bc + c]) > thr) {
+            const double wc = wcol[(int64_t)Q.ci[a] * bc + c];
+            m = any ? std::min(m, wc) : wc;
+            any = true;
+          }
+      wrow[I * br + r] = any ? m : 0.0;
+    }
+  bsr_scale_rows(Q, wrow);
+  return Q;
+}
+
+void pg_transfers(const HBsr &A, const std::vector<double> &dinv, const HBsr &Pt, HBsr &P, HBsr &R) {
+  P = bsr_axpby(1.0, Pt, -1.0, pg_damped(A, dinv, Pt));
+  const HBsr At = bsr_transpose(A);
+  R = bsr_transpose(bsr_axpby(1.0, Pt, -1.0, pg_damped(At, dinv, Pt)));
+}
+
 std::vector<int32_t> node_colors(const HBsr &A) {
   const int64_t n = A.nbr;
   const int bs = A.br * A.bc;
@@ -386,11 +441,15 @@ void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<Fie
       tentative(fl.agg, fl.nagg, fl.A.br, k, fine, f, fl.B, Pt, Bc);
       tm[3] += now_s() - t;
       t = now_s();
-      HBsr DAP = bsr_spgemm(fl.A, Pt);
-      bsr_scale_rows(DAP, fl.dinv);
-      const double omega = 4.0 / (3.0 * fl.lam);
-      fl.P = bsr_axpby(1.0, Pt, -omega, DAP);
-      fl.R = bsr_transpose(fl.P);
+      if (f.pg) {
+        pg_transfers(fl.A, fl.dinv, Pt, fl.P, fl.R);
+      } else {
+        HBsr DAP = bsr_spgemm(fl.A, Pt);
+        bsr_scale_rows(DAP, fl.dinv);
+        const double omega = 4.0 / (3.0 * fl.lam);
+        fl.P = bsr_axpby(1.0, Pt, -omega, DAP);
+        fl.R = bsr_transpose(fl.P);
+      }
       tm[4] += now_s() - t;
       t = now_s();
       nxt[i].A = bsr_spgemm(fl.R, bsr_spgemm(fl.A, fl.P));

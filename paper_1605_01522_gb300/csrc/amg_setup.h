@@ -30,6 +30,7 @@ struct FieldInfo {
   int ns = 0;  // 0 constants, 1 rigid-body modes
   double theta = 0.0;
   std::vector<double> coords;
+  bool pg = false;  // Petrov-Galerkin transfers (non-symmetric block)
 };
 
 struct HLevelField {
@@ -75,6 +76,14 @@ std::vector<double> amg_dinv(const HBsr &A);
 // exceeds 1e-12 times the largest entry of that block row (so rounding-level
 // Galerkin entries do not count).
 std::vector<int32_t> node_colors(const HBsr &A);
+// Petrov-Galerkin transfers after Sala & Tuminaro (2008), for non-symmetric
+// blocks (the paper's fluid field, Sec. 7.2): with Q = D^-1 A Pt, per coarse
+// scalar dof j omega_j = <A q_j, q_j> / <A q_j, D^-1 A q_j> (the minimiser of
+// ||A (p_j - w q_j)||_{D^-1}; 0 unless positive); row i of P takes the
+// minimum of omega_j over its columns with |Q_ij| > 1e-12 max|Q| (0 if none),
+// which keeps P Bc = B when A B = 0; P = Pt - diag(omega) Q.  R is the
+// transpose of the same construction on A^T (same D).
+void pg_transfers(const HBsr &A, const std::vector<double> &dinv, const HBsr &Pt, HBsr &P, HBsr &R);
 std::vector<double> bsr_to_dense(const HBsr &A);
 
 }  // namespace mfs

@@ -1038,11 +1038,20 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       sync();
       tm[3] += now_s() - t;
       t = now_s();
-      DB DAP = spgemm(fl.A, Pt);
-      k_scale_rows<<<nblocks(DAP.nbr), kT, 0, gstream()>>>(DAP.v.p, DAP.rp.p, DAP.nbr, DAP.br, DAP.bc, fl.dinv.p);
-      const double omega = 4.0 / (3.0 * fl.lam);
-      fl.P = merge(1.0, Pt, -omega, DAP, true);
-      fl.R = transpose(fl.P, true);
+      if (f.pg) {
+        // Petrov-Galerkin damping parameters (column dot products, row
+        // minima) on the host, as in the host setup; P and R come back up
+        HBsr hP, hR;
+        pg_transfers(l == 0 ? diag[i] : download(fl.A), fl.dinv.download(), download(Pt), hP, hR);
+        fl.P = upload(hP);
+        fl.R = upload(hR);
+      } else {
+        DB DAP = spgemm(fl.A, Pt);
+        k_scale_rows<<<nblocks(DAP.nbr), kT, 0, gstream()>>>(DAP.v.p, DAP.rp.p, DAP.nbr, DAP.br, DAP.bc, fl.dinv.p);
+        const double omega = 4.0 / (3.0 * fl.lam);
+        fl.P = merge(1.0, Pt, -omega, DAP, true);
+        fl.R = transpose(fl.P, true);
+      }
       sync();
       tm[4] += now_s() - t;
       t = now_s();

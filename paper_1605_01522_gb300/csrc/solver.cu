@@ -1497,6 +1497,8 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       info[i].dim = f.dim;
       info[i].ns = f.nullspace;
       info[i].theta = f.strength_theta;
+      if (f.petrov_galerkin != 0 && f.petrov_galerkin != 1) throw SetupError(MFS_ERR_INVALID, "bad field");
+      info[i].pg = f.petrov_galerkin == 1;
       if (f.nullspace == MFS_NS_RBM) {
         if (!f.coords || f.dim != f.dofs_per_node || (f.dim != 2 && f.dim != 3))
           throw SetupError(MFS_ERR_INVALID, "rigid-body modes need coords and dofs_per_node == dim in {2,3}");

@@ -61,7 +61,7 @@ class Block(C.Structure):
 class FieldDesc(C.Structure):
     _fields_ = [("nnodes", C.c_int64), ("dofs_per_node", C.c_int), ("dim", C.c_int),
                 ("coords", C.POINTER(C.c_double)), ("nullspace", C.c_int),
-                ("strength_theta", C.c_double)]
+                ("strength_theta", C.c_double), ("petrov_galerkin", C.c_int)]
 
 
 class Params(C.Structure):
@@ -251,7 +251,8 @@ class Solver:
             co = np.ascontiguousarray(f.coords, np.float64)
             keep.append(co)
             fields[i] = FieldDesc(f.nnodes, f.b, f.dim, co.ctypes.data_as(C.POINTER(C.c_double)),
-                                  NS_RBM if f.nullspace == "rbm" else NS_CONST, f.theta)
+                                  NS_RBM if f.nullspace == "rbm" else NS_CONST, f.theta,
+                                  1 if getattr(f, "petrov_galerkin", False) else 0)
         h = C.c_void_p()
         rc = lib.mfs_setup(blocks, len(system.blocks), fields, system.nfields, C.byref(prm), C.byref(h))
         if rc != OK:

@@ -28,6 +28,12 @@ WORKLOADS = {
     "constrained_box_ne64_f3_m4": (lambda: inputs.constrained_box(ne=64, nfields=3, seed=5),
                                    dict(max_levels=5, coarse_max=1000),
                                    {"simple": {}, "simple+amg_bgs": dict(simple_pred="amg_bgs")}),
+    # the split box with an Oseen velocity block (wind 0.2, 0.1, 0); its velocity
+    # field takes Petrov-Galerkin transfers ("+sa": P^T restriction instead)
+    "oseen_fsi_box_ne48": (lambda: inputs.fsi_box(ne=48, seed=2, wind=(0.2, 0.1, 0.0)),
+                           dict(max_levels=5, coarse_max=1000),
+                           {"simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag"),
+                            "simple+sa": dict(simple_group=[0, 0, 0, 1], simple_approx="diag", pg_off=True)}),
     "fsi_box_ne48": (lambda: inputs.fsi_box(ne=48, seed=2), dict(max_levels=5, coarse_max=1000),
                      {"bgs_amg": {}, "simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag"),
                       "amg_simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
@@ -53,9 +59,13 @@ def main():
             extra = pcs[pc]
             t0 = time.time()
             ex = dict(extra)
+            sp_ = [amg.FieldSpec.of(f) for f in s.fields]
+            if ex.pop("pg_off", False):
+                for f in sp_:
+                    f.pg = False
             if ex.pop("smoother", None) == "gs":
                 ex["smoother"] = SmootherParams("gs", omega=0.79, sweeps=1)
-            M = precond.Preconditioner(A, specs, precond.Params(pc.split("+")[0], **kw, **ex))
+            M = precond.Preconditioner(A, sp_, precond.Params(pc.split("+")[0], **kw, **ex))
             t1 = time.time()
             r = krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=400)
             t2 = time.time()

@@ -42,6 +42,8 @@ def _small(name):
         return inputs.fsi_box(ne=8), dict(max_levels=3, coarse_max=100)
     if name == "cons":
         return inputs.constrained_box(ne=9), dict(max_levels=3, coarse_max=100)
+    if name == "oseen":
+        return inputs.fsi_box(ne=8, wind=(0.1, 0.05, 0.0)), dict(max_levels=3, coarse_max=100)
     raise KeyError(name)
 
 
@@ -108,9 +110,13 @@ GS = [("2d", "bgs_amg", dict(smoother="gs")), ("3d", "amg_bgs", dict(smoother="g
       ("3d2", "amg_simple", dict(smoother="gs", gs_sweeps=2, gs_omega=1.0)),
       ("3d", "bgs_gs", dict(smoother="gs")), ("2d", "bgs_gs", dict(smoother="gs", gs_omega=0.69, bgs_order="sym")),
       ("cons", "simple", dict(smoother="gs", simple_pred="amg_bgs"))]
+# Petrov-Galerkin transfers on the Oseen velocity field (Sec. 7.2, R != P^T)
+PG = [("oseen", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag")),
+      ("oseen", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag", simple_pred="amg_bgs")),
+      ("oseen", "bgs_amg", {})]
 
 
-@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED + GS)
+@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED + GS + PG)
 def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
     s, kw = _small(name)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
@@ -124,7 +130,7 @@ def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
 
 
 @pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI
-                         + AMG_SIMPLE[:4] + NESTED + GS)
+                         + AMG_SIMPLE[:4] + NESTED + GS + PG[:2])
 def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     s, kw = _small(name)
     ro, D = _oracle_solve(s, kw, pc, extra)
@@ -142,7 +148,7 @@ def test_solve_fp64_iterations_match_oracle(name, pc, extra):
 
 @pytest.mark.parametrize("name,pc,extra", [("2d", "bgs_amg", {}), ("3d", "bgs_amg", {}), ("3d", "amg_bgs", {}),
                                            ("3d", "simple", {}), ("fsi", "bgs_amg", {})] + FSI[:1]
-                         + AMG_SIMPLE[1:2] + NESTED[:2] + GS[:2] + GS[4:5])
+                         + AMG_SIMPLE[1:2] + NESTED[:2] + GS[:2] + GS[4:5] + PG[:1])
 def test_solve_fp32_preconditioner(name, pc, extra):
     s, kw = _small(name)
     ro, D = _oracle_solve(s, kw, pc, extra)

@@ -116,3 +116,18 @@ def test_gpu_setup_constrained_box_nested_simple():
             assert _rel(g.export_csr("A", 0, l, i, j), h.export_csr("A", 0, l, i, j)) < TOL
     g.close()
     h.close()
+
+
+def test_gpu_setup_petrov_galerkin_matches_host():
+    s = inputs.fsi_box(ne=10, wind=(0.2, 0.1, 0.0))
+    kw = dict(max_levels=3, coarse_max=100, simple_group=[0, 0, 0, 1], simple_approx="diag")
+    g = mfs.Solver(s, precond="simple", setup_device=1, **kw)
+    h = mfs.Solver(s, precond="simple", setup_only=1, **kw)
+    assert g.num_levels(0) == h.num_levels(0)
+    for l in range(g.num_levels(0) - 1):
+        for i in range(3):
+            assert _rel(g.export_csr("P", 0, l, i), h.export_csr("P", 0, l, i)) < TOL
+            assert _rel(g.export_csr("R", 0, l, i), h.export_csr("R", 0, l, i)) < TOL
+            assert _rel(g.export_csr("A", 0, l + 1, i, i), h.export_csr("A", 0, l + 1, i, i)) < TOL
+    g.close()
+    h.close()

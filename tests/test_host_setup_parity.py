@@ -162,6 +162,28 @@ def test_gauss_seidel_colours_match_oracle(pc):
     assert n >= 6
 
 
+def test_petrov_galerkin_transfers_match_oracle():
+    """Oseen split box: the velocity field (non-symmetric, marked Petrov-Galerkin)
+    gets R != P^T equal to the oracle's Sala-Tuminaro transfers on every level;
+    the symmetric fields keep R = P^T."""
+    s = inputs.fsi_box(ne=8, wind=(0.2, 0.1, 0.0))
+    assert s.fields[2].petrov_galerkin
+    kw = dict(max_levels=3, coarse_max=100, simple_group=[0, 0, 0, 1], simple_approx="diag")
+    lib = mfs.Solver(s, precond="simple", setup_only=1, **kw)
+    M = precond.Preconditioner(s.scipy_blocks(), [amg.FieldSpec.of(f) for f in s.fields],
+                               precond.Params("simple", **kw))
+    lv = M.groups[0].levels
+    assert lib.num_levels(0) == len(lv) == 3
+    for l in range(len(lv) - 1):
+        for i in range(3):
+            assert _rel(lib.export_csr("P", 0, l, i), lv[l][i].P) < TOL
+            assert _rel(lib.export_csr("R", 0, l, i), lv[l][i].R) < TOL
+            assert _rel(lib.export_csr("A", 0, l + 1, i, i), lv[l + 1][i].A) < TOL
+            asym = np.abs((lv[l][i].R - lv[l][i].P.T).toarray()).max()
+            assert (asym > 1e-3) if i == 2 else (asym == 0.0)
+    lib.close()
+
+
 def test_setup_rejects_bad_input():
     s, kw = _get("2d")
     bad = inputs.BlockSystem(s.fields, {k: v for k, v in s.blocks.items() if k != (1, 1)}, s.rhs)
