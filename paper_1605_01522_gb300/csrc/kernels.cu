@@ -13,6 +13,10 @@ namespace dev {
 namespace {
 
 constexpr int kThreads = 256;
+// plain-BSR matrices with at most kCtaRowsMax rows averaging at least
+// kCtaRowBlocks blocks per row take one CTA per row instead of one warp
+constexpr int64_t kCtaRowsMax = 4096;
+constexpr int64_t kCtaRowBlocks = 128;
 constexpr int kGsCtaThreads = 1024;  // threads of the one-CTA Gauss-Seidel kernel for small levels
 LaunchHook *g_hook = nullptr;
 
@@ -149,6 +153,45 @@ k_spmv_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restri
   if (lane < BR) {
     const int64_t i = row * BR + lane;
     const T a = pick<BR, T>(acc, lane);
+    y[i] = z != nullptr ? alpha * a + beta * z[i] : alpha * a;
+  }
+}
+
+// One CTA per block row, for few and long rows (restrictions to small coarse
+// levels): threads stride over the row's blocks, then a fixed butterfly per
+// warp and a fixed-order sum over the warps.
+template <int BR, int BC, typename T>
+__global__ void __launch_bounds__(kThreads)
+k_spmv_cta(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+           const T *__restrict__ val, const T *__restrict__ x, T *y, T alpha, T beta, const T *z) {
+  __shared__ T part[kThreads / 32][BR];
+  const int64_t row = blockIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T acc[BR];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+  for (int k = rp[row] + threadIdx.x; k < rp[row + 1]; k += blockDim.x) {
+    const int64_t c = __ldg(col + k);
+    T xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = __ldg(x + c * BC + q);
+    const T *v = val + (int64_t)k * (BR * BC);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[r] += __ldg(v + r * BC + q) * xv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+    if (lane == 0) part[warp][r] = acc[r];
+  }
+  __syncthreads();
+  if (threadIdx.x < BR) {
+    T a = T(0);
+    for (int w = 0; w < kThreads / 32; ++w) a += part[w][threadIdx.x];
+    const int64_t i = row * BR + threadIdx.x;
     y[i] = z != nullptr ? alpha * a + beta * z[i] : alpha * a;
   }
 }
@@ -341,6 +384,25 @@ k_gs_small(int nc, int64_t n, const int32_t *__restrict__ coff, const int32_t *_
       __syncthreads();
     }
   for (int64_t k = tid; k < n * BR; k += blockDim.x) x[k] = xs[k];
+}
+
+// x = inv b for the explicit inverse of a coarsest matrix (row-major, float64):
+// b staged in shared memory as float64, one warp per row, fixed butterfly sum.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_inv_apply(int n, const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x) {
+  extern __shared__ double bs[];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) bs[j] = (double)b[j];
+  __syncthreads();
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double *a = inv + (int64_t)row * n;
+  double acc = 0.0;
+  for (int j = lane; j < n; j += 32) acc += __ldg(a + j) * bs[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) x[row] = (T)acc;
 }
 
 template <typename T>
@@ -658,12 +720,20 @@ template <typename T>
 void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStream_t s) {
   if (A.nbr == 0) return;
   const T *v = vals<T>(A);
+  const bool cta = A.kind == 1 && A.nbr <= kCtaRowsMax && A.nnzb >= kCtaRowBlocks * A.nbr;
   HookScope hs(s, K_SPMV, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + A.nrows() * (z ? 2 : 1)),
-               sparse_sig<T>(A), A.nbr, 2.0 * A.nnzb * A.br * A.bc + (z ? 3.0 : 1.0) * A.nrows());
+               cta ? 7000 + sparse_sig<T>(A) % 1000 : sparse_sig<T>(A), A.nbr,
+               2.0 * A.nnzb * A.br * A.bc + (z ? 3.0 : 1.0) * A.nrows());
   if (A.kind == 1) {
-    MFS_BLOCK_DISPATCH(A.br, A.bc,
-                       (k_spmv_warp<BR_, BC_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
-                           A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
+    if (cta) {
+      MFS_BLOCK_DISPATCH(A.br, A.bc,
+                         (k_spmv_cta<BR_, BC_, T><<<(unsigned)A.nbr, kThreads, 0, s>>>(
+                             A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
+    } else {
+      MFS_BLOCK_DISPATCH(A.br, A.bc,
+                         (k_spmv_warp<BR_, BC_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
+                             A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
+    }
     return;
   }
   if (A.unroll == 4) {
@@ -791,6 +861,13 @@ void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int s
 template <typename T>
 void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   if (lu.n == 0) return;
+  if (lu.inv) {
+    HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + 2.0 * sizeof(T) * lu.n, 2, lu.n, 2.0 * lu.n * (double)lu.n);
+    constexpr int kRowsPerCta = kThreads / 32;
+    k_inv_apply<T><<<(unsigned)((lu.n + kRowsPerCta - 1) / kRowsPerCta), kThreads, (size_t)lu.n * sizeof(double), s>>>(
+        lu.n, lu.inv, b, x);
+    return;
+  }
   HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n,
                2.0 * lu.n * (double)lu.n);
   // stage the factors in shared memory when y and LU fit in 200 KB

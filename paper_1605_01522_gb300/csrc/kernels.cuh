@@ -42,8 +42,8 @@ enum KernelClass { K_SPMV = 0, K_SMOOTH = 1, K_VECTOR = 2, K_COARSE = 3, K_ARNOL
 // sig identifies the kernel variant: for SpMV / smoothing
 // layout*1000 + br*100 + bc*10 + (float64 ? 1 : 0) with layout 0 SELL-32,
 // 1 warp BSR, 2 merged rows, 3 SELL-32 with 4 slots in flight, 4 / 5 / 6 the
-// Gauss-Seidel colour kernels on SELL-32 / warp BSR / SELL-32 x4; otherwise a
-// small id.
+// Gauss-Seidel colour kernels on SELL-32 / warp BSR / SELL-32 x4, 7 one CTA per
+// BSR row; otherwise a small id.
 // rows = block rows (sparse kernels) or vector length.
 struct LaunchHook {
   // returns false when this launch is not to be recorded (after() is then skipped)
@@ -63,6 +63,7 @@ struct DenseLU {
   int n = 0;
   const double *lu = nullptr;   // column-major, unit-lower L and U
   const int32_t *perm = nullptr;
+  const double *inv = nullptr;  // row-major inverse built from the factors (small n), or null
 };
 
 // y = alpha * A x + beta * z   (z may alias y or be null when beta == 0)
@@ -117,7 +118,8 @@ template <typename T>
 void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int sweeps, bool backward,
                cudaStream_t s);
 
-// x = LU^-1 b  (dense, one CTA; b, x of type T, arithmetic in float64)
+// x = LU^-1 b  (dense; b, x of type T, arithmetic in float64): with lu.inv one
+// warp per row of the explicit inverse, else one CTA of triangular sweeps
 template <typename T>
 void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s);
 

@@ -227,12 +227,37 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   return best == 0 ? a : (best == 1 ? a4 : b);
 }
 
+// Explicit inverse (row-major) of a factored coarsest matrix: column j solves
+// L U x = P e_j with the stored factors; the coarse solve then becomes one
+// parallel matrix-vector product instead of two dependent triangular sweeps.
+static std::vector<double> lu_inverse(const HDenseLU &lu) {
+  const int n = lu.n;
+  std::vector<double> inv((size_t)n * n);
+#pragma omp parallel for schedule(static)
+  for (int j = 0; j < n; ++j) {
+    std::vector<double> y(n);
+    for (int i = 0; i < n; ++i) y[i] = lu.perm[i] == j ? 1.0 : 0.0;
+    for (int k = 0; k < n; ++k)  // unit-lower L, column-major
+      for (int i = k + 1; i < n; ++i) y[i] -= lu.lu[(size_t)k * n + i] * y[k];
+    for (int k = n - 1; k >= 0; --k) {
+      y[k] /= lu.lu[(size_t)k * n + k];
+      for (int i = 0; i < k; ++i) y[i] -= lu.lu[(size_t)k * n + i] * y[k];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + j] = y[i];
+  }
+  return inv;
+}
+
+// coarsest levels up to this size are solved through their explicit inverse
+constexpr int kCoarseInverseMax = 4096;
+
 static dev::DenseLU upload_lu(Arena &ar, const HDenseLU &lu) {
   dev::DenseLU d;
   d.n = lu.n;
   if (lu.n > 16384) throw SetupError(MFS_ERR_INVALID, "coarsest level too large for the dense LU (raise max_levels or lower coarse_max)");
   d.lu = ar.upload(lu.lu);
   d.perm = ar.upload(lu.perm);
+  if (lu.n > 0 && lu.n <= kCoarseInverseMax) d.inv = ar.upload(lu_inverse(lu));
   return d;
 }
 

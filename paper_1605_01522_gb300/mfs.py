@@ -33,7 +33,7 @@ EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_sol
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
 _OTHER = {2: {1: "smooth_first", 2: "fill", 3: "axpy_diag", 4: "axpy", 5: "convert", 6: "scale"},
-          3: {1: "lu_solve"},
+          3: {1: "lu_solve", 2: "coarse_inverse_apply"},
           4: {1: "mdot", 2: "reduce_partials", 3: "cgs_fused", 4: "cgs_update", 5: "gemv_add"}}
 
 
@@ -46,7 +46,7 @@ def kernel_name(key: int) -> str:
         bc, f64 = divmod(rest, 10)
         base = "spmv" if cls == 0 else "smooth"
         layout = {0: "sell", 1: "warp", 2: "rows", 3: "sell4", 4: "gs_sell", 5: "gs_warp",
-                  6: "gs_sell4"}.get(kind, str(kind))
+                  6: "gs_sell4", 7: "cta"}.get(kind, str(kind))
         return f"{base}_{layout}<{br}x{bc},{'f64' if f64 else 'f32'}>"
     return _OTHER.get(cls, {}).get(sig, f"class{cls}_id{sig}")
 

@@ -170,3 +170,22 @@ def test_fullsize_gauss_seidel_smoother(prec):
         assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
     else:
         assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32p"])
+def test_fullsize_oseen_petrov_galerkin(prec):
+    """Split box with an Oseen velocity block (wind (0.2, 0.1, 0)); the velocity
+    hierarchy uses Petrov-Galerkin transfers: SIMPLE(diag) against the oracle's
+    216 iterations (+-1 %, restarted runs)."""
+    s = inputs.fsi_box(ne=48, seed=2, wind=(0.2, 0.1, 0.0))
+    D = precond.assemble(s.scipy_blocks(), 4)
+    ref = _counts()["oseen_fsi_box_ne48/simple"]
+    with mfs.Solver(s, precond="simple", precision=prec, **KW, **FSI_SIMPLE) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK
+    assert np.linalg.norm(s.rhs - D @ x) <= 1e-8 * np.linalg.norm(s.rhs)
+    if prec == "fp64":
+        assert abs(info["iters"] - ref["iters"]) <= max(1, round(0.01 * ref["iters"])), (info["iters"], ref["iters"])
+    else:
+        assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
