@@ -1547,8 +1547,10 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     }
     for (int i = 0; i < nfields; ++i)
       if (!hb.count({i, i})) throw SetupError(MFS_ERR_INVALID, "missing diagonal block");
+    const double t_in = now_ms();
     build_host(h.get(), hb, info);
     color_levels(h.get());
+    const double t_host = now_ms();
     h->host_only = host_only;
     if (host_only) {
       h->setup_ms = now_ms() - t0;
@@ -1566,8 +1568,10 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     const bool f32 = p.precision == MFS_FP32P;
     MFS_CUDA(cudaGetDevice(&h->device));
     Arena &mat = *h->mat;
+    const double t_dev = now_ms();
     for (auto &kv : hb) h->A64[kv.first] = upload_sell(mat, kv.second, true, f32);
     h->rows64 = merge_rows(mat, hb, h->nf, h->foff);
+    const double t_fine = now_ms();
     if (f32) {
       h->p32.reset(new Precond<float>());
       upload_precond<float>(h.get(), mat, *h->p32, hb, true);
@@ -1575,9 +1579,16 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       h->p64.reset(new Precond<double>());
       upload_precond<double>(h.get(), mat, *h->p64, hb, false);
     }
+    const double t_pre = now_ms();
     alloc_solver_work(h.get());
     if (p.profile) h->prof.reset(new EventProf());
     MFS_CUDA(cudaStreamSynchronize(0));  // uploads and memsets ran on the legacy stream
+    if (p.verbose)
+      fprintf(stderr,
+              "mfs_setup: input %.1f ms, hierarchy %.1f ms, init %.1f ms, fine layouts %.1f ms, "
+              "preconditioner upload %.1f ms, workspace %.1f ms (%lld arrays)\n",
+              t_in - t0, t_host - t_in, t_dev - t_host, t_fine - t_dev, t_pre - t_fine, now_ms() - t_pre,
+              (long long)(h->mat->ptrs.size() + h->ar.ptrs.size()));
   } catch (const SetupError &e) {
     return fail(e.code, e.what());
   } catch (const CudaError &e) {
