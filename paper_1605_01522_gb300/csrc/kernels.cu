@@ -519,6 +519,48 @@ __global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64
     out[i] = (TO)in[i];
 }
 
+__global__ void k_sell_widths(const int32_t *__restrict__ rp, int64_t nbr, int32_t *__restrict__ rl,
+                              int32_t *__restrict__ w) {
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int len = I < nbr ? rp[I + 1] - rp[I] : 0;
+  if (I < nbr) rl[I] = len;
+  int m = len;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && (I >> 5) * 32 < nbr) w[I >> 5] = m;
+}
+
+// one thread per block row: slot t of row I goes to slice I/32, lane I%32
+__global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__restrict__ ci, int nsrc,
+                            const double *__restrict__ v0, const double *__restrict__ v1,
+                            const double *__restrict__ v2, int b0, int b1, int b2, int br, int64_t nbr,
+                            const int32_t *__restrict__ sp, int32_t *__restrict__ col, double *__restrict__ v64,
+                            float *__restrict__ v32) {
+  const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= nbr) return;
+  const int64_t lane = I & 31, base = sp[I >> 5];
+  const int bct = b0 + b1 + b2, bs = br * bct;
+  for (int64_t a = rp[I]; a < rp[I + 1]; ++a) {
+    const int64_t slot = base + (a - rp[I]);
+    col[slot * 32 + lane] = ci[a];
+    for (int r = 0; r < br; ++r) {
+      int o = 0;
+      for (int j = 0; j < nsrc; ++j) {
+        const double *v = j == 0 ? v0 : (j == 1 ? v1 : v2);
+        const int bj = j == 0 ? b0 : (j == 1 ? b1 : b2);
+        for (int q = 0; q < bj; ++q) {
+          const double x = v[(a * br + r) * bj + q];
+          const int64_t e = (slot * bs + r * bct + o + q) * 32 + lane;
+          if (v64) v64[e] = x;
+          if (v32) v32[e] = (float)x;
+        }
+        o += bj;
+      }
+    }
+  }
+}
+
 __global__ void k_scale(const double *x, double a, double *y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = a * x[i];
@@ -892,6 +934,18 @@ void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T), 4, n, 2.0 * n);
   if (n) k_axpy<T><<<ew_grid(n), kThreads, 0, s>>>(y, x, a, n);
 }
+void sell_widths(const int32_t *rp, int64_t nbr, int32_t *rl, int32_t *w, cudaStream_t s) {
+  if (nbr) k_sell_widths<<<grid_for(nbr), kThreads, 0, s>>>(rp, nbr, rl, w);
+}
+
+void sell_fill(const int32_t *rp, const int32_t *ci, int nsrc, const double *v0, const double *v1,
+               const double *v2, const int *bcs, int br, int64_t nbr, const int32_t *sp, int32_t *col,
+               double *v64, float *v32, cudaStream_t s) {
+  if (nbr)
+    k_sell_fill<<<grid_for(nbr), kThreads, 0, s>>>(rp, ci, nsrc, v0, v1, v2, bcs[0], nsrc > 1 ? bcs[1] : 0,
+                                                   nsrc > 2 ? bcs[2] : 0, br, nbr, sp, col, v64, v32);
+}
+
 template <typename TI, typename TO>
 void convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)), 5, n, 0.0);

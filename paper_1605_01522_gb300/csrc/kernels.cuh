@@ -123,6 +123,19 @@ void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int s
 template <typename T>
 void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s);
 
+// Layout building on the device (setup): from a plain BSR matrix already in
+// device memory (int32 row pointer and block columns, float64 row-major
+// blocks), row lengths rl and per-slice widths w (max row length of each slice
+// of 32 rows) ...
+void sell_widths(const int32_t *rp, int64_t nbr, int32_t *rl, int32_t *w, cudaStream_t s);
+// ... then, with slice offsets sp (slots), the SELL-32 arrays (zeroed before):
+// col, and v64 and/or v32 (either may be null).  With nsrc > 1 the sources
+// share rp / ci and are merged column-wise per block ([A_0 | A_1 | A_2],
+// bcs[j] columns each).
+void sell_fill(const int32_t *rp, const int32_t *ci, int nsrc, const double *v0, const double *v1,
+               const double *v2, const int *bcs, int br, int64_t nbr, const int32_t *sp, int32_t *col,
+               double *v64, float *v32, cudaStream_t s);
+
 // elementwise helpers
 template <typename T> void fill(T *x, int64_t n, T v, cudaStream_t s);
 template <typename T> void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s);  // x -= dinv*t

@@ -967,9 +967,25 @@ HBsr gpu_spgemm(const HBsr &A, const HBsr &B) {
   return C;
 }
 
+// DB of the shape of H from a device copy (D2D on the setup stream)
+static DB from_device(const HBsr &H, const DevBlock &d) {
+  DB A;
+  A.br = H.br, A.bc = H.bc, A.nbr = H.nbr, A.nbc = H.nbc, A.nnzb = H.nnzb();
+  A.rp.resize(A.nbr + 1);
+  A.ci.resize(A.nnzb);
+  A.v.resize(A.nnzb * A.br * A.bc);
+  GS_CUDA(cudaMemcpyAsync(A.rp.p, d.rp, (size_t)(A.nbr + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, gstream()));
+  if (A.nnzb) {
+    GS_CUDA(cudaMemcpyAsync(A.ci.p, d.ci, (size_t)A.nnzb * sizeof(int32_t), cudaMemcpyDeviceToDevice, gstream()));
+    GS_CUDA(cudaMemcpyAsync(A.v.p, d.v, (size_t)A.v.n * sizeof(double), cudaMemcpyDeviceToDevice, gstream()));
+  }
+  return A;
+}
+
 void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector<FieldInfo> &info,
                      int max_levels, int64_t coarse_max, uint64_t seed, bool want_off,
-                     const BlockMap *fine_off, int verbose) {
+                     const BlockMap *fine_off, int verbose, const std::vector<DevBlock> *dev_diag,
+                     const std::map<std::pair<int, int>, DevBlock> *dev_off, std::vector<HBsr> *steal) {
   StreamScope scope;  // outlives every device array below
   double tm[7] = {0, 0, 0, 0, 0, 0, 0};  // power, strength, aggregate, tentative, smooth+transpose, RAP, offdiag
   g.nf = (int)diag.size();
@@ -977,12 +993,13 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
   std::vector<std::vector<GLevel>> lv(1);
   lv[0].resize(g.nf);
   for (int i = 0; i < g.nf; ++i) {
-    lv[0][i].A = upload(diag[i]);
+    lv[0][i].A = dev_diag ? from_device(diag[i], (*dev_diag)[i]) : upload(diag[i]);
     fill_dinv(lv[0][i].A, lv[0][i].dinv);
   }
   std::vector<std::map<std::pair<int, int>, DB>> off(1);
   if (want_off && fine_off)
-    for (auto &kv : *fine_off) off[0][kv.first] = upload(kv.second);
+    for (auto &kv : *fine_off)
+      off[0][kv.first] = dev_off ? from_device(kv.second, dev_off->at(kv.first)) : upload(kv.second);
   auto total = [&](int l) {
     int64_t s = 0;
     for (auto &f : lv[l]) s += f.A.nbr * f.A.br;
@@ -1084,7 +1101,9 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
     for (int i = 0; i < g.nf; ++i) {
       GLevel &d = lv[l][i];
       HLevelField &h = g.lv[l][i];
-      h.A = l == 0 ? diag[i] : download(d.A);
+      if (l > 0) h.A = download(d.A);
+      else if (steal) h.A = std::move((*steal)[i]);
+      else h.A = diag[i];
       h.dinv = d.dinv.download();
       h.lam = d.lam;
       if (l + 1 < lv.size()) {

@@ -154,6 +154,109 @@ static dev::Sell upload_layout(Arena &ar, const HBsr &A, bool want64, bool want3
   return S;
 }
 
+// An input block in device memory as plain BSR (int32 row pointer and block
+// columns, float64 blocks), uploaded once per setup; the fine layouts are
+// built from it on the device.
+struct RawDev {
+  int32_t *rp = nullptr, *ci = nullptr;
+  double *v = nullptr;
+  int br = 0, bc = 0;
+  int64_t nbr = 0, nbc = 0, nnzb = 0;
+};
+
+static RawDev upload_raw(Arena &tmp, const HBsr &A, cudaStream_t st) {
+  RawDev R;
+  R.br = A.br;
+  R.bc = A.bc;
+  R.nbr = A.nbr;
+  R.nbc = A.nbc;
+  R.nnzb = A.nnzb();
+  if (A.nnzb() > INT32_MAX) throw SetupError(MFS_ERR_INVALID, "matrix too large for 32-bit block offsets");
+  std::vector<int32_t> rp(A.rp.begin(), A.rp.end());
+  R.rp = tmp.alloc<int32_t>((int64_t)rp.size());
+  R.ci = tmp.alloc<int32_t>(R.nnzb);
+  R.v = tmp.alloc<double>(R.nnzb * R.br * R.bc);
+  MFS_CUDA(cudaMemcpyAsync(R.rp, rp.data(), rp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (R.nnzb) {
+    MFS_CUDA(cudaMemcpyAsync(R.ci, A.ci.data(), A.ci.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    MFS_CUDA(cudaMemcpyAsync(R.v, A.v.data(), A.v.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  MFS_CUDA(cudaStreamSynchronize(st));  // rp is a temporary host vector
+  return R;
+}
+
+// upload_layout for a device-resident block (or nsrc blocks of one pattern
+// merged column-wise, kind 0 only), converted by kernels on stream st.
+static dev::Sell upload_layout_dev(Arena &ar, const RawDev *const *src, int nsrc, bool want64, bool want32, int kind,
+                                   cudaStream_t st) {
+  const RawDev &A = *src[0];
+  dev::Sell S;
+  int bcs[3] = {0, 0, 0};
+  S.bc = 0;
+  for (int j = 0; j < nsrc; ++j) {
+    bcs[j] = src[j]->bc;
+    S.bc += src[j]->bc;
+  }
+  S.br = A.br;
+  S.nbr = A.nbr;
+  S.nbc = A.nbc;
+  S.nnzb = A.nnzb;
+  if (A.nbr == 0) return S;
+  const int64_t bs = (int64_t)S.br * S.bc;
+  if (kind == 1) {
+    if (nsrc != 1) throw SetupError(MFS_ERR_INVALID, "merged rows need the SELL layout");
+    S.kind = 1;
+    int32_t *rp = ar.alloc<int32_t>(A.nbr + 1), *col = ar.alloc<int32_t>(A.nnzb);
+    MFS_CUDA(cudaMemcpyAsync(rp, A.rp, (A.nbr + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    if (A.nnzb) MFS_CUDA(cudaMemcpyAsync(col, A.ci, A.nnzb * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    S.sp = rp;
+    S.col = col;
+    if (want64) {
+      double *v = ar.alloc<double>(A.nnzb * bs);
+      if (A.nnzb) MFS_CUDA(cudaMemcpyAsync(v, A.v, A.nnzb * bs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      S.v64 = v;
+    }
+    if (want32) {
+      float *v = ar.alloc<float>(A.nnzb * bs);
+      dev::convert<double, float>(A.v, v, A.nnzb * bs, st);
+      S.v32 = v;
+    }
+    MFS_CUDA(cudaStreamSynchronize(st));
+    return S;
+  }
+  S.nslices = (A.nbr + 31) / 32;
+  int32_t *rl = ar.alloc<int32_t>(A.nbr);
+  int32_t *w = nullptr;
+  MFS_CUDA(cudaMallocAsync((void **)&w, (size_t)S.nslices * sizeof(int32_t), st));
+  dev::sell_widths(A.rp, A.nbr, rl, w, st);
+  std::vector<int32_t> hw(S.nslices), sp(S.nslices + 1, 0);
+  MFS_CUDA(cudaMemcpyAsync(hw.data(), w, S.nslices * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  MFS_CUDA(cudaFreeAsync(w, st));
+  MFS_CUDA(cudaStreamSynchronize(st));
+  for (int64_t k = 0; k < S.nslices; ++k) {
+    if ((int64_t)sp[k] + hw[k] > INT32_MAX / 32) throw SetupError(MFS_ERR_INVALID, "matrix too large for 32-bit slot offsets");
+    sp[k + 1] = sp[k] + hw[k];
+  }
+  S.nslots = sp[S.nslices];
+  int32_t *dsp = ar.upload(sp);
+  int32_t *col = ar.alloc<int32_t>(S.nslots * 32);
+  double *v64 = want64 ? ar.alloc<double>(S.nslots * bs * 32) : nullptr;
+  float *v32 = want32 ? ar.alloc<float>(S.nslots * bs * 32) : nullptr;
+  if (col) MFS_CUDA(cudaMemsetAsync(col, 0, S.nslots * 32 * sizeof(int32_t), st));
+  if (v64) MFS_CUDA(cudaMemsetAsync(v64, 0, S.nslots * bs * 32 * sizeof(double), st));
+  if (v32) MFS_CUDA(cudaMemsetAsync(v32, 0, S.nslots * bs * 32 * sizeof(float), st));
+  dev::sell_fill(A.rp, A.ci, nsrc, src[0]->v, nsrc > 1 ? src[1]->v : nullptr, nsrc > 2 ? src[2]->v : nullptr, bcs,
+                 A.br, A.nbr, dsp, col, v64, v32, st);
+  MFS_CUDA(cudaGetLastError());
+  MFS_CUDA(cudaStreamSynchronize(st));
+  S.sp = dsp;
+  S.rl = rl;
+  S.col = col;
+  S.v64 = v64;
+  S.v32 = v32;
+  return S;
+}
+
 template <typename T> static float time_spmv(const dev::Sell &S, cudaStream_t st) {
   T *x = nullptr, *y = nullptr;
   MFS_CUDA(cudaMallocAsync((void **)&x, (size_t)std::max<int64_t>(1, S.ncols()) * sizeof(T), st));
@@ -213,6 +316,44 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
     throw;
   }
   cudaStreamDestroy(st);
+  const int best = t[0] <= t[1] && t[0] <= t[2] ? 0 : (t[1] <= t[2] ? 1 : 2);
+  dev::Sell &loser = best == 2 ? a : b;
+  ar.release(loser.sp);
+  ar.release(loser.rl);
+  ar.release(loser.col);
+  ar.release(loser.v64);
+  ar.release(loser.v32);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best;
+  }
+  return best == 0 ? a : (best == 1 ? a4 : b);
+}
+
+// upload_sell for a device-resident input block: the same tuning and cache,
+// the candidate layouts built on the device.
+static dev::Sell upload_sell_dev(Arena &ar, const RawDev &A, bool want64, bool want32, cudaStream_t st) {
+  const RawDev *src[1] = {&A};
+  if (A.nbr < kTuneMinRows) return upload_layout_dev(ar, src, 1, want64, want32, 1, st);
+  const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb, want32 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      dev::Sell S = upload_layout_dev(ar, src, 1, want64, want32, it->second == 2 ? 1 : 0, st);
+      if (it->second == 1) S.unroll = 4;
+      return S;
+    }
+  }
+  dev::Sell a = upload_layout_dev(ar, src, 1, want64, want32, 0, st);
+  dev::Sell b = upload_layout_dev(ar, src, 1, want64, want32, 1, st);
+  MFS_CUDA(cudaStreamSynchronize(0));
+  float t[3];
+  dev::Sell a4 = a;
+  a4.unroll = 4;
+  t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
+  t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
+  t[2] = want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st);
   const int best = t[0] <= t[1] && t[0] <= t[2] ? 0 : (t[1] <= t[2] ? 1 : 2);
   dev::Sell &loser = best == 2 ? a : b;
   ar.release(loser.sp);
@@ -858,6 +999,7 @@ using namespace mfs;
 
 struct mfs_handle {
   mfs_params prm{};
+  const std::map<std::pair<int, int>, RawDev> *raw = nullptr;  // input blocks on the device (setup only)
   int nf = 0;
   std::vector<int64_t> fsize, foff;
   int64_t n = 0;
@@ -1107,6 +1249,38 @@ HBsr to_hbsr(const mfs_block &b) {
 // share one sparsity pattern (fields on the same nodes), store the row's
 // blocks side by side so one kernel reads each column index once and writes
 // y_i once.  Empty result = per-block SpMVs.
+// The merged-row layout built on the device from the row field's input
+// blocks (same test as merge_rows: identical patterns, supported shapes).
+std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb,
+                                           const std::map<std::pair<int, int>, RawDev> &raw, int nf,
+                                           const std::vector<int64_t> &foff, cudaStream_t st) {
+  std::vector<dev::RowMerged> out;
+  if (nf < 2 || nf > 3) return out;
+  for (int i = 0; i < nf; ++i) {
+    int b[3] = {0, 0, 0};
+    const RawDev *src[3] = {nullptr, nullptr, nullptr};
+    const HBsr *h0 = nullptr;
+    for (int j = 0; j < nf; ++j) {
+      auto it = hb.find({i, j});
+      if (it == hb.end()) return {};
+      if (!h0) h0 = &it->second;
+      if (it->second.rp != h0->rp || it->second.ci != h0->ci) return {};
+      b[j] = it->second.bc;
+      src[j] = &raw.at({i, j});
+    }
+    if (!dev::rows_supported(h0->br, b, nf)) return {};
+    dev::RowMerged R;
+    R.M = upload_layout_dev(ar, src, nf, true, false, 0, st);
+    R.nb = nf;
+    for (int j = 0; j < nf; ++j) {
+      R.b[j] = b[j];
+      R.off[j] = foff[j];
+    }
+    out.push_back(R);
+  }
+  return out;
+}
+
 std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb, int nf,
                                        const std::vector<int64_t> &foff) {
   std::vector<dev::RowMerged> out;
@@ -1174,10 +1348,28 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
                 const std::vector<FieldInfo> &info) {
   const mfs_params &p = h->prm;
   const bool gpu = p.setup_device == 1 && !p.setup_only;
+  // gf: the input fields of the group's members (empty: blocks not among the inputs)
+  // steal: d itself, when the caller no longer needs it (moved into level 0)
   auto group = [&](HGroup &g, const std::vector<HBsr> &d, const std::vector<FieldInfo> &fi, bool off,
-                   const BlockMap *fo) {
-    if (gpu) build_group_gpu(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
-    else build_group(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
+                   const BlockMap *fo, const std::vector<int> &gf, std::vector<HBsr> *steal = nullptr) {
+    if (!gpu) {
+      build_group(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose);
+      return;
+    }
+    std::vector<DevBlock> dd;
+    std::map<std::pair<int, int>, DevBlock> dof;
+    const bool have = h->raw && !gf.empty();
+    if (have) {
+      auto view = [&](int i, int j) {
+        const RawDev &r = h->raw->at({gf[i], gf[j]});
+        return DevBlock{r.rp, r.ci, r.v};
+      };
+      for (int k = 0; k < (int)gf.size(); ++k) dd.push_back(view(k, k));
+      if (fo)
+        for (auto &kv : *fo) dof[kv.first] = view(kv.first.first, kv.first.second);
+    }
+    build_group_gpu(g, d, fi, p.max_levels, p.coarse_max, p.seed, off, fo, p.verbose, have ? &dd : nullptr,
+                    have && fo ? &dof : nullptr, steal);
   };
   auto split_groups = [&]() {
     h->host->G1.clear();
@@ -1210,7 +1402,9 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
     for (auto &kv : blocks)
       if (kv.first.first == kv.first.second) diag.push_back(kv.second);
       else off[kv.first] = kv.second;
-    group(h->host->hg0, diag, info, p.precond != MFS_BGS_AMG, &off);
+    std::vector<int> all(h->nf);
+    for (int i = 0; i < h->nf; ++i) all[i] = i;
+    group(h->host->hg0, diag, info, p.precond != MFS_BGS_AMG, &off, all, &diag);
     if (p.precond != MFS_AMG_SIMPLE) return;
     // AMG(SIMPLE): per smoothed level, A~_11 of the merged predictor rows and
     // the explicit level Schur complement S~^l with its smoother data
@@ -1285,7 +1479,7 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
       const int i = kv.first.first, j = kv.first.second;
       if (i != j && l1.count(i) && l1.count(j)) off1[{l1[i], l1[j]}] = kv.second;
     }
-  group(h->host->hg0, diag1, info1, mono_pred, mono_pred ? &off1 : nullptr);
+  group(h->host->hg0, diag1, info1, mono_pred, mono_pred ? &off1 : nullptr, h->host->G1, &diag1);
   // A~_11: SIMPLEC sums of absolute entries over the merged predictor rows, or the diagonal
   h->host->dtilde.clear();
   for (int j : h->host->G1) {
@@ -1345,7 +1539,7 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
       }
     }
   if (h->host->schur_diag.size() != h->host->G2.size()) throw SetupError(MFS_ERR_INVALID, "missing Schur diagonal block");
-  group(h->host->hg1, h->host->schur_diag, sinfo, false, nullptr);
+  group(h->host->hg1, h->host->schur_diag, sinfo, false, nullptr, {});
 }
 
 // Device half of the setup: upload the host hierarchy in precision T
@@ -1547,6 +1741,29 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     }
     for (int i = 0; i < nfields; ++i)
       if (!hb.count({i, i})) throw SetupError(MFS_ERR_INVALID, "missing diagonal block");
+    // one upload of the input blocks, shared by the GPU setup and the fine layouts
+    std::unique_ptr<Arena> raw_arena;
+    std::map<std::pair<int, int>, RawDev> rd;
+    struct StreamGuard {
+      cudaStream_t s = nullptr;
+      ~StreamGuard() {
+        if (s) {
+          cudaStreamSynchronize(s);
+          cudaStreamDestroy(s);
+        }
+      }
+    } rst;
+    struct RawReset {
+      mfs_handle *h;
+      ~RawReset() { h->raw = nullptr; }
+    } raw_reset{h.get()};
+    if (!host_only) {
+      dev::init();
+      raw_arena.reset(new Arena());
+      MFS_CUDA(cudaStreamCreateWithFlags(&rst.s, cudaStreamNonBlocking));
+      for (auto &kv : hb) rd[kv.first] = upload_raw(*raw_arena, kv.second, rst.s);
+      h->raw = &rd;
+    }
     const double t_in = now_ms();
     build_host(h.get(), hb, info);
     color_levels(h.get());
@@ -1557,7 +1774,6 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       *out = h.release();
       return MFS_OK;
     }
-    dev::init();
     if (!h->s) {
       // the legacy default stream cannot be captured: use a stream of our own,
       // non-blocking so that legacy-stream work of other threads (another
@@ -1569,8 +1785,12 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     MFS_CUDA(cudaGetDevice(&h->device));
     Arena &mat = *h->mat;
     const double t_dev = now_ms();
-    for (auto &kv : hb) h->A64[kv.first] = upload_sell(mat, kv.second, true, f32);
-    h->rows64 = merge_rows(mat, hb, h->nf, h->foff);
+    // fine layouts built on the device from the uploaded input blocks
+    for (auto &kv : hb) h->A64[kv.first] = upload_sell_dev(mat, rd.at(kv.first), true, f32, rst.s);
+    h->rows64 = merge_rows_dev(mat, hb, rd, h->nf, h->foff, rst.s);
+    MFS_CUDA(cudaStreamSynchronize(rst.s));
+    h->raw = nullptr;
+    raw_arena.reset();
     const double t_fine = now_ms();
     if (f32) {
       h->p32.reset(new Precond<float>());

@@ -22,6 +22,9 @@ import numpy as np
 from . import mfs
 
 BYTES_PER_DOF_ESTIMATE = 3200  # before a system's first setup (measured after it)
+# device memory a setup holds beyond its final footprint (input copy, GPU
+# setup products, candidate layouts), as a multiple of the final shared bytes
+SETUP_TRANSIENT_FACTOR = 2
 
 
 class Request:
@@ -46,7 +49,9 @@ class Server:
     """hbm_budget: bytes of device memory the server may hold (resident
     hierarchies + running requests); workers: requests in flight at once."""
 
-    def __init__(self, hbm_budget, workers=8, tol=1e-8, keep_resident=True, **solver_kw):
+    def __init__(self, hbm_budget, workers=8, tol=1e-8, keep_resident=True, max_setups=4, **solver_kw):
+        """max_setups: setups (new matrices) in flight at once, which bounds
+        their transient device memory."""
         self.budget = int(hbm_budget)
         self.tol = tol
         self.kw = solver_kw
@@ -62,6 +67,8 @@ class Server:
         self.done = []
         self.stop = False
         self.next_id = 0
+        self.setups_running = 0
+        self.max_setups = max_setups
         self.threads = [threading.Thread(target=self._work, daemon=True) for _ in range(workers)]
         for t in self.threads:
             t.start()
@@ -96,9 +103,11 @@ class Server:
         self.resident.clear()
 
     def stats(self):
+        ran = [r for r in self.done if r.t_done is not None and r.t_start is not None]
         lat = np.array([r.latency for r in self.done if r.latency is not None])
-        solve = np.array([r.t_done - r.t_start for r in self.done if r.t_done])
-        setup = np.array([r.t_start - r.t_admit for r in self.done if r.t_done and r.setup_done_here])
+        solve = np.array([r.t_done - r.t_start for r in ran]) if ran else np.zeros(1)
+        setup = np.array([r.t_start - r.t_admit for r in ran if r.setup_done_here])
+        errors = collections.Counter(r.error for r in self.done if r.error)
         t0 = min(r.t_arrive for r in self.done)
         t1 = max(r.t_done for r in self.done)
         ok = sum(1 for r in self.done if r.rc == mfs.OK)
@@ -107,17 +116,23 @@ class Server:
                 "p50_solve_ms": float(np.percentile(solve, 50) * 1e3), "p99_solve_ms": float(np.percentile(solve, 99) * 1e3),
                 "mean_setup_ms": float(setup.mean() * 1e3) if len(setup) else 0.0,
                 "solves_per_s": ok / (t1 - t0), "peak_hbm_bytes": self.peak_used, "peak_in_flight": self.peak_running,
-                "setups": int(sum(1 for r in self.done if r.setup_done_here))}
+                "setups": int(sum(1 for r in self.done if r.setup_done_here)),
+                "failed": int(sum(errors.values())), "errors": dict(errors.most_common(3))}
 
     # ------------------------------------------------------------- internals
     def _estimate(self, r):
+        """Bytes to reserve: the workspace for a clone; for a setup also the
+        hierarchy and the setup's transient memory."""
         shared, own = self.footprint.get(r.key, (None, None))
         if shared is None:
             n = r.system.ndofs
             shared, own = BYTES_PER_DOF_ESTIMATE * n // 2, BYTES_PER_DOF_ESTIMATE * n // 2
         if r.reuse and r.key in self.resident:
             return own
-        return shared + own
+        return (1 + SETUP_TRANSIENT_FACTOR) * shared + own
+
+    def _needs_setup(self, r):
+        return not (r.reuse and r.key in self.resident)
 
     def _evict_for(self, need):
         """Drop idle resident hierarchies (LRU first) until `need` bytes fit."""
@@ -136,6 +151,8 @@ class Server:
         if not self.pending:
             return None
         r = self.pending[0]
+        if self._needs_setup(r) and self.setups_running >= self.max_setups:
+            return None
         need = self._estimate(r)
         if self.used + need > self.budget:
             self._evict_for(need)
@@ -158,6 +175,8 @@ class Server:
         if r.reuse and r.key in self.resident:
             self.resident.move_to_end(r.key)
             self.resident[r.key][3] += 1
+        else:
+            self.setups_running += 1
         return r
 
     def _work(self):
@@ -177,7 +196,12 @@ class Server:
                 if base is not None:
                     sv = base.clone()
                 else:
-                    sv = mfs.Solver(r.system, **self.kw)
+                    try:
+                        sv = mfs.Solver(r.system, **self.kw)
+                    finally:
+                        with self.cv:
+                            self.setups_running -= 1
+                            self.cv.notify_all()
                     r.setup_done_here = True
                 r.t_start = time.perf_counter()
                 x = np.zeros(r.system.ndofs)
@@ -198,9 +222,12 @@ class Server:
                             keep = True
                 if base is not None and r.key in self.resident:
                     self.resident[r.key][3] -= 1
+            # release a handle that is not kept before the request counts as
+            # finished, so that drain() never returns with device work in flight
+            if sv is not None and not keep:
+                sv.close()
+            with self.cv:
                 self.running -= 1
                 self.done.append(r)
                 self.cv.notify_all()
-            if sv is not None and not keep:
-                sv.close()
             r.event.set()
