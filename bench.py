@@ -527,8 +527,8 @@ def run_serve(args, rank, world):
     gaps = rng.exponential(1.0 / args.rate, size=args.requests)
     picks = rng.integers(len(keys), size=args.requests)
     reuse = rng.random(args.requests) < 0.3
-    srv = serving.Server(hbm_budget=int(args.hbm_gb * (1 << 30)), workers=args.threads, precond=args.precond,
-                         precision=args.precision, **SOLVER_KW)
+    srv = serving.Server(hbm_budget=int(args.hbm_gb * (1 << 30)), workers=args.threads, max_setups=args.max_setups,
+                         precond=args.precond, precision=args.precision, **SOLVER_KW)
     t0 = time.perf_counter()
     t = t0
     for i in range(args.requests):
@@ -546,7 +546,8 @@ def run_serve(args, rank, world):
             "dtype": "f32+f64" if args.precision == "fp32p" else "f64", "data": "synthetic",
             "config": {"workload": f"serving: {args.requests} Poisson requests at {args.rate}/s, 2- or 3-field 3D boxes, "
                                    f"n_e in {sizes}, 30 % reuse a resident hierarchy, HBM budget {args.hbm_gb} GB, "
-                                   f"{args.threads} workers, {args.precond.upper()} {args.precision.upper()}, rtol 1e-8",
+                                   f"{args.threads} workers, at most {args.max_setups} setups at once, "
+                                   f"{args.precond.upper()} {args.precision.upper()}, rtol 1e-8",
                        **st}}
     print(json.dumps(line), flush=True)
 
@@ -579,6 +580,7 @@ def main():
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--hbm-gb", type=float, default=150.0)
+    ap.add_argument("--max-setups", type=int, default=8, help="serve: setups in flight at once")
     ap.add_argument("--serve-sizes", default="16,24,32,48,64")
     args = ap.parse_args()
     NE = args.ne

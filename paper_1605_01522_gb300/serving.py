@@ -120,16 +120,16 @@ class Server:
                 "failed": int(sum(errors.values())), "errors": dict(errors.most_common(3))}
 
     # ------------------------------------------------------------- internals
-    def _estimate(self, r):
+    def _estimate(self, r, transient=True):
         """Bytes to reserve: the workspace for a clone; for a setup also the
-        hierarchy and the setup's transient memory."""
+        hierarchy and (transient=True) the setup's transient memory."""
         shared, own = self.footprint.get(r.key, (None, None))
         if shared is None:
             n = r.system.ndofs
             shared, own = BYTES_PER_DOF_ESTIMATE * n // 2, BYTES_PER_DOF_ESTIMATE * n // 2
         if r.reuse and r.key in self.resident:
             return own
-        return (1 + SETUP_TRANSIENT_FACTOR) * shared + own
+        return (1 + (SETUP_TRANSIENT_FACTOR if transient else 0)) * shared + own
 
     def _needs_setup(self, r):
         return not (r.reuse and r.key in self.resident)
@@ -156,6 +156,13 @@ class Server:
         need = self._estimate(r)
         if self.used + need > self.budget:
             self._evict_for(need)
+        if self.used + need > self.budget and self.running == 0:
+            # alone on the device: the transient reserve is not needed to fit,
+            # and a system never set up before is tried whatever its estimate
+            need = self._estimate(r, transient=False)
+            self._evict_for(need)
+            if r.key not in self.footprint:
+                need = min(need, max(0, self.budget - self.used))
         if self.used + need > self.budget:
             if self.running == 0 and need > self.budget:
                 self.pending.popleft()

@@ -81,7 +81,7 @@ def test_budget_limits_memory_and_concurrency():
             srv.submit(key, pool[key], b, reuse)
         srv.drain(timeout=600)
         st = srv.stats()
-        assert st["converged"] == len(reqs)
+        assert st["converged"] == len(reqs), (st["errors"], budget, one)
         assert st["peak_hbm_bytes"] <= budget
     finally:
         srv.close()
