@@ -414,6 +414,27 @@ def run_mfs(args, rank, world):
         secondary = {"kernel": f"{r[0]} ({r[1]} block rows)", "bound": "hbm", "achieved": g, "peak": hbm_peak,
                      "unit": "GB/s", "frac": g / hbm_peak, "peak_kind": peak_kind,
                      "traffic": ncu_traffic(r[0], r[1]), "timed": "warm-up solve, every launch timed"}
+    # the V-cycles as a whole: every sparse preconditioner kernel (smoothing,
+    # residual, coupling, restriction, prolongation on every level; not the
+    # GMRES matvec), algorithmic bytes over summed launch time, warm-up solve
+    pre = [r for r in detail_all
+           if r[0].startswith(("spmv", "smooth")) and "<" in r[0] and not r[0].startswith("spmv_rows")]
+    vcycle = None
+    if pre:
+        vb, vms = sum(r[4] for r in pre), sum(r[3] for r in pre)
+        by_rows = {}
+        for r in pre:  # block rows identify the matrix size (fine level, coarse levels, transfers)
+            e = by_rows.setdefault(r[1], [0.0, 0.0, 0])
+            e[0] += r[4]
+            e[1] += r[3]
+            e[2] += r[2]
+        groups = sorted(by_rows.items(), key=lambda kv: -kv[1][1])[:6]
+        vcycle = {"GBps": vb / (vms / 1e3) / 1e9, "frac": vb / (vms / 1e3) / 1e9 / hbm_peak, "peak": hbm_peak,
+                  "peak_kind": peak_kind, "share_of_solve_time": vms / tot_ms,
+                  "by_block_rows": [{"rows": k, "GBps": round(v[0] / (v[1] / 1e3) / 1e9, 1),
+                                     "share_of_vcycle_time": round(v[1] / vms, 4), "launches": v[2]}
+                                    for k, v in groups],
+                  "timed": "warm-up solve, every launch timed (algorithmic bytes / summed event time)"}
     stats = stats_all
     launches_total = sum(v[0] for v in stats_all.values()) * args.steps
     if rank != 0:
@@ -438,6 +459,7 @@ def run_mfs(args, rank, world):
                                             "kernel_class_share": shares, "top_kernels": top}),
         "roofline": roof,
         "roofline_top_f32": secondary,
+        "vcycle": vcycle,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches_total),
