@@ -167,6 +167,7 @@ def kernel_source_digest(kernel):
     src = open(os.path.join(ROOT, "paper_1605_01522_gb300", "csrc", "kernels.cu")).read()
     fn = {"smooth_sell": ["sell_row", "k_smooth"], "spmv_sell": ["sell_row", "k_spmv"],
           "smooth_sell4": ["sell_row", "k_smooth"], "spmv_sell4": ["sell_row", "k_spmv"],
+          "smooth_sell8": ["sell_row", "k_smooth"], "spmv_sell8": ["sell_row", "k_spmv"],
           "spmv_rows": ["k_spmv_rows"], "smooth_warp": ["bsr_warp_row", "k_smooth_warp"],
           "spmv_warp": ["bsr_warp_row", "k_spmv_warp"]}.get(kernel.split("<")[0])
     if not fn:

@@ -13,6 +13,10 @@ namespace dev {
 namespace {
 
 constexpr int kThreads = 256;
+// CTAs of the one-thread-per-row SELL-32 kernels: two slices, so that a grid
+// of a few thousand CTAs spreads evenly over the SMs (with 256-thread CTAs
+// the busiest SM held 8 where the average was 7.1)
+constexpr int kSellThreads = 64;
 // plain-BSR matrices with at most kCtaRowsMax rows averaging at least
 // kCtaRowBlocks blocks per row take one CTA per row instead of one warp
 constexpr int64_t kCtaRowsMax = 4096;
@@ -38,7 +42,8 @@ struct HookScope {
 };
 
 template <typename T> int sparse_sig(const Sell &A) {
-  const int layout = A.kind == 0 && A.unroll == 4 ? 3 : A.kind;  // 3: SELL-32 with 4 slots in flight
+  // 3 / 9: SELL-32 with 4 / 8 slots in flight
+  const int layout = A.kind == 0 && A.unroll == 4 ? 3 : (A.kind == 0 && A.unroll == 8 ? 9 : A.kind);
   return layout * 1000 + A.br * 100 + A.bc * 10 + (sizeof(T) == 8 ? 1 : 0);
 }
 
@@ -780,11 +785,15 @@ void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStre
   }
   if (A.unroll == 4) {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
-                       (k_spmv<BR_, BC_, T, 4><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                       (k_spmv<BR_, BC_, T, 4><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
+                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+  } else if (A.unroll == 8) {
+    MFS_BLOCK_DISPATCH(A.br, A.bc,
+                       (k_spmv<BR_, BC_, T, 8><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
                            A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
   } else {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
-                       (k_spmv<BR_, BC_, T, 2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+                       (k_spmv<BR_, BC_, T, 2><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
                            A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
   }
 }
@@ -825,7 +834,7 @@ void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s) {
                2000 + A.br * 100 + A.bc * 10 + 1, A.nbr, 2.0 * A.nnzb * A.br * A.bc);
   const double *x0 = x + R.off[0], *x1 = x + R.off[1], *x2 = R.nb > 2 ? x + R.off[2] : x;
   const int b3[3] = {R.b[0], R.b[1], R.nb > 2 ? R.b[2] : 0};
-  MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+  MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
                                   A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
 }
 
@@ -842,10 +851,13 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
     return;
   }
   if (A.unroll == 4) {
-    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 4><<<grid_for(A.nbr), kThreads, 0, s>>>(
+    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 4><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
+                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+  } else if (A.unroll == 8) {
+    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 8><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
                                   A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
   } else {
-    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 2><<<grid_for(A.nbr), kThreads, 0, s>>>(
+    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 2><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
                                   A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
   }
 }

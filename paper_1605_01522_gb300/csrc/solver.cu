@@ -61,6 +61,9 @@ struct Arena {
     bytes += count * (int64_t)sizeof(T);
     return (T *)p;
   }
+  // synchronous copy on the legacy stream: a copy from pageable memory may
+  // still be in flight when this returns, so work on other (non-blocking)
+  // streams that reads the result must first synchronise with stream 0
   template <typename T> T *upload(const std::vector<T> &h) {
     T *p = alloc<T>((int64_t)h.size());
     if (p) MFS_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -87,8 +90,9 @@ struct Arena {
 };
 
 // Layout autotuning: matrices with at least kTuneMinRows block rows are built
-// in both layouts (SELL-32, one thread per block row; plain BSR, one warp per
-// block row), each timed with CUDA events, and the faster is kept.  Smaller
+// in both layouts (SELL-32, one thread per block row, with 2, 4 or 8 block
+// slots in flight; plain BSR, one warp per block row), each timed with CUDA
+// events, and the fastest is kept.  Smaller
 // matrices are latency bound and take the warp layout.  Decisions are cached
 // per (block shape, rows, blocks, precision) for the life of the process.
 constexpr int64_t kTuneMinRows = 2048;
@@ -238,7 +242,11 @@ static dev::Sell upload_layout_dev(Arena &ar, const RawDev *const *src, int nsrc
     sp[k + 1] = sp[k] + hw[k];
   }
   S.nslots = sp[S.nslices];
-  int32_t *dsp = ar.upload(sp);
+  // on st, like the kernels below: a synchronous cudaMemcpy from pageable
+  // memory may return before the data reach the device, and its legacy stream
+  // does not order the non-blocking stream st
+  int32_t *dsp = ar.alloc<int32_t>((int64_t)sp.size());
+  MFS_CUDA(cudaMemcpyAsync(dsp, sp.data(), sp.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   int32_t *col = ar.alloc<int32_t>(S.nslots * 32);
   double *v64 = want64 ? ar.alloc<double>(S.nslots * bs * 32) : nullptr;
   float *v32 = want32 ? ar.alloc<float>(S.nslots * bs * 32) : nullptr;
@@ -286,6 +294,43 @@ template <typename T> static float time_spmv(const dev::Sell &S, cudaStream_t st
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int64_t, int64_t, int>, int> g_tune;
 
+// Layout candidates of the autotuner: 0 SELL-32 with 2 slots in flight,
+// 1 with 4, 2 plain BSR with one warp per row, 3 SELL-32 with 8 slots in
+// flight (only for blocks of at most 3 entries, whose rows are short on bytes).
+static int tune_pick(const dev::Sell &a, const dev::Sell &b, bool want32, cudaStream_t st) {
+  dev::Sell a4 = a, a8 = a;
+  a4.unroll = 4;
+  a8.unroll = 8;
+  const bool small = a.br * a.bc <= 3;
+  float t[4];
+  t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
+  t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
+  t[2] = want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st);
+  t[3] = !small ? 1e30f : (want32 ? time_spmv<float>(a8, st) : time_spmv<double>(a8, st));
+  int best = 0;
+  for (int c = 1; c < 4; ++c)
+    if (t[c] < t[best]) best = c;
+  return best;
+}
+
+static void tune_apply(dev::Sell &S, int best) {
+  if (best == 1) S.unroll = 4;
+  if (best == 3) S.unroll = 8;
+}
+
+// keep the chosen candidate, release the other layout
+static dev::Sell tune_keep(Arena &ar, dev::Sell &a, dev::Sell &b, int best) {
+  dev::Sell &loser = best == 2 ? a : b;
+  ar.release(loser.sp);
+  ar.release(loser.rl);
+  ar.release(loser.col);
+  ar.release(loser.v64);
+  ar.release(loser.v32);
+  dev::Sell S = best == 2 ? b : a;
+  tune_apply(S, best);
+  return S;
+}
+
 static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32) {
   if (A.nbr < kTuneMinRows) return upload_layout(ar, A, want64, want32, 1);
   const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb(), want32 ? 1 : 0);
@@ -294,7 +339,7 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       dev::Sell S = upload_layout(ar, A, want64, want32, it->second == 2 ? 1 : 0);
-      if (it->second == 1) S.unroll = 4;
+      tune_apply(S, it->second);
       return S;
     }
   }
@@ -303,31 +348,19 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   cudaStream_t st;
   MFS_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
   MFS_CUDA(cudaStreamSynchronize(0));  // uploads and memsets of the legacy stream
-  // candidates: SELL-32 with 2 or 4 slots in flight, BSR warp per row
-  float t[3];
-  dev::Sell a4 = a;
-  a4.unroll = 4;
+  int best = 0;
   try {
-    t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
-    t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
-    t[2] = want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st);
+    best = tune_pick(a, b, want32, st);
   } catch (...) {
     cudaStreamDestroy(st);
     throw;
   }
   cudaStreamDestroy(st);
-  const int best = t[0] <= t[1] && t[0] <= t[2] ? 0 : (t[1] <= t[2] ? 1 : 2);
-  dev::Sell &loser = best == 2 ? a : b;
-  ar.release(loser.sp);
-  ar.release(loser.rl);
-  ar.release(loser.col);
-  ar.release(loser.v64);
-  ar.release(loser.v32);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = best;
   }
-  return best == 0 ? a : (best == 1 ? a4 : b);
+  return tune_keep(ar, a, b, best);
 }
 
 // upload_sell for a device-resident input block: the same tuning and cache,
@@ -341,31 +374,19 @@ static dev::Sell upload_sell_dev(Arena &ar, const RawDev &A, bool want64, bool w
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
       dev::Sell S = upload_layout_dev(ar, src, 1, want64, want32, it->second == 2 ? 1 : 0, st);
-      if (it->second == 1) S.unroll = 4;
+      tune_apply(S, it->second);
       return S;
     }
   }
   dev::Sell a = upload_layout_dev(ar, src, 1, want64, want32, 0, st);
   dev::Sell b = upload_layout_dev(ar, src, 1, want64, want32, 1, st);
   MFS_CUDA(cudaStreamSynchronize(0));
-  float t[3];
-  dev::Sell a4 = a;
-  a4.unroll = 4;
-  t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
-  t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
-  t[2] = want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st);
-  const int best = t[0] <= t[1] && t[0] <= t[2] ? 0 : (t[1] <= t[2] ? 1 : 2);
-  dev::Sell &loser = best == 2 ? a : b;
-  ar.release(loser.sp);
-  ar.release(loser.rl);
-  ar.release(loser.col);
-  ar.release(loser.v64);
-  ar.release(loser.v32);
+  const int best = tune_pick(a, b, want32, st);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     g_tune[key] = best;
   }
-  return best == 0 ? a : (best == 1 ? a4 : b);
+  return tune_keep(ar, a, b, best);
 }
 
 // Explicit inverse (row-major) of a factored coarsest matrix: column j solves

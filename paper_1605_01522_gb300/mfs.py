@@ -46,7 +46,7 @@ def kernel_name(key: int) -> str:
         bc, f64 = divmod(rest, 10)
         base = "spmv" if cls == 0 else "smooth"
         layout = {0: "sell", 1: "warp", 2: "rows", 3: "sell4", 4: "gs_sell", 5: "gs_warp",
-                  6: "gs_sell4", 7: "cta"}.get(kind, str(kind))
+                  6: "gs_sell4", 7: "cta", 9: "sell8"}.get(kind, str(kind))
         return f"{base}_{layout}<{br}x{bc},{'f64' if f64 else 'f32'}>"
     return _OTHER.get(cls, {}).get(sig, f"class{cls}_id{sig}")
 

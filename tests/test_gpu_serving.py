@@ -77,11 +77,11 @@ def test_budget_limits_memory_and_concurrency():
     budget = int(2.5 * one)
     srv = serving.Server(hbm_budget=budget, workers=8, keep_resident=False, **KW)
     try:
-        for key, b, reuse in reqs:
-            srv.submit(key, pool[key], b, reuse)
+        handles = [srv.submit(key, pool[key], b, reuse) for key, b, reuse in reqs]
         srv.drain(timeout=600)
         st = srv.stats()
-        assert st["converged"] == len(reqs), (st["errors"], budget, one)
+        bad = [(r.key, r.rc, r.error, r.info) for r in handles if r.rc != mfs.OK]
+        assert st["converged"] == len(reqs), (bad, budget, one)
         assert st["peak_hbm_bytes"] <= budget
     finally:
         srv.close()
