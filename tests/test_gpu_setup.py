@@ -131,3 +131,20 @@ def test_gpu_setup_petrov_galerkin_matches_host():
             assert _rel(g.export_csr("A", 0, l + 1, i, i), h.export_csr("A", 0, l + 1, i, i)) < TOL
     g.close()
     h.close()
+
+
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple"])
+def test_solve_after_host_setup_matches_gpu_setup(pc):
+    """A handle built by the host setup (setup_device=0) solves like one built on
+    the GPU: the two hierarchies agree to rounding, so the FP64 solves take the
+    same iterations and reach the same solution to 1e-9."""
+    s = inputs.coupled_box_3d(ne=11, nfields=3)
+    kw = dict(max_levels=4, coarse_max=100, precond=pc)
+    out = []
+    for dev in (0, 1):
+        with mfs.Solver(s, setup_device=dev, **kw) as lib:
+            x, info, rc = lib.solve(s.rhs, np.zeros(s.ndofs), tol=1e-8)
+        assert rc == mfs.OK
+        out.append((x, info["iters"]))
+    assert abs(out[0][1] - out[1][1]) <= 1
+    assert np.linalg.norm(out[0][0] - out[1][0]) <= 1e-9 * np.linalg.norm(out[1][0])
