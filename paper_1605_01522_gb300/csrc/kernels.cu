@@ -4,6 +4,7 @@
 // a warp are contiguous per slot and every reduction has a fixed order.
 #include "kernels.cuh"
 
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 
@@ -53,6 +54,48 @@ template <typename T> double matrix_bytes(const Sell &A) {
   return (double)A.nnzb * (A.br * A.bc * sizeof(T) + sizeof(int32_t)) + (double)A.nbr * sizeof(int32_t);
 }
 
+// The N entries of one plain-BSR block (row-major, consecutive) in the widest
+// loads its size allows: 16-byte loads when N * sizeof(T) is a multiple of
+// 16, 8-byte ones when a multiple of 8, else one load per entry.  Block k
+// starts k * N * sizeof(T) bytes into a value array that starts on a 16-byte
+// boundary (every value array is its own allocation; the setup checks it), so
+// every vector is aligned.  Fewer, wider loads keep the load queue of one-warp-per-row
+// kernels from filling (6x6 float blocks: 9 loads instead of 36).
+template <int N, typename T>
+__device__ __forceinline__ void ldg_block(const T *__restrict__ p, T (&o)[N]) {
+  constexpr int B = N * (int)sizeof(T);
+  if constexpr (sizeof(T) == 8 && B % 16 == 0) {
+    const double2 *q = reinterpret_cast<const double2 *>(p);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 v = __ldg(q + i);
+      o[2 * i] = v.x;
+      o[2 * i + 1] = v.y;
+    }
+  } else if constexpr (sizeof(T) == 4 && B % 16 == 0) {
+    const float4 *q = reinterpret_cast<const float4 *>(p);
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 v = __ldg(q + i);
+      o[4 * i] = v.x;
+      o[4 * i + 1] = v.y;
+      o[4 * i + 2] = v.z;
+      o[4 * i + 3] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && B % 8 == 0) {
+    const float2 *q = reinterpret_cast<const float2 *>(p);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float2 v = __ldg(q + i);
+      o[2 * i] = v.x;
+      o[2 * i + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = __ldg(p + i);
+  }
+}
+
 inline unsigned grid_for(int64_t n, int threads = kThreads) {
   return (unsigned)((n + threads - 1) / threads);
 }
@@ -98,11 +141,12 @@ __device__ __forceinline__ void bsr_warp_row(const int32_t *__restrict__ rp, con
     T xv[BC];
 #pragma unroll
     for (int q = 0; q < BC; ++q) xv[q] = __ldg(x + c * BC + q);
-    const T *v = val + (int64_t)k * (BR * BC);
+    T blk[BR * BC];
+    ldg_block<BR * BC, T>(val + (int64_t)k * (BR * BC), blk);
 #pragma unroll
     for (int r = 0; r < BR; ++r)
 #pragma unroll
-      for (int q = 0; q < BC; ++q) acc[r] += __ldg(v + r * BC + q) * xv[q];
+      for (int q = 0; q < BC; ++q) acc[r] += blk[r * BC + q] * xv[q];
   }
 #pragma unroll
   for (int r = 0; r < BR; ++r)
@@ -180,11 +224,12 @@ k_spmv_cta(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restric
     T xv[BC];
 #pragma unroll
     for (int q = 0; q < BC; ++q) xv[q] = __ldg(x + c * BC + q);
-    const T *v = val + (int64_t)k * (BR * BC);
+    T blk[BR * BC];
+    ldg_block<BR * BC, T>(val + (int64_t)k * (BR * BC), blk);
 #pragma unroll
     for (int r = 0; r < BR; ++r)
 #pragma unroll
-      for (int q = 0; q < BC; ++q) acc[r] += __ldg(v + r * BC + q) * xv[q];
+      for (int q = 0; q < BC; ++q) acc[r] += blk[r * BC + q] * xv[q];
   }
 #pragma unroll
   for (int r = 0; r < BR; ++r) {
@@ -316,11 +361,12 @@ __device__ __forceinline__ void gs_group_row(const int32_t *__restrict__ rp, con
     T xv[BR];
 #pragma unroll
     for (int q = 0; q < BR; ++q) xv[q] = __ldg(x + c * BR + q);
-    const T *v = val + (int64_t)k * (BR * BR);
+    T blk[BR * BR];
+    ldg_block<BR * BR, T>(val + (int64_t)k * (BR * BR), blk);
 #pragma unroll
     for (int r = 0; r < BR; ++r)
 #pragma unroll
-      for (int q = 0; q < BR; ++q) acc[r] += __ldg(v + r * BR + q) * xv[q];
+      for (int q = 0; q < BR; ++q) acc[r] += blk[r * BR + q] * xv[q];
   }
 #pragma unroll
   for (int r = 0; r < BR; ++r)

@@ -58,6 +58,9 @@ struct Arena {
     void *p = nullptr;
     MFS_CUDA(cudaMalloc(&p, (size_t)count * sizeof(T)));
     ptrs.push_back({p, count * (int64_t)sizeof(T)});
+    // the plain-BSR kernels read blocks with 16-byte loads from the start of
+    // a value array (cudaMalloc aligns to 256 bytes)
+    if (reinterpret_cast<uintptr_t>(p) & 15) throw CudaError(MFS_ERR_CUDA, "device allocation not 16-byte aligned");
     bytes += count * (int64_t)sizeof(T);
     return (T *)p;
   }
