@@ -288,40 +288,65 @@ k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ 
   }
 }
 
-template <int BR, int B0, int B1, int B2>
-__global__ void __launch_bounds__(kThreads)
+// Merged coupled rows in float64, H threads per block row.  H = 1: one
+// thread per row, 64-thread CTAs (two slices).  H > 1: a CTA of 32 H threads
+// takes one slice of 32 rows, its warp h the slots h, h + H, ...; the H
+// partial sums of a row are added in the fixed order h = 0, 1, ... through
+// shared memory.  More threads per row keep more FP64 FMAs in flight (the
+// FP64 pipe bounds this kernel on GB300).
+template <int BR, int B0, int B1, int B2, int H>
+__global__ void __launch_bounds__(H == 1 ? 64 : 32 * H)
 k_spmv_rows(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
             const int32_t *__restrict__ col, const double *__restrict__ val, const double *__restrict__ x0,
             const double *__restrict__ x1, const double *__restrict__ x2, double *__restrict__ y) {
   constexpr int BCT = B0 + B1 + B2;
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= nbr) return;
-  const int lane = (int)(row & 31);
-  const int64_t base = sp[row >> 5];
-  const int len = rl[row];
-  const int32_t *cp = col + base * 32 + lane;
-  const double *vp = val + base * (BR * BCT * 32) + lane;
+  const int lane = threadIdx.x & 31, h = H == 1 ? 0 : threadIdx.x >> 5;
+  const int64_t row = H == 1 ? (int64_t)blockIdx.x * 64 + threadIdx.x : (int64_t)blockIdx.x * 32 + lane;
+  const bool active = row < nbr;
   double acc[BR];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = 0.0;
+  if (active) {
+    const int64_t base = sp[row >> 5];
+    const int len = rl[row];
+    const int32_t *cp = col + base * 32 + lane;
+    const double *vp = val + base * (BR * BCT * 32) + lane;
 #pragma unroll 2
-  for (int t = 0; t < len; ++t) {
-    const int64_t c = __ldg(cp + (int64_t)t * 32);
-    double xv[BCT];
+    for (int t = h; t < len; t += H) {
+      const int64_t c = __ldg(cp + (int64_t)t * 32);
+      double xv[BCT];
 #pragma unroll
-    for (int q = 0; q < B0; ++q) xv[q] = __ldg(x0 + c * B0 + q);
+      for (int q = 0; q < B0; ++q) xv[q] = __ldg(x0 + c * B0 + q);
 #pragma unroll
-    for (int q = 0; q < B1; ++q) xv[B0 + q] = __ldg(x1 + c * B1 + q);
+      for (int q = 0; q < B1; ++q) xv[B0 + q] = __ldg(x1 + c * B1 + q);
 #pragma unroll
-    for (int q = 0; q < B2; ++q) xv[B0 + B1 + q] = __ldg(x2 + c * B2 + q);
-    const double *v = vp + (int64_t)t * (BR * BCT * 32);
+      for (int q = 0; q < B2; ++q) xv[B0 + B1 + q] = __ldg(x2 + c * B2 + q);
+      const double *v = vp + (int64_t)t * (BR * BCT * 32);
 #pragma unroll
-    for (int r = 0; r < BR; ++r)
+      for (int r = 0; r < BR; ++r)
 #pragma unroll
-      for (int q = 0; q < BCT; ++q) acc[r] += __ldg(v + (r * BCT + q) * 32) * xv[q];
+        for (int q = 0; q < BCT; ++q) acc[r] += __ldg(v + (r * BCT + q) * 32) * xv[q];
+    }
   }
+  if constexpr (H == 1) {
+    if (active)
 #pragma unroll
-  for (int r = 0; r < BR; ++r) y[row * BR + r] = acc[r];
+      for (int r = 0; r < BR; ++r) y[row * BR + r] = acc[r];
+  } else {
+    __shared__ double part[H - 1][BR][32];
+    if (h > 0)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) part[h - 1][r][lane] = acc[r];
+    __syncthreads();
+    if (h == 0 && active)
+#pragma unroll
+      for (int r = 0; r < BR; ++r) {
+        double a = acc[r];
+#pragma unroll
+        for (int q = 0; q < H - 1; ++q) a += part[q][r][lane];
+        y[row * BR + r] = a;
+      }
+  }
 }
 
 template <int BR, typename T, int U>
@@ -880,8 +905,17 @@ void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s) {
                2000 + A.br * 100 + A.bc * 10 + 1, A.nbr, 2.0 * A.nnzb * A.br * A.bc);
   const double *x0 = x + R.off[0], *x1 = x + R.off[1], *x2 = R.nb > 2 ? x + R.off[2] : x;
   const int b3[3] = {R.b[0], R.b[1], R.nb > 2 ? R.b[2] : 0};
-  MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+  const unsigned grid = (unsigned)A.nslices;  // H > 1: one slice per CTA
+  if (R.split == 4) {
+    MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2, 4><<<grid, 128, 0, s>>>(
+                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+  } else if (R.split == 2) {
+    MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2, 2><<<grid, 64, 0, s>>>(
+                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+  } else {
+    MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2, 1><<<grid_for(A.nbr, 64), 64, 0, s>>>(
+                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+  }
 }
 
 template <typename T>

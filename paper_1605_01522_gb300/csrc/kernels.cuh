@@ -78,6 +78,7 @@ struct RowMerged {
   int nb = 0;      // number of merged column fields (2 or 3)
   int b[3] = {0, 0, 0};
   int64_t off[3] = {0, 0, 0};  // offset of each column field in the coupled vector
+  int split = 1;   // threads per block row (1, 2 or 4), timed at setup
 };
 bool rows_supported(int br, const int *b, int nb);
 void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s);

@@ -360,8 +360,10 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
   }
   cudaStreamDestroy(st);
   {
+    // a setup that tuned the same shape concurrently and finished first
+    // decides, so that every handle of the process runs the same variant
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = best;
+    best = g_tune.emplace(key, best).first->second;
   }
   return tune_keep(ar, a, b, best);
 }
@@ -384,10 +386,12 @@ static dev::Sell upload_sell_dev(Arena &ar, const RawDev &A, bool want64, bool w
   dev::Sell a = upload_layout_dev(ar, src, 1, want64, want32, 0, st);
   dev::Sell b = upload_layout_dev(ar, src, 1, want64, want32, 1, st);
   MFS_CUDA(cudaStreamSynchronize(0));
-  const int best = tune_pick(a, b, want32, st);
+  int best = tune_pick(a, b, want32, st);
   {
+    // a setup that tuned the same shape concurrently and finished first
+    // decides, so that every handle of the process runs the same variant
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    g_tune[key] = best;
+    best = g_tune.emplace(key, best).first->second;
   }
   return tune_keep(ar, a, b, best);
 }
@@ -1275,6 +1279,52 @@ HBsr to_hbsr(const mfs_block &b) {
 // y_i once.  Empty result = per-block SpMVs.
 // The merged-row layout built on the device from the row field's input
 // blocks (same test as merge_rows: identical patterns, supported shapes).
+// Threads per block row of the merged float64 matvec (1, 2 or 4): timed
+// once per (row block shape, rows, blocks) and process, like the layouts.
+static std::map<std::tuple<int, int, int, int, int64_t, int64_t>, int> g_tune_rows;
+
+static int tune_rows(const dev::RowMerged &R, int64_t n, cudaStream_t st) {
+  const dev::Sell &A = R.M;
+  const auto key = std::make_tuple(A.br, R.b[0], R.b[1], R.nb > 2 ? R.b[2] : 0, (int64_t)A.nbr, (int64_t)A.nnzb);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_rows.find(key);
+    if (it != g_tune_rows.end()) return it->second;
+  }
+  double *x = nullptr, *y = nullptr;
+  MFS_CUDA(cudaMallocAsync((void **)&x, (size_t)std::max<int64_t>(1, n) * sizeof(double), st));
+  MFS_CUDA(cudaMallocAsync((void **)&y, (size_t)std::max<int64_t>(1, A.nrows()) * sizeof(double), st));
+  MFS_CUDA(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), st));
+  cudaEvent_t e0, e1;
+  MFS_CUDA(cudaEventCreate(&e0));
+  MFS_CUDA(cudaEventCreate(&e1));
+  int best = 1;
+  float tbest = 1e30f;
+  for (int split : {1, 2, 4}) {
+    dev::RowMerged T = R;
+    T.split = split;
+    for (int rep = 0; rep < 4; ++rep) {
+      MFS_CUDA(cudaEventRecord(e0, st));
+      dev::spmv_rows(T, x, y, st);
+      MFS_CUDA(cudaEventRecord(e1, st));
+      MFS_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      MFS_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep > 0 && ms < tbest) {
+        tbest = ms;
+        best = split;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(x, st);
+  cudaFreeAsync(y, st);
+  MFS_CUDA(cudaStreamSynchronize(st));
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_tune_rows.emplace(key, best).first->second;
+}
+
 std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb,
                                            const std::map<std::pair<int, int>, RawDev> &raw, int nf,
                                            const std::vector<int64_t> &foff, cudaStream_t st) {
@@ -1296,10 +1346,13 @@ std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<i
     dev::RowMerged R;
     R.M = upload_layout_dev(ar, src, nf, true, false, 0, st);
     R.nb = nf;
+    int64_t n = 0;
     for (int j = 0; j < nf; ++j) {
       R.b[j] = b[j];
       R.off[j] = foff[j];
+      n = std::max(n, foff[j] + src[j]->nbc * src[j]->bc);
     }
+    R.split = tune_rows(R, n, st);
     out.push_back(R);
   }
   return out;
