@@ -387,6 +387,24 @@ def run_mfs(args, rank, world):
         lib.kernel_stats(reset=True)
         e2e = {"value": world / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": 2 * 8 * n,
                "d2h_bytes_per_step": 8 * n}
+    # the V-cycles timed whole: preconditioner applications through mfs_apply
+    # (each one = every V-cycle kernel of one FGMRES iteration, plus the two
+    # float64 <-> float32 conversions), launched back to back with no
+    # per-launch events, bracketed by one event pair on the solver's stream
+    with torch.cuda.stream(stream):
+        v_in = b / torch.linalg.norm(b)
+        z_out = torch.empty_like(v_in)
+    for _ in range(3):
+        lib.apply(v_in, z_out)
+    n_apply = 20
+    ea = torch.cuda.Event(enable_timing=True)
+    eb = torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(n_apply):
+        lib.apply(v_in, z_out)
+    eb.record(stream)
+    eb.synchronize()
+    apply_ms = ea.elapsed_time(eb) / n_apply
     # roofline of the dominant kernel, timed live over the timed region.
     # float64 sparse kernels are bound by GB300's FP64 FMA rate (ncu: SM
     # throughput ~80 % while DRAM is ~50 %), float32 ones by HBM bandwidth.
@@ -437,6 +455,14 @@ def run_mfs(args, rank, world):
                                      "share_of_vcycle_time": round(v[1] / vms, 4), "launches": v[2]}
                                     for k, v in groups],
                   "timed": "warm-up solve, every launch timed (algorithmic bytes / summed event time)"}
+        it_w = max(1, infos[-1]["iters"])
+        vcycle["wall"] = {"GBps": vb / it_w / (apply_ms / 1e3) / 1e9,
+                          "frac": vb / it_w / (apply_ms / 1e3) / 1e9 / hbm_peak,
+                          "ms_per_apply": apply_ms, "bytes_per_apply": vb / it_w,
+                          "timed": f"{n_apply} back-to-back preconditioner applications (mfs_apply, the "
+                                   "V-cycle kernels of one iteration + 2 precision conversions), one event "
+                                   "pair, no per-launch events; bytes = the V-cycle kernels' algorithmic "
+                                   "bytes per iteration of the warm-up solve"}
     stats = stats_all
     launches_total = sum(v[0] for v in stats_all.values()) * args.steps
     if rank != 0:
