@@ -148,6 +148,9 @@ typedef struct {
   int gs_sweeps;                     /* MFS_GS: sweeps per smoother application (1) */
   double gs_omega;                   /* MFS_GS: damping omega of the Gauss-Seidel update (0.79,
                                         the paper's DD(GS(0.79)), Sec. 7.1); 0 < omega < 2 */
+  int rows_split;                    /* threads per block row of the float64 coupled matvec
+                                        (merged row layout): 0 (default) = timed at setup
+                                        among 1, 2 and 4; or 1, 2, 4 to fix it */
 } mfs_params;
 
 typedef struct {

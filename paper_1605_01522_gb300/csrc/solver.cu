@@ -1327,7 +1327,7 @@ static int tune_rows(const dev::RowMerged &R, int64_t n, cudaStream_t st) {
 
 std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb,
                                            const std::map<std::pair<int, int>, RawDev> &raw, int nf,
-                                           const std::vector<int64_t> &foff, cudaStream_t st) {
+                                           const std::vector<int64_t> &foff, int split, cudaStream_t st) {
   std::vector<dev::RowMerged> out;
   if (nf < 2 || nf > 3) return out;
   for (int i = 0; i < nf; ++i) {
@@ -1352,7 +1352,7 @@ std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<i
       R.off[j] = foff[j];
       n = std::max(n, foff[j] + src[j]->nbc * src[j]->bc);
     }
-    R.split = tune_rows(R, n, st);
+    R.split = split > 0 ? split : tune_rows(R, n, st);
     out.push_back(R);
   }
   return out;
@@ -1767,7 +1767,8 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       (p.smoother == MFS_GS && (p.gs_sweeps < 1 || !(p.gs_omega > 0.0) || !(p.gs_omega < 2.0))) ||
       (p.precond == MFS_BGS_GS && p.smoother != MFS_GS) ||
       (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
-      (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS))
+      (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS) ||
+      (p.rows_split != 0 && p.rows_split != 1 && p.rows_split != 2 && p.rows_split != 4))
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;
@@ -1864,7 +1865,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     const double t_dev = now_ms();
     // fine layouts built on the device from the uploaded input blocks
     for (auto &kv : hb) h->A64[kv.first] = upload_sell_dev(mat, rd.at(kv.first), true, f32, rst.s);
-    h->rows64 = merge_rows_dev(mat, hb, rd, h->nf, h->foff, rst.s);
+    h->rows64 = merge_rows_dev(mat, hb, rd, h->nf, h->foff, p.rows_split, rst.s);
     MFS_CUDA(cudaStreamSynchronize(rst.s));
     h->raw = nullptr;
     raw_arena.reset();

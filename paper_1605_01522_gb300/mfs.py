@@ -73,7 +73,8 @@ class Params(C.Structure):
                 ("max_iters", C.c_int), ("precision", C.c_int), ("seed", C.c_uint64),
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
                 ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int),
-                ("simple_pred", C.c_int), ("gs_sweeps", C.c_int), ("gs_omega", C.c_double)]
+                ("simple_pred", C.c_int), ("gs_sweeps", C.c_int), ("gs_omega", C.c_double),
+                ("rows_split", C.c_int)]
 
 
 class Info(C.Structure):

@@ -4,7 +4,9 @@ import ctypes
 import os
 import re
 
-from paper_1605_01522_gb300 import build, mfs
+import pytest
+
+from paper_1605_01522_gb300 import build, inputs, mfs
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -33,3 +35,14 @@ def test_status_strings_and_defaults():
     p = mfs.default_params()
     assert (p.precond, p.bgs_order, p.bgs_sweeps, p.restart, p.cheb_degree) == (0, 0, 1, 50, 2)
     assert abs(p.cheb_ratio - 30.0) < 1e-15 and abs(p.cheb_boost - 1.1) < 1e-15
+    assert p.rows_split == 0  # threads per row of the float64 matvec: timed at setup
+
+
+@pytest.mark.parametrize("split", [3, -1, 8])
+def test_bad_rows_split_is_refused(split):
+    """Only 0 (timed) and 1, 2, 4 threads per block row exist; parameters are
+    checked before anything is built (a host-only setup reaches the check)."""
+    s = inputs.thermo_elastic_2d(ne=4)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(s, setup_only=1, rows_split=split)
+    assert e.value.code == mfs.ERR_INVALID

@@ -70,10 +70,13 @@ def _oracle_solve(s, kw, pc, extra):
     return krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=600), D
 
 
+@pytest.mark.parametrize("rows_split", [0, 1, 2, 4])
 @pytest.mark.parametrize("name", ["2d", "3d", "3d2"])
-def test_matvec_matches_scipy(name):
+def test_matvec_matches_scipy(name, rows_split):
+    """Every variant of the merged-row float64 matvec (1, 2 or 4 threads per
+    block row, or the one the setup's timing picks)."""
     s, kw = _small(name)
-    with mfs.Solver(s, **kw) as lib:
+    with mfs.Solver(s, **kw, rows_split=rows_split) as lib:
         D = precond.assemble(s.scipy_blocks(), s.nfields)
         x = np.random.default_rng(1).standard_normal(s.ndofs)
         y = lib.matvec(_cuda(x)).cpu().numpy()
