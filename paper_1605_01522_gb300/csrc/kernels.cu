@@ -1,7 +1,9 @@
-// Solve-phase CUDA kernels for sm_103a: blocked SELL-32 SpMV, the fused
-// residual + polynomial smoothing step, the dense LU coarse solve and the
-// CGS2 Arnoldi reductions.  All sparse work is HBM-bandwidth bound; loads of
-// a warp are contiguous per slot and every reduction has a fixed order.
+// Solve-phase CUDA kernels for sm_103a: blocked SELL-32 and plain-BSR SpMV,
+// the fused residual + polynomial smoothing step, multicolour Gauss-Seidel,
+// the coarse solves and the CGS2 Arnoldi reductions.  The float32 sparse work
+// is bound by HBM bandwidth (small coarse levels by latency), the float64
+// matvec and CGS2 passes by GB300's FP64 rate; loads of a warp are contiguous
+// per slot and every reduction has a fixed order.
 #include "kernels.cuh"
 
 #include <cstdint>

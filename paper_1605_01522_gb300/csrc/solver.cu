@@ -1273,12 +1273,6 @@ HBsr to_hbsr(const mfs_block &b) {
   return A;
 }
 
-// Fine operator rows: when every block A_ij of a block row i exists and all
-// share one sparsity pattern (fields on the same nodes), store the row's
-// blocks side by side so one kernel reads each column index once and writes
-// y_i once.  Empty result = per-block SpMVs.
-// The merged-row layout built on the device from the row field's input
-// blocks (same test as merge_rows: identical patterns, supported shapes).
 // Threads per block row of the merged float64 matvec (1, 2 or 4): timed
 // once per (row block shape, rows, blocks) and process, like the layouts.
 static std::map<std::tuple<int, int, int, int, int64_t, int64_t>, int> g_tune_rows;
@@ -1325,6 +1319,11 @@ static int tune_rows(const dev::RowMerged &R, int64_t n, cudaStream_t st) {
   return g_tune_rows.emplace(key, best).first->second;
 }
 
+// Fine operator rows: when every block A_ij of a block row i exists and all
+// share one sparsity pattern (fields on the same nodes), store the row's
+// blocks side by side so one kernel reads each column index once and writes
+// y_i once; built on the device from the row field's uploaded input blocks.
+// Empty result = per-block SpMVs.
 std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb,
                                            const std::map<std::pair<int, int>, RawDev> &raw, int nf,
                                            const std::vector<int64_t> &foff, int split, cudaStream_t st) {
@@ -1358,54 +1357,6 @@ std::vector<dev::RowMerged> merge_rows_dev(Arena &ar, const std::map<std::pair<i
   return out;
 }
 
-std::vector<dev::RowMerged> merge_rows(Arena &ar, const std::map<std::pair<int, int>, HBsr> &hb, int nf,
-                                       const std::vector<int64_t> &foff) {
-  std::vector<dev::RowMerged> out;
-  if (nf < 2 || nf > 3) return out;
-  for (int i = 0; i < nf; ++i) {
-    std::vector<const HBsr *> row;
-    for (int j = 0; j < nf; ++j) {
-      auto it = hb.find({i, j});
-      if (it == hb.end()) return {};
-      row.push_back(&it->second);
-    }
-    int b[3] = {0, 0, 0};
-    for (int j = 0; j < nf; ++j) {
-      if (row[j]->rp != row[0]->rp || row[j]->ci != row[0]->ci) return {};
-      b[j] = row[j]->bc;
-    }
-    const int br = row[0]->br;
-    if (!dev::rows_supported(br, b, nf)) return {};
-    HBsr M;
-    M.br = br;
-    M.bc = b[0] + b[1] + b[2];
-    M.nbr = row[0]->nbr;
-    M.nbc = row[0]->nbc;
-    M.rp = row[0]->rp;
-    M.ci = row[0]->ci;
-    M.v.assign((size_t)M.nnzb() * M.br * M.bc, 0.0);
-#pragma omp parallel for schedule(static)
-    for (int64_t k = 0; k < M.nnzb(); ++k)
-      for (int r = 0; r < br; ++r) {
-        int o = 0;
-        for (int j = 0; j < nf; ++j) {
-          for (int q = 0; q < b[j]; ++q) M.v[(size_t)k * br * M.bc + r * M.bc + o + q] = row[j]->blk(k)[r * b[j] + q];
-          o += b[j];
-        }
-      }
-    dev::RowMerged R;
-    R.M = upload_layout(ar, M, true, false, 0);
-    R.nb = nf;
-    for (int j = 0; j < nf; ++j) {
-      R.b[j] = b[j];
-      R.off[j] = foff[j];
-    }
-    out.push_back(R);
-  }
-  return out;
-}
-
-// Host half of the setup: hierarchies, SIMPLE diagonal and explicit S~.
 // Multicolour Gauss-Seidel colours of every smoothed level field (levels
 // below the coarsest; every level of the single-level BGS(GS) and of
 // AMG(SIMPLE)'s level Schur complements).
@@ -1421,6 +1372,7 @@ void color_levels(mfs_handle *h) {
   run(h->host->hg1, p.precond == MFS_AMG_SIMPLE);
 }
 
+// Host half of the setup: hierarchies, SIMPLE diagonal and explicit S~.
 void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks,
                 const std::vector<FieldInfo> &info) {
   const mfs_params &p = h->prm;
