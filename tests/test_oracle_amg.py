@@ -6,6 +6,11 @@ of the lexicographically-first maximal independent set, exact reproduction of
 the near-nullspace by the tentative prolongator, uniqueness of the QR
 factorisation with positive diagonal, symmetry of Galerkin products, the
 energy decrease of prolongator smoothing and a dense eigenvalue solver.
+The strength graph at theta > 0 is recomputed by brute force from dense node
+blocks (numpy's Frobenius norm pair by pair, then the union with the
+transpose) on Q1 elasticity / diffusion blocks and on non-symmetric random
+block matrices; squared norms, a max-norm and a missing symmetrisation each
+fail that comparison.
 Petrov-Galerkin transfers (Sala & Tuminaro 2008): each column parameter is the
 minimiser of its D^-1-norm objective (checked by brute force), row parameters
 are the column minimum over the row pattern, P keeps the kernel of a
@@ -280,3 +285,122 @@ def test_pg_vcycle_beats_transposed_restriction_on_convection_diffusion():
         assert r.converged
         its.append(r.iters)
     assert its[1] < 0.8 * its[0], its
+
+
+# ---------------------------------------------------------------------------
+# Strength of connection at theta > 0, pinned by brute force over node pairs.
+# The oracle forms all node-block norms at once by a sparse product
+# (E^T (A .* A) E); the check below slices every dense b x b node block,
+# takes its Frobenius norm with numpy.linalg.norm, applies the threshold
+# ||A_IJ||_F > theta sqrt(||A_II||_F ||A_JJ||_F) pair by pair and then
+# takes the union with the transpose (the symmetrised graph of the
+# smoothed-aggregation setup, Sec. 3.3 after Vanek, Mandel & Brezina).
+# ---------------------------------------------------------------------------
+
+def _strength_brute(A, b, theta):
+    D = A.toarray()
+    nn = D.shape[0] // b
+    blk = lambda I, J: D[I * b:(I + 1) * b, J * b:(J + 1) * b]
+    dn = [np.linalg.norm(blk(I, I), "fro") for I in range(nn)]
+    S = np.zeros((nn, nn), bool)
+    for I in range(nn):
+        for J in range(nn):
+            if I == J:
+                continue
+            nij = np.linalg.norm(blk(I, J), "fro")
+            if nij > 0.0 and nij > theta * np.sqrt(dn[I] * dn[J]):
+                S[I, J] = True
+    return S | S.T
+
+
+def _random_block_matrix(nn, b, seed):
+    """Non-symmetric random node-block matrix: about 15 % of the off-diagonal
+    node pairs present in one direction only, block magnitudes log-uniform
+    over four decades (so the threshold cuts through them), diagonal blocks
+    of unit scale."""
+    rng = np.random.default_rng(seed)
+    D = np.zeros((nn * b, nn * b))
+    for I in range(nn):
+        D[I * b:(I + 1) * b, I * b:(I + 1) * b] = rng.standard_normal((b, b)) + 3.0 * np.eye(b)
+        for J in range(nn):
+            if J != I and rng.random() < 0.15:
+                scale = 10.0 ** rng.uniform(-3.0, 1.0)
+                B = scale * rng.standard_normal((b, b))
+                if b > 1 and rng.random() < 0.5:  # one dominant entry: max-norm != Frobenius
+                    B = np.zeros((b, b))
+                    B[rng.integers(b), rng.integers(b)] = scale
+                D[I * b:(I + 1) * b, J * b:(J + 1) * b] = B
+    return sp.csr_matrix(D)
+
+
+def _strength_cases():
+    cases = []
+    s2 = inputs.thermo_elastic_2d(ne=6)
+    s3 = inputs.coupled_box_3d(ne=4, nfields=3, seed=1)
+    for theta in (0.02, 0.3):
+        cases.append((f"te2d-elast-{theta}", s2.blocks[(0, 0)].to_scipy(), 2, theta))
+        cases.append((f"box-elast-{theta}", s3.blocks[(0, 0)].to_scipy(), 3, theta))
+        cases.append((f"box-diff-{theta}", s3.blocks[(2, 2)].to_scipy(), 1, theta))
+        for b in (1, 2, 3):
+            cases.append((f"rand-b{b}-{theta}", _random_block_matrix(40, b, 7 + b), b, theta))
+    return cases
+
+
+@pytest.mark.parametrize("name,A,b,theta", _strength_cases(), ids=lambda v: v if isinstance(v, str) else "")
+def test_strength_graph_matches_brute_force_node_blocks(name, A, b, theta):
+    G = amg.strength_graph(A, b, theta)
+    S = _strength_brute(A, b, theta)
+    assert np.array_equal(G.toarray() > 0, S), name
+    if name.startswith("rand"):
+        # the raw relation is not symmetric here, so the union matters
+        D = A.toarray()
+        nn = D.shape[0] // b
+        raw = np.array([[I != J and np.linalg.norm(D[I*b:(I+1)*b, J*b:(J+1)*b]) > 0 for J in range(nn)]
+                        for I in range(nn)])
+        assert not np.array_equal(raw, raw.T)
+
+
+def _mutant(kind):
+    """The oracle's strength function with one planted mistake."""
+    def f(A, b, theta):
+        nn = A.shape[0] // b
+        E = amg.node_incidence(nn, b)
+        if kind == "maxnorm":
+            # per node block the largest |a| instead of the Frobenius norm
+            Ab = abs(A).tocoo()
+            mx = {}
+            for r, c, v in zip(Ab.row // b, Ab.col // b, Ab.data):
+                mx[(r, c)] = max(mx.get((r, c), 0.0), v)
+            rows = np.array([k[0] for k in mx])
+            cols = np.array([k[1] for k in mx])
+            norms = np.array(list(mx.values()))
+        else:
+            A2 = A.multiply(A).tocsr()
+            N = (E.T @ A2 @ E).tocoo()
+            rows, cols = N.row, N.col
+            norms = N.data if kind == "squared" else np.sqrt(N.data)
+        dn = np.zeros(nn)
+        on = rows == cols
+        dn[rows[on]] = norms[on]
+        keep = (~on) & (norms > theta * np.sqrt(dn[rows] * dn[cols]))
+        G = sp.csr_matrix((np.ones(int(keep.sum())), (rows[keep], cols[keep])), shape=(nn, nn))
+        if kind != "nosym":
+            G = ((G + G.T) > 0).astype(np.float64).tocsr()
+        return G
+    return f
+
+
+@pytest.mark.parametrize("kind", ["squared", "maxnorm", "nosym"])
+def test_strength_brute_force_catches_planted_mistakes(kind):
+    """Each planted mistake (squared norms, max-norm for Frobenius, no
+    symmetrisation) disagrees with the brute force on at least one case,
+    while the unmutated form of the mutant agrees on all of them."""
+    bad = _mutant(kind)
+    good = _mutant("none")
+    caught = False
+    for name, A, b, theta in _strength_cases():
+        S = _strength_brute(A, b, theta)
+        assert np.array_equal(good(A, b, theta).toarray() > 0, S), name
+        if not np.array_equal(bad(A, b, theta).toarray() > 0, S):
+            caught = True
+    assert caught, kind
