@@ -8,18 +8,25 @@ coarse LU and residuals stay FP64.  One step = one full solve from x0 = 0
 with the hierarchy resident (setup excluded, timed separately).
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-on the same workload (bounded sample of FGMRES iterations, scaled to
-solves/s by the oracle's stored iteration count).
+on the same workload: each step is one whole oracle solve (all its FGMRES
+iterations), the steps run concurrently in one single-threaded process per
+host core, and the timed region is the wall time of the K timed steps.
 """
 from __future__ import annotations
 
+import os
+import sys
+
+if "reference" in sys.argv:
+    # every oracle process computes on one core: one BLAS thread each
+    for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        os.environ[_v] = "1"
+
 import argparse
 import json
-import os
 import statistics
 import subprocess
 import tempfile
-import sys
 import time
 
 import numpy as np
@@ -30,12 +37,18 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled solves/s to 1e-8 residual"
 UNIT = "solves/s"
 NE = 64
-WORKLOAD = "coupled_box_3d_ne64_f3"
-SOLVER_KW = dict(max_levels=5, coarse_max=1000)
 FALLBACK_HBM_GBS = 6800.0
-# FP64 FMA peak: 152 SMs x 2.07 GHz x 4 FP64 flops/clock/SM = 1.26 TFLOP/s
-# (the nominal 1.25 TFLOP/s FP64 rate of this part); no measured value exists
-FP64_TFLOPS = 1.25
+# mesh edge of each workload unless --ne is given
+DEFAULT_NE = {"box": 64, "cons": 64, "fsi": 48, "oseen": 48, "te2d": 32}
+
+
+def solver_kw(args=None):
+    """Hierarchy depth: the 2D thermo-elastic system takes 3 SA-AMG levels
+    (coarsening continues to the third whatever its size), the 3D systems up
+    to 5 levels with a coarsest level of at most 1000 dofs."""
+    if args is not None and args.workload == "te2d":
+        return dict(max_levels=3, coarse_max=0)
+    return dict(max_levels=5, coarse_max=1000)
 CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
                 "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
                 "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
@@ -43,10 +56,13 @@ CLOCK_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_eve
 
 def workload_config(args, s, extra=None):
     if args.workload == "fsi":
-        what = f"4-field split-box saddle 48^3 Q1 ({s.ndofs} dofs: structure | mesh + PSPG Stokes u, p)"
+        what = f"4-field split-box saddle {NE}^3 Q1 ({s.ndofs} dofs: structure | mesh + PSPG Stokes u, p)"
     elif args.workload == "oseen":
-        what = (f"4-field split-box saddle 48^3 Q1 with an Oseen velocity block, wind (0.2, 0.1, 0) ({s.ndofs} dofs), "
+        what = (f"4-field split-box saddle {NE}^3 Q1 with an Oseen velocity block, wind (0.2, 0.1, 0) ({s.ndofs} dofs), "
                 f"velocity transfers {'R = P^T' if args.no_pg else 'Petrov-Galerkin'}")
+    elif args.workload == "te2d":
+        what = (f"2-field thermo-elastic 2D {NE}x{NE} Q1 ({s.ndofs} dofs: plane-strain elasticity + transient heat), "
+                f"3 SA-AMG levels")
     elif args.workload == "cons":
         what = (f"constrained 3-field box {NE}^3 Q1 + 4 patch-mean Lagrange multipliers ({s.ndofs} dofs, "
                 f"zero multiplier block)")
@@ -60,7 +76,7 @@ def workload_config(args, s, extra=None):
         "ndofs": s.ndofs,
         "precond": args.precond,
         "precision": args.precision,
-        "l2": "inputs larger than L2 (matrices ~2 GB per solve pass)",
+        "l2": "L2 flushed between timed solves (256 MB write outside each solve's event pair)",
         "parallelism": "replicas" if args.gpus > 1 else "1 GPU",
     }
     if args.precond == "simple":
@@ -205,25 +221,19 @@ def ncu_traffic(kernel, rows):
 
 def make_system(args=None):
     from paper_1605_01522_gb300 import inputs
-    if args is not None and args.workload == "fsi":
-        return inputs.fsi_box(ne=48, seed=2)
-    if args is not None and args.workload == "cons":
+    w = args.workload if args is not None else "box"
+    if w == "fsi":
+        return inputs.fsi_box(ne=NE, seed=2)
+    if w == "cons":
         return inputs.constrained_box(ne=NE, nfields=3, seed=5)
-    if args is not None and args.workload == "oseen":
-        s = inputs.fsi_box(ne=48, seed=2, wind=(0.2, 0.1, 0.0))
+    if w == "oseen":
+        s = inputs.fsi_box(ne=NE, seed=2, wind=(0.2, 0.1, 0.0))
         if args.no_pg:
             s.fields[2].petrov_galerkin = False
         return s
+    if w == "te2d":
+        return inputs.thermo_elastic_2d(ne=NE, seed=0)
     return inputs.coupled_box_3d(ne=NE, nfields=3, seed=1)
-
-
-def counts_key(args):
-    name = {"fsi": "fsi_box_ne48", "cons": f"constrained_box_ne{NE}_f3_m4",
-            "oseen": "oseen_fsi_box_ne48"}.get(args.workload, WORKLOAD)
-    pc = args.precond + ("+amg_bgs" if args.precond == "simple" and args.simple_pred == "amg_bgs" else "")
-    pc += "+gs" if args.smoother == "gs" and args.precond != "bgs_gs" else ""
-    pc += "+sa" if args.workload == "oseen" and args.no_pg else ""
-    return name + "/" + pc
 
 
 def precond_extra(args):
@@ -240,76 +250,189 @@ def precond_extra(args):
     return extra
 
 
-def oracle_params(name, extra):
+def oracle_params(args):
     """The oracle's parameter block for the library options of precond_extra."""
     from oracle import precond
     from oracle.cycles import SmootherParams
-    ex = dict(extra)
+    ex = dict(precond_extra(args))
     sm = SmootherParams("gs", omega=0.79, sweeps=1) if ex.pop("smoother", None) == "gs" else None
-    return precond.Params(name, **SOLVER_KW, **ex, smoother=sm)
+    return precond.Params(args.precond, **solver_kw(args), **ex, smoother=sm)
 
 
-def oracle_counts():
-    path = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
-    with open(path) as f:
-        return json.load(f)
+# ---------------------------------------------------------------------------
+# The FP64 CPU oracle, timed by whole solves
+# ---------------------------------------------------------------------------
+
+_ORACLE = {}  # the forking process's operator, hierarchy and right-hand side
 
 
-def oracle_sample(s, precond_name, n_iter, extra=None):
-    """Time n_iter FGMRES iterations of the FP64 oracle (its own hierarchy,
-    built untimed) on the full workload; returns (seconds per iteration, setup s)."""
-    from oracle import amg, krylov, precond
+def oracle_prepare(args):
+    """Build the workload and the oracle's own hierarchy (untimed); returns
+    (system, setup seconds)."""
+    from oracle import amg, precond
+    s = make_system(args)
     A = s.scipy_blocks()
     D = precond.assemble(A, s.nfields)
     t0 = time.perf_counter()
-    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields],
-                               oracle_params(precond_name, extra or {}))
-    t1 = time.perf_counter()
-    krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=n_iter)
-    t2 = time.perf_counter()
-    return (t2 - t1) / n_iter, t1 - t0
+    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields], oracle_params(args))
+    _ORACLE.update(D=D, M=M, rhs=s.rhs)
+    return s, time.perf_counter() - t0
+
+
+def _oracle_worker(core, tasks, results):
+    """Forked worker: pinned to one core, runs whole FGMRES(50) solves from
+    x0 = 0 to 1e-8 on the inherited (read-only) operator and hierarchy."""
+    from oracle import krylov
+    try:
+        os.sched_setaffinity(0, {core})
+    except OSError:
+        pass
+    D, M, rhs = _ORACLE["D"], _ORACLE["M"], _ORACLE["rhs"]
+    while True:
+        cmd = tasks.get()
+        if cmd is None:
+            return
+        count, budget = cmd
+        out, t_start = [], time.perf_counter()
+        while True:
+            t0 = time.perf_counter()
+            r = krylov.fgmres(lambda v: D @ v, M, rhs, 1e-8, 50)
+            out.append((time.perf_counter() - t0, r.iters, float(r.relres)))
+            done = len(out) >= count if count else time.perf_counter() - t_start >= budget
+            if done:
+                break
+        results.put((core, out))
+
+
+class OraclePool:
+    """One single-threaded oracle process per host core, forked from the
+    process that built the hierarchy (copy-on-write, never written after the
+    fork; this process has made no CUDA call)."""
+
+    def __init__(self, cores):
+        import multiprocessing as mp
+        ctx = mp.get_context("fork")
+        self.cores = list(cores)
+        self.tasks = [ctx.SimpleQueue() for _ in self.cores]
+        self.results = ctx.SimpleQueue()
+        self.procs = [ctx.Process(target=_oracle_worker, args=(c, q, self.results), daemon=True)
+                      for c, q in zip(self.cores, self.tasks)]
+        for p in self.procs:
+            p.start()
+
+    def run(self, cmds):
+        """cmds[i] = (count, budget_s) for worker i, or None to leave it idle;
+        a worker runs `count` solves, or (count 0) solves until budget_s has
+        passed (at least one).  Returns (wall seconds from the first command
+        to the last result, [(seconds, iters, relres) of every solve])."""
+        t0 = time.perf_counter()
+        busy = 0
+        for q, c in zip(self.tasks, cmds):
+            if c is not None:
+                q.put(c)
+                busy += 1
+        out = []
+        for _ in range(busy):
+            out += self.results.get()[1]
+        return time.perf_counter() - t0, out
+
+    def close(self):
+        for q in self.tasks:
+            q.put(None)
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def split_steps(total, nproc):
+    return [(total // nproc + (1 if i < total % nproc else 0), 0.0) if i < total else None for i in range(nproc)]
 
 
 def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle on the host cores.  One step = one whole
+    solve; the K timed steps run concurrently, one single-threaded process
+    per core (at most K processes), after W warm-up solves spread the same
+    way; ms_per_step = wall time of the K timed steps / K."""
     if rank != 0:
         return
-    s = make_system(args)
-    counts = oracle_counts()
-    key = counts_key(args)
-    iters = counts[key]["iters"]
-    n_iter = 2
-    times = []
-    setup_s = None
-    from oracle import amg, krylov, precond
-    A = s.scipy_blocks()
-    D = precond.assemble(A, s.nfields)
-    t0 = time.perf_counter()
-    M = precond.Preconditioner(A, [amg.FieldSpec.of(f) for f in s.fields],
-                               oracle_params(args.precond, precond_extra(args)))
-    setup_s = time.perf_counter() - t0
-    for k in range(args.warmup + args.steps):
-        t1 = time.perf_counter()
-        krylov.fgmres(lambda v: D @ v, M, s.rhs, 1e-8, 50, maxiter=n_iter)
-        dt = (time.perf_counter() - t1) / n_iter * iters
-        if k >= args.warmup:
-            times.append(dt)
-    per_solve = statistics.mean(times)
-    value = 1.0 / per_solve
-    sample = (f"{n_iter} FGMRES iterations per step of the FP64 oracle (scipy, its own hierarchy, setup "
-              f"{setup_s:.1f} s untimed) on the full workload, scaled by the oracle's {iters} iterations per solve")
+    s, setup_s = oracle_prepare(args)
+    cores = sorted(os.sched_getaffinity(0))
+    nproc = max(1, min(len(cores), args.steps))
+    pool = OraclePool(cores[:nproc])
+    if args.warmup:
+        pool.run(split_steps(args.warmup, nproc))
+    wall, res = pool.run(split_steps(args.steps, nproc))
+    pool.close()
+    value = args.steps / wall
+    iters = sorted({r[1] for r in res})
+    sample = (f"{args.steps} whole FGMRES(50) solves to 1e-8 of the FP64 oracle (numpy/scipy, {iters} iterations "
+              f"each, true residual <= {max(r[2] for r in res):.2e}) run concurrently by {nproc} single-threaded "
+              f"processes pinned one per host core (after {args.warmup} warm-up solves); the oracle's own "
+              f"hierarchy built once before the processes fork ({setup_s:.1f} s, untimed)")
+    cfg = workload_config(args, s, {"oracle_iters": iters, "oracle_setup_s": round(setup_s, 1),
+                                    "solve_s_mean": statistics.mean(r[0] for r in res)})
+    cfg["precision"] = "fp64"
+    cfg["workload"] = cfg["workload"].replace(f"in {args.precision.upper()}", "in FP64 (the CPU oracle)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(args, s, {"oracle_iters": iters}),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nproc, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def run_oracle_baseline(args):
+    """CPU-baseline child of the GPU arm: prepares the oracle, forks one
+    process per core, prints "ready", and after a line on stdin (the GPU
+    arm's measurements are over) times whole solves on one core alone, then
+    on every core at once; prints the result as one JSON line."""
+    s, setup_s = oracle_prepare(args)
+    cores = sorted(os.sched_getaffinity(0))
+    pool = OraclePool(cores)
+    print("ready", flush=True)
+    sys.stdin.readline()
+    budget = args.baseline_s
+    w1, r1 = pool.run([(0, budget)] + [None] * (len(cores) - 1))
+    wn, rn = pool.run([(0, budget)] * len(cores))
+    pool.close()
+    print(json.dumps({"single": {"solves": len(r1), "wall_s": w1, "value": len(r1) / w1,
+                                 "iters": sorted({r[1] for r in r1}), "relres": max(r[2] for r in r1)},
+                      "all": {"solves": len(rn), "wall_s": wn, "value": len(rn) / wn, "cores": len(cores),
+                              "iters": sorted({r[1] for r in rn})},
+                      "setup_s": setup_s}), flush=True)
+
+
+class BaselineChild:
+    """The oracle baseline in a separate process (started before any GPU work
+    so that its preparation overlaps the GPU setup; its timed solves start
+    only when release() is called)."""
+
+    def __init__(self, args):
+        cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--oracle-baseline",
+               "--workload", args.workload, "--ne", str(NE), "--precond", args.precond,
+               "--smoother", args.smoother, "--simple-pred", args.simple_pred,
+               "--baseline-s", str(args.baseline_s)] + (["--no-pg"] if args.no_pg else [])
+        self.proc = subprocess.Popen(cmd, stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True)
+
+    def result(self):
+        self.proc.stdin.write("go\n")
+        self.proc.stdin.flush()
+        res = None
+        for line in self.proc.stdout:
+            line = line.strip()
+            if line.startswith("{"):
+                res = json.loads(line)
+        self.proc.wait()
+        return res
 
 
 def run_mfs(args, rank, world):
     import torch
     from paper_1605_01522_gb300 import mfs
 
+    # the oracle baseline runs in its own process: start it before any GPU
+    # work (its preparation overlaps ours; its solves wait for release)
+    child = BaselineChild(args) if world == 1 and not args.no_cpu_baseline else None
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     dist = None
@@ -319,7 +442,7 @@ def run_mfs(args, rank, world):
     s = make_system(args)
     stream = torch.cuda.Stream(device=dev)
     prm = mfs.default_params(precond=args.precond, precision=args.precision, profile=1,
-                             cuda_stream=stream.cuda_stream, no_graphs=int(args.no_graphs), **SOLVER_KW,
+                             cuda_stream=stream.cuda_stream, no_graphs=int(args.no_graphs), **solver_kw(args),
                              **precond_extra(args))
     t0 = time.perf_counter()
     lib = mfs.Solver(s, params=prm)
@@ -346,23 +469,30 @@ def run_mfs(args, rank, world):
         torch.cuda.synchronize()
         _, info, rc = lib.solve(b, x, tol=1e-8)
     lib.kernel_stats(reset=True)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
+    # each timed solve is bracketed by its own event pair; between solves a
+    # 256 MB write (twice the 129 MB L2) evicts the previous solve's data, so
+    # every solve starts from HBM even when its matrices would fit in L2
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
-        ev0.record(stream)
-        for _ in range(args.steps):
+        for k in range(args.steps):
             with torch.cuda.stream(stream):
+                flush.fill_(float(k))
                 x.zero_()
+            evs[k][0].record(stream)
             _, info, rc = lib.solve(b, x, tol=1e-8)
+            evs[k][1].record(stream)
             infos.append(info)
             if rc != mfs.OK:
                 raise RuntimeError(f"solve failed rc={rc} info={info}")
-        ev1.record(stream)
         torch.cuda.synchronize()
-    elapsed = ev0.elapsed_time(ev1) / 1e3
+        # the FP64 FMA rate of this GPU at the clocks of the timed region
+        # (the denominator of the float64 kernels' roofline)
+        fp64_peak = mfs.fp64_rate(stream.cuda_stream)
+    elapsed = sum(e0.elapsed_time(e1) for e0, e1 in evs) / 1e3
     if dist:
         dist.barrier()
     value, elapsed = reduce_timing(elapsed, args.steps, world, dist, dev)
@@ -379,6 +509,9 @@ def run_mfs(args, rank, world):
         e2e_times = []
         for k in range(max(2, args.steps // 2) + 1):
             xh.zero_()
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))
+            stream.synchronize()
             t1 = time.perf_counter()
             _, info_h, rc = lib.solve(bh.numpy(), xh.numpy(), tol=1e-8)
             dt = time.perf_counter() - t1
@@ -413,9 +546,12 @@ def run_mfs(args, rank, world):
     gbps = nbytes / (ms / 1e3) / 1e9
     tflops = flops / (ms / 1e3) / 1e12
     if kname.endswith("f64>"):
-        roof = {"bound": "alu", "achieved": tflops, "peak": FP64_TFLOPS, "unit": "TFLOP/s",
-                "frac": tflops / FP64_TFLOPS, "peak_kind": "nominal FP64 FMA rate (152 SMs x 2.07 GHz x 4 flop/clk)",
-                "hbm_GBps": gbps, "hbm_frac": gbps / hbm_peak}
+        roof = {"bound": "alu", "achieved": tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": tflops / fp64_peak,
+                "peak_kind": "measured (mfs_fp64_rate: independent FP64 FMA chains on every SM, best of 5, "
+                             "right after the timed region)",
+                "fp64_nominal_TFLOPs": 1.25, "hbm_GBps": gbps, "hbm_frac": gbps / hbm_peak,
+                "hbm_peak": hbm_peak, "hbm_peak_kind": peak_kind}
     else:
         roof = {"bound": "hbm", "achieved": gbps, "peak": hbm_peak, "unit": "GB/s", "frac": gbps / hbm_peak,
                 "peak_kind": peak_kind}
@@ -468,14 +604,19 @@ def run_mfs(args, rank, world):
     if rank != 0:
         return
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        counts = oracle_counts()
-        iters_o = counts[counts_key(args)]["iters"]
-        n_iter = 3
-        per_iter, osetup = oracle_sample(s, args.precond, n_iter, precond_extra(args))
-        cpu = {"value": 1.0 / (per_iter * iters_o), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{n_iter} FGMRES({args.precond}) iterations of the FP64 oracle on the full workload "
-                         f"(own hierarchy, setup {osetup:.1f} s untimed), scaled by its {iters_o} iterations/solve"}
+    if child is not None:
+        b = child.result()
+        if b:
+            one, alln = b["single"], b["all"]
+            cpu = {"value": one["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{one['solves']} whole FGMRES(50) solve(s) to 1e-8 of the FP64 oracle (numpy/scipy, "
+                             f"{one['iters']} iterations, true residual {one['relres']:.2e}) on one host core, "
+                             f"{one['wall_s']:.1f} s; own hierarchy built untimed ({b['setup_s']:.1f} s); run after "
+                             f"the GPU measurements",
+                   "all_cores": {"value": alln["value"], "unit": UNIT, "cores": alln["cores"],
+                                 "sample": f"{alln['solves']} whole solves by {alln['cores']} single-threaded "
+                                           f"processes pinned one per core, started together, "
+                                           f"{alln['wall_s']:.1f} s wall"}}
     shares = {c: round(v[1] / max(1e-9, sum(u[1] for u in stats.values())), 4) for c, v in stats.items()}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -509,7 +650,7 @@ def run_batch(args, rank, world):
     t0 = time.perf_counter()
     sizes, mats, rhs = inputs.batch_workload(args.nsys, 12, 48, 3)
     t1 = time.perf_counter()
-    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, **SOLVER_KW) for ne, sy in mats.items()}
+    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, **solver_kw(args)) for ne, sy in mats.items()}
     solvers, used = [], set()
     for ne in sizes.tolist():
         solvers.append(base[ne] if ne not in used else base[ne].clone())
@@ -578,7 +719,7 @@ def run_serve(args, rank, world):
     picks = rng.integers(len(keys), size=args.requests)
     reuse = rng.random(args.requests) < 0.3
     srv = serving.Server(hbm_budget=int(args.hbm_gb * (1 << 30)), workers=args.threads, max_setups=args.max_setups,
-                         precond=args.precond, precision=args.precision, **SOLVER_KW)
+                         precond=args.precond, precision=args.precision, **solver_kw(args))
     t0 = time.perf_counter()
     t = t0
     for i in range(args.requests):
@@ -615,13 +756,18 @@ def main():
     ap.add_argument("--precision", default="fp32p", choices=["fp32p", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
-    ap.add_argument("--ne", type=int, default=NE, help="mesh edge (64 = the benchmark workload)")
+    ap.add_argument("--ne", type=int, default=None,
+                    help="mesh edge (default: 64 for box/cons, 48 for fsi/oseen, 32 for te2d)")
+    ap.add_argument("--oracle-baseline", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--baseline-s", type=float, default=10.0,
+                    help="CPU baseline: each oracle process runs whole solves for at least this long (one at least)")
     ap.add_argument("--no-graphs", action="store_true")
     ap.add_argument("--no-pg", action="store_true", help="oseen workload: R = P^T on the velocity field")
-    ap.add_argument("--workload", default="box", choices=["box", "fsi", "cons", "oseen", "batch", "serve"],
+    ap.add_argument("--workload", default="box", choices=["box", "fsi", "cons", "oseen", "te2d", "batch", "serve"],
                     help="box: the 64^3 three-field system (headline); fsi: the 48^3 split-box saddle; "
                          "cons: the box with 4 Lagrange-multiplier constraints (zero diagonal block); "
                          "oseen: the split box with a non-symmetric Oseen velocity block (Petrov-Galerkin AMG); "
+                         "te2d: the 2-field thermo-elastic 2D system (3,267 dofs at --ne 32); "
                          "batch: 256 independent systems; serve: Poisson request stream")
     ap.add_argument("--simple-pred", default="bgs_amg", choices=["bgs_amg", "amg_bgs"],
                     help="SIMPLE's predictor solver: BGS(AMG) sweep or AMG(BGS) V-cycle")
@@ -633,10 +779,12 @@ def main():
     ap.add_argument("--max-setups", type=int, default=8, help="serve: setups in flight at once")
     ap.add_argument("--serve-sizes", default="16,24,32,48,64")
     args = ap.parse_args()
-    NE = args.ne
+    NE = args.ne if args.ne is not None else DEFAULT_NE.get(args.workload, 64)
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
-    if args.impl == "reference":
+    if args.oracle_baseline:
+        run_oracle_baseline(args)
+    elif args.impl == "reference":
         run_reference(args, rank, world)
     elif args.workload == "batch":
         run_batch(args, rank, world)

@@ -216,6 +216,15 @@ int mfs_matvec(struct mfs_handle *h, const double *x, double *y);
  * device scratch.  Host pointers are rejected (MFS_ERR_INVALID). */
 int mfs_dot(struct mfs_handle *h, const double *x, const double *y, double *out);
 
+/* Measured float64 FMA rate of the current device, *tflops in TFLOP/s
+ * (host).  The paper has no counterpart: it is the denominator of the
+ * roofline of the float64 kernels (the coupled matvec and the Arnoldi
+ * passes of Sec. 3.1's GMRES), which GB300's FP64 pipe bounds.  Launches
+ * independent FMA chains on every SM on `stream` (NULL = legacy default
+ * stream), timed by CUDA events, best of 5 after one warm-up; synchronous.
+ * Errors: MFS_ERR_INVALID for a NULL output, MFS_ERR_CUDA. */
+int mfs_fp64_rate(double *tflops, void *stream);
+
 /* Allocation-free variant of mfs_dot.  The paper has no counterpart: it is
  * for callers that must not call cudaMalloc while they run - a host
  * framework whose caching allocator already holds the device memory, a
@@ -229,11 +238,15 @@ int mfs_dot(struct mfs_handle *h, const double *x, const double *y, double *out)
  * device that loads the library holds it until the process exits.  The
  * call makes no cudaMalloc / cudaFree or other allocating call.  Its first
  * call on a device looks up that array's device address
- * (cudaGetSymbolAddress) with the device current; make that first call
- * before any stream capture.  All calls share the one array: calls that
- * overlap on the GPU (other streams, other host threads) race, so
- * serialise them.  Nothing in the array needs clearing between calls.
- * Errors: MFS_ERR_INVALID for NULL pointers, host vectors, n < 0 or
+ * (cudaGetSymbolAddress) with the device current.  The call synchronises
+ * `stream`, so it cannot be made on a stream that is being captured (it is
+ * refused there).  All calls share the one array: calls that overlap on the
+ * GPU (other streams, other host threads) race, so serialise them.  Nothing
+ * in the array needs clearing between calls.  Its launches are never
+ * counted by the kernel statistics of a handle (mfs_kernel_stats), even
+ * while another thread runs a profiled solve.
+ * Errors: MFS_ERR_INVALID for NULL pointers, host vectors or vectors on
+ * another device than the current one, a capturing stream, n < 0 or
  * n > MFS_DOT_NOALLOC_MAX_N (see mfs_last_error); MFS_ERR_CUDA when a CUDA
  * call fails. */
 #define MFS_DOT_NOALLOC_PARTIALS 1024

@@ -26,6 +26,8 @@ constexpr int64_t kCtaRowsMax = 4096;
 constexpr int64_t kCtaRowBlocks = 128;
 constexpr int kGsCtaThreads = 1024;  // threads of the one-CTA Gauss-Seidel kernel for small levels
 LaunchHook *g_hook = nullptr;
+// > 0 while this thread's launches must bypass the process-wide hook
+thread_local int g_hook_off = 0;
 
 struct HookScope {
   cudaStream_t s;
@@ -37,7 +39,7 @@ struct HookScope {
   bool on = false;
   HookScope(cudaStream_t s_, int c, double b, int sg, int64_t r, double f)
       : s(s_), cls(c), bytes(b), sig(sg), rows(r), flops(f) {
-    if (g_hook) on = g_hook->before(s, cls, sig, rows);
+    if (g_hook && !g_hook_off) on = g_hook->before(s, cls, sig, rows);
   }
   ~HookScope() {
     if (on) g_hook->after(s, cls, bytes, sig, rows, flops);
@@ -798,7 +800,52 @@ inline unsigned ew_grid(int64_t n) {
   return (unsigned)(g > 0 ? g : 1);
 }
 
+// FP64 FMA throughput probe: kFmaChains independent chains a = a * m + c per
+// thread; the sum is stored only when it equals a value it cannot take
+// (m, c are runtime values), so no chain can be dropped by the compiler.
+constexpr int kFmaChains = 8;
+__device__ double g_fp64_sink;
+__global__ void __launch_bounds__(256) k_fp64_rate(int iters, double m, double c) {
+  double a[kFmaChains];
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) a[k] = 1e-3 * threadIdx.x + k;
+  for (int it = 0; it < iters; ++it)
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], m, c);
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kFmaChains; ++k) s += a[k];
+  if (s == -12345.678) g_fp64_sink = s;
+}
+
 }  // namespace
+
+double fp64_rate(cudaStream_t s) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1.0;
+  const int ctas = sms * 8, threads = 256, iters = 4096;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
+  float best = 1e30f;
+  bool ok = true;
+  for (int r = 0; r < 6 && ok; ++r) {
+    ok = cudaEventRecord(e0, s) == cudaSuccess;
+    k_fp64_rate<<<ctas, threads, 0, s>>>(iters, 0.999999, 1e-7);
+    ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+    float ms = 0.f;
+    ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+    if (ok && r > 0 && ms < best) best = ms;  // the first launch is a warm-up
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok || cudaGetLastError() != cudaSuccess) return -1.0;
+  const double flops = 2.0 * kFmaChains * (double)iters * threads * ctas;
+  return flops / (best * 1e-3) / 1e12;
+}
+
+namespace {
 
 #define MFS_BLOCK_DISPATCH(BRV, BCV, CALL)                                      \
   switch (BRV * 16 + BCV) {                                                     \
@@ -822,6 +869,8 @@ inline unsigned ew_grid(int64_t n) {
   }
 
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
+HookBypass::HookBypass() { ++g_hook_off; }
+HookBypass::~HookBypass() { --g_hook_off; }
 
 void init() {
   // once per device and process (concurrent setups must not race on it)

@@ -52,6 +52,14 @@ struct LaunchHook {
   virtual ~LaunchHook() {}
 };
 void set_launch_hook(LaunchHook *h);
+// While one of these lives, launches made by the constructing thread skip
+// the hook (calls that serve no handle must not feed a handle's profile).
+struct HookBypass {
+  HookBypass();
+  ~HookBypass();
+  HookBypass(const HookBypass &) = delete;
+  HookBypass &operator=(const HookBypass &) = delete;
+};
 // one-time device settings (call before any stream capture)
 void init();
 
@@ -136,6 +144,10 @@ void sell_widths(const int32_t *rp, int64_t nbr, int32_t *rl, int32_t *w, cudaSt
 void sell_fill(const int32_t *rp, const int32_t *ci, int nsrc, const double *v0, const double *v1,
                const double *v2, const int *bcs, int br, int64_t nbr, const int32_t *sp, int32_t *col,
                double *v64, float *v32, cudaStream_t s);
+
+// Measured FP64 FMA rate of this device in TFLOP/s (best of 5 timed launches
+// of independent FMA chains on every SM, CUDA events on s); < 0 on error.
+double fp64_rate(cudaStream_t s);
 
 // elementwise helpers
 template <typename T> void fill(T *x, int64_t n, T v, cudaStream_t s);

@@ -50,13 +50,14 @@ int scratch_for_current_device(double **out) {
   return MFS_OK;
 }
 
-bool on_device(const void *p) {
+// device (or managed) memory of device `dev`
+bool on_device(const void *p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
 }  // namespace
@@ -74,8 +75,23 @@ extern "C" int mfs_dot_noalloc(const double *x, const double *y, int64_t n, doub
     *out = 0.0;
     return MFS_OK;
   }
-  if (!on_device(x) || !on_device(y)) {
-    mfs::set_last_error("mfs_dot_noalloc: x and y must be device pointers");
+  // first CUDA call: nothing else may run on a stream under capture
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    mfs::set_last_error("mfs_dot_noalloc: the stream is being captured (the call synchronises it)");
+    return MFS_ERR_INVALID;
+  }
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    mfs::set_last_error("mfs_dot_noalloc: no current CUDA device");
+    return MFS_ERR_CUDA;
+  }
+  // the scratch address is the current device's, so the vectors must live there too
+  if (!on_device(x, dev) || !on_device(y, dev)) {
+    mfs::set_last_error("mfs_dot_noalloc: x and y must be device pointers on the current device");
     return MFS_ERR_INVALID;
   }
   double *scratch = nullptr;
@@ -84,11 +100,15 @@ extern "C" int mfs_dot_noalloc(const double *x, const double *y, int64_t n, doub
     mfs::set_last_error("mfs_dot_noalloc: cannot resolve the scratch array on this device");
     return rc;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   const int nblk = mfs::dev::mdot_blocks(n);
-  if (nblk > kPartials) return MFS_ERR_INVALID;
+  if (nblk > kPartials) {
+    mfs::set_last_error("mfs_dot_noalloc: more reduction blocks than MFS_DOT_NOALLOC_PARTIALS");
+    return MFS_ERR_INVALID;
+  }
   // every partial that the second stage reads is written by the first stage,
-  // so the contents left by the previous call need no clearing
+  // so the contents left by the previous call need no clearing; the launches
+  // bypass the profiling hook of any handle that another thread is solving with
+  mfs::dev::HookBypass bypass;
   mfs::dev::mdot(x, 0, 1, y, n, scratch, nblk, s);
   mfs::dev::reduce_partials(scratch, 1, nblk, scratch + kPartials, s);
   double result = 0.0;

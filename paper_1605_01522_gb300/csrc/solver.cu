@@ -2055,6 +2055,17 @@ int mfs_dot(mfs_handle *h, const double *x, const double *y, double *out) {
   return MFS_OK;
 }
 
+int mfs_fp64_rate(double *tflops, void *stream) {
+  if (!tflops) return fail(MFS_ERR_INVALID, "mfs_fp64_rate: NULL output");
+  const double r = dev::fp64_rate((cudaStream_t)stream);
+  if (!(r > 0.0)) {
+    cudaGetLastError();
+    return fail(MFS_ERR_CUDA, "mfs_fp64_rate: CUDA error");
+  }
+  *tflops = r;
+  return MFS_OK;
+}
+
 int mfs_apply(mfs_handle *h, const double *v, double *z) {
   if (!h || !v || !z || v == z) return fail(MFS_ERR_INVALID, "bad apply arguments");
   return with_io(h, v, z, precond_apply);

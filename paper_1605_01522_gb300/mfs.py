@@ -28,7 +28,7 @@ PRECONDS = {"bgs_amg": BGS_AMG, "simple": SIMPLE, "amg_bgs": AMG_BGS, "amg_simpl
 ORDERS = {"bwd": BWD, "fwd": FWD, "sym": SYM}
 
 # every symbol include/mfs.h declares
-EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_solve_batch", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_ndofs", "mfs_device_bytes",
+EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_solve_batch", "mfs_apply", "mfs_matvec", "mfs_dot", "mfs_dot_noalloc", "mfs_fp64_rate", "mfs_ndofs", "mfs_device_bytes",
            "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
@@ -124,6 +124,8 @@ def load(build_if_missing: bool = True):
     lib.mfs_dot.restype = C.c_int
     lib.mfs_dot_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.POINTER(C.c_double), C.c_void_p]
     lib.mfs_dot_noalloc.restype = C.c_int
+    lib.mfs_fp64_rate.argtypes = [C.POINTER(C.c_double), C.c_void_p]
+    lib.mfs_fp64_rate.restype = C.c_int
     lib.mfs_device_bytes.argtypes = [H, C.c_int]
     lib.mfs_device_bytes.restype = C.c_int64
     lib.mfs_ndofs.argtypes = [H]
@@ -161,10 +163,27 @@ def dot_noalloc(x, y, n=None, stream=None):
     allocation; partial sums in the library's static device array)."""
     lib = load()
     out = C.c_double()
-    n = x.numel() if n is None else n
+    size = lambda a: a.numel() if hasattr(a, "numel") else len(a)
+    n = size(x) if n is None else n
+    if n > min(size(x), size(y)):
+        raise ValueError(f"dot_noalloc: n = {n} exceeds a vector's length ({size(x)}, {size(y)})")
+    if hasattr(x, "device") and hasattr(y, "device"):
+        import torch
+        if x.device != y.device or (x.is_cuda and x.device.index != torch.cuda.current_device()):
+            raise ValueError("dot_noalloc: x and y must be on the current CUDA device")
     rc = lib.mfs_dot_noalloc(_ptr(x), _ptr(y), n, C.byref(out), stream)
     if rc != OK:
         raise MfsError(rc, "mfs_dot_noalloc")
+    return out.value
+
+
+def fp64_rate(stream=None):
+    """Measured float64 FMA rate of the current device in TFLOP/s (mfs_fp64_rate)."""
+    lib = load()
+    out = C.c_double()
+    rc = lib.mfs_fp64_rate(C.byref(out), stream)
+    if rc != OK:
+        raise MfsError(rc, "mfs_fp64_rate")
     return out.value
 
 
