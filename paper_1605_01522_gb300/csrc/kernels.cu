@@ -845,8 +845,6 @@ double fp64_rate(cudaStream_t s) {
   return flops / (best * 1e-3) / 1e12;
 }
 
-namespace {
-
 #define MFS_BLOCK_DISPATCH(BRV, BCV, CALL)                                      \
   switch (BRV * 16 + BCV) {                                                     \
     case 1 * 16 + 1: { constexpr int BR_ = 1, BC_ = 1; CALL; } break;           \
