@@ -192,13 +192,24 @@ int mfs_solve(struct mfs_handle *h, const double *rhs, double *x, double tol, mf
 int mfs_clone(const struct mfs_handle *src, void *stream, struct mfs_handle **out);
 
 /* Solve nsys independent systems, one per handle (distinct handles; clones
- * of one setup allowed), each A_k x_k = rhs_k to tol as mfs_solve does.
- * `nthreads` host threads (<= 0: 16) each drive one handle's FGMRES at a
- * time on that handle's stream, so the systems' kernels overlap on the GPU;
- * every result is bit-for-bit the one mfs_solve gives for that system alone.
- * infos / status (may be NULL) receive per-system results; the return value
- * is MFS_OK or the first failing system's code.  The per-launch profiler is
- * not used in batches. */
+ * of one setup allowed; any sizes, field counts, preconditioners and
+ * precisions), each A_k x_k = rhs_k to tol as mfs_solve does; rhs / x host
+ * or device.  Not in the paper: it batches many of the Sec. 3-4 solves.
+ *  nthreads == 0: fused.  The systems' FGMRES iterations advance together;
+ *    every step of an iteration (each kernel of each system's preconditioner
+ *    application, matvec and Arnoldi pass) runs as ONE launch over all
+ *    systems that take that kernel, driven by per-system argument tables,
+ *    and the steps of an iteration are one CUDA graph replayed once per
+ *    iteration on a library stream; systems that finish stop taking part.
+ *    The graph and tables are built on the first call with a handle list
+ *    and kept for later calls with the same list (until one of its handles
+ *    is freed).
+ *  nthreads > 0: that many host threads each drive one handle's FGMRES at
+ *    a time on the handle's own stream, so the systems' kernels overlap.
+ * Either way every result is bit-for-bit the one mfs_solve gives for that
+ * system alone.  infos / status (may be NULL) receive per-system results;
+ * the return value is MFS_OK or the first failing system's code.  The
+ * per-launch profiler is not used in batches. */
 int mfs_solve_batch(struct mfs_handle *const *hs, int nsys, const double *const *rhs, double *const *x, double tol,
                     mfs_info *infos, int *status, int nthreads);
 

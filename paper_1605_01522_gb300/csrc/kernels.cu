@@ -29,6 +29,11 @@ LaunchHook *g_hook = nullptr;
 // > 0 while this thread's launches must bypass the process-wide hook
 thread_local int g_hook_off = 0;
 
+// While set, this thread's launches are appended here instead of issued.
+thread_local Recorder *g_rec = nullptr;
+// accounting of the launch being issued (HookScope fills it for the recorder)
+thread_local RecOp g_acct;
+
 struct HookScope {
   cudaStream_t s;
   int cls;
@@ -39,12 +44,57 @@ struct HookScope {
   bool on = false;
   HookScope(cudaStream_t s_, int c, double b, int sg, int64_t r, double f)
       : s(s_), cls(c), bytes(b), sig(sg), rows(r), flops(f) {
+    if (g_rec) {
+      g_acct.cls = c;
+      g_acct.sig = sg;
+      g_acct.rows = r;
+      g_acct.bytes = b;
+      g_acct.flops = f;
+      return;
+    }
     if (g_hook && !g_hook_off) on = g_hook->before(s, cls, sig, rows);
   }
   ~HookScope() {
     if (on) g_hook->after(s, cls, bytes, sig, rows, flops);
   }
 };
+
+// Every solve-phase kernel is a traits struct K: K::Args (its arguments),
+// K::run(args, block, blocks) (its body for one block of a grid of `blocks`)
+// and K::kMaxThreads.  k_solo runs it over a normal grid; k_multi runs many
+// independent launches of K (one per system of a batch) as ONE grid: CTA c
+// runs block map[c].bid of the launch whose arguments are tab[map[c].t],
+// unless that launch's system map[c].g is inactive.
+template <class K>
+__global__ void __launch_bounds__(K::kMaxThreads) k_solo(const __grid_constant__ typename K::Args a) {
+  K::run(a, (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <class K>
+__global__ void __launch_bounds__(K::kMaxThreads)
+k_multi(const typename K::Args *__restrict__ tab, const MsBlock *__restrict__ map, const int *__restrict__ active) {
+  const MsBlock m = map[blockIdx.x];
+  if (active != nullptr && active[m.g] == 0) return;
+  K::run(tab[m.t], m.bid, m.nb);
+}
+
+// issue one launch of K, or record it (with the accounting of the enclosing
+// HookScope) when this thread has a recorder
+template <class K>
+void go(unsigned grid, unsigned threads, size_t smem, cudaStream_t s, const typename K::Args &a) {
+  if (g_rec) {
+    RecOp op = g_acct;
+    op.fn = (const void *)&k_multi<K>;
+    op.grid = grid;
+    op.threads = threads;
+    op.smem = smem;
+    op.args.assign((const unsigned char *)&a, (const unsigned char *)&a + sizeof(a));
+    g_rec->ops.push_back(std::move(op));
+    g_acct = RecOp();
+    return;
+  }
+  k_solo<K><<<grid, threads, smem, s>>>(a);
+}
 
 template <typename T> int sparse_sig(const Sell &A) {
   // 3 / 9: SELL-32 with 4 / 8 slots in flight
@@ -195,10 +245,9 @@ __device__ __forceinline__ T pick(const T (&acc)[BR], int r) {
 }
 
 template <int BR, int BC, typename T>
-__global__ void __launch_bounds__(kThreads)
-k_spmv_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-            const T *__restrict__ val, const T *__restrict__ x, T *y, T alpha, T beta, const T *z) {
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void d_spmv_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+            const T *__restrict__ val, const T *__restrict__ x, T *y, T alpha, T beta, const T *z, int bid_, int nb_) {
+  const int64_t row = ((int64_t)bid_ * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= nbr) return;
   T acc[BR];
@@ -209,16 +258,33 @@ k_spmv_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restri
     y[i] = z != nullptr ? alpha * a + beta * z[i] : alpha * a;
   }
 }
+template <int BR, int BC, typename T>
+struct KSpmvWarp {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t nbr;
+    const int32_t *rp;
+    const int32_t *col;
+    const T *val;
+    const T *x;
+    T *y;
+    T alpha;
+    T beta;
+    const T *z;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_spmv_warp<BR, BC, T>(a.nbr, a.rp, a.col, a.val, a.x, a.y, a.alpha, a.beta, a.z, bid, nb);
+  }
+};
 
 // One CTA per block row, for few and long rows (restrictions to small coarse
 // levels): threads stride over the row's blocks, then a fixed butterfly per
 // warp and a fixed-order sum over the warps.
 template <int BR, int BC, typename T>
-__global__ void __launch_bounds__(kThreads)
-k_spmv_cta(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
-           const T *__restrict__ val, const T *__restrict__ x, T *y, T alpha, T beta, const T *z) {
+__device__ __forceinline__ void d_spmv_cta(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+           const T *__restrict__ val, const T *__restrict__ x, T *y, T alpha, T beta, const T *z, int bid_, int nb_) {
   __shared__ T part[kThreads / 32][BR];
-  const int64_t row = blockIdx.x;
+  const int64_t row = bid_;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T acc[BR];
 #pragma unroll
@@ -249,13 +315,30 @@ k_spmv_cta(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restric
     y[i] = z != nullptr ? alpha * a + beta * z[i] : alpha * a;
   }
 }
+template <int BR, int BC, typename T>
+struct KSpmvCta {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t nbr;
+    const int32_t *rp;
+    const int32_t *col;
+    const T *val;
+    const T *x;
+    T *y;
+    T alpha;
+    T beta;
+    const T *z;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_spmv_cta<BR, BC, T>(a.nbr, a.rp, a.col, a.val, a.x, a.y, a.alpha, a.beta, a.z, bid, nb);
+  }
+};
 
 template <int BR, typename T>
-__global__ void __launch_bounds__(kThreads)
-k_smooth_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+__device__ __forceinline__ void d_smooth_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
               const T *__restrict__ val, const T *__restrict__ dinv, const T *__restrict__ b,
-              const T *__restrict__ x, T *__restrict__ xout, T *__restrict__ d, T c1, T c2) {
-  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+              const T *__restrict__ x, T *__restrict__ xout, T *__restrict__ d, T c1, T c2, int bid_, int nb_) {
+  const int64_t row = ((int64_t)bid_ * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= nbr) return;
   T acc[BR];
@@ -268,13 +351,32 @@ k_smooth_warp(int64_t nbr, const int32_t *__restrict__ rp, const int32_t *__rest
     xout[i] = x[i] + dd;
   }
 }
+template <int BR, typename T>
+struct KSmoothWarp {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t nbr;
+    const int32_t *rp;
+    const int32_t *col;
+    const T *val;
+    const T *dinv;
+    const T *b;
+    const T *x;
+    T *xout;
+    T *d;
+    T c1;
+    T c2;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_smooth_warp<BR, T>(a.nbr, a.rp, a.col, a.val, a.dinv, a.b, a.x, a.xout, a.d, a.c1, a.c2, bid, nb);
+  }
+};
 
 template <int BR, int BC, typename T, int U>
-__global__ void __launch_bounds__(kThreads)
-k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+__device__ __forceinline__ void d_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
        const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ x, T *y,
-       T alpha, T beta, const T *z) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+       T alpha, T beta, const T *z, int bid_, int nb_) {
+  const int64_t row = (int64_t)bid_ * blockDim.x + threadIdx.x;
   if (row >= nbr) return;
   T acc[BR];
   sell_row<BR, BC, T, U>(sp, rl, col, val, x, row, acc);
@@ -291,6 +393,25 @@ k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ 
     for (int r = 0; r < BR; ++r) yp[r] = alpha * acc[r];
   }
 }
+template <int BR, int BC, typename T, int U>
+struct KSpmvSell {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t nbr;
+    const int32_t *sp;
+    const int32_t *rl;
+    const int32_t *col;
+    const T *val;
+    const T *x;
+    T *y;
+    T alpha;
+    T beta;
+    const T *z;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_spmv<BR, BC, T, U>(a.nbr, a.sp, a.rl, a.col, a.val, a.x, a.y, a.alpha, a.beta, a.z, bid, nb);
+  }
+};
 
 // Merged coupled rows in float64, H threads per block row.  H = 1: one
 // thread per row, 64-thread CTAs (two slices).  H > 1: a CTA of 32 H threads
@@ -299,13 +420,12 @@ k_spmv(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ 
 // shared memory.  More threads per row keep more FP64 FMAs in flight (the
 // FP64 pipe bounds this kernel on GB300).
 template <int BR, int B0, int B1, int B2, int H>
-__global__ void __launch_bounds__(H == 1 ? 64 : 32 * H)
-k_spmv_rows(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+__device__ __forceinline__ void d_spmv_rows(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
             const int32_t *__restrict__ col, const double *__restrict__ val, const double *__restrict__ x0,
-            const double *__restrict__ x1, const double *__restrict__ x2, double *__restrict__ y) {
+            const double *__restrict__ x1, const double *__restrict__ x2, double *__restrict__ y, int bid_, int nb_) {
   constexpr int BCT = B0 + B1 + B2;
   const int lane = threadIdx.x & 31, h = H == 1 ? 0 : threadIdx.x >> 5;
-  const int64_t row = H == 1 ? (int64_t)blockIdx.x * 64 + threadIdx.x : (int64_t)blockIdx.x * 32 + lane;
+  const int64_t row = H == 1 ? (int64_t)bid_ * 64 + threadIdx.x : (int64_t)bid_ * 32 + lane;
   const bool active = row < nbr;
   double acc[BR];
 #pragma unroll
@@ -352,14 +472,31 @@ k_spmv_rows(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restri
       }
   }
 }
+template <int BR, int B0, int B1, int B2, int H>
+struct KSpmvRows {
+  static constexpr int kMaxThreads = (H == 1 ? 64 : 32 * H);
+  struct Args {
+    int64_t nbr;
+    const int32_t *sp;
+    const int32_t *rl;
+    const int32_t *col;
+    const double *val;
+    const double *x0;
+    const double *x1;
+    const double *x2;
+    double *y;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_spmv_rows<BR, B0, B1, B2, H>(a.nbr, a.sp, a.rl, a.col, a.val, a.x0, a.x1, a.x2, a.y, bid, nb);
+  }
+};
 
 template <int BR, typename T, int U>
-__global__ void __launch_bounds__(kThreads)
-k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
+__device__ __forceinline__ void d_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict__ rl,
          const int32_t *__restrict__ col, const T *__restrict__ val, const T *__restrict__ dinv,
          const T *__restrict__ b, const T *__restrict__ x, T *__restrict__ xout, T *__restrict__ d,
-         T c1, T c2) {
-  const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+         T c1, T c2, int bid_, int nb_) {
+  const int64_t row = (int64_t)bid_ * blockDim.x + threadIdx.x;
   if (row >= nbr) return;
   T acc[BR];
   sell_row<BR, BR, T, U>(sp, rl, col, val, x, row, acc);
@@ -372,6 +509,27 @@ k_smooth(int64_t nbr, const int32_t *__restrict__ sp, const int32_t *__restrict_
     xout[i] = x[i] + dd;
   }
 }
+template <int BR, typename T, int U>
+struct KSmoothSell {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t nbr;
+    const int32_t *sp;
+    const int32_t *rl;
+    const int32_t *col;
+    const T *val;
+    const T *dinv;
+    const T *b;
+    const T *x;
+    T *xout;
+    T *d;
+    T c1;
+    T c2;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_smooth<BR, T, U>(a.nbr, a.sp, a.rl, a.col, a.val, a.dinv, a.b, a.x, a.xout, a.d, a.c1, a.c2, bid, nb);
+  }
+};
 
 // G lanes per row of a plain BSR matrix: the lanes of a group stride over the
 // row's blocks, then a fixed xor-butterfly inside the group sums them.  x goes
@@ -405,11 +563,10 @@ __device__ __forceinline__ void gs_group_row(const int32_t *__restrict__ rp, con
 
 // One colour: reordered rows [r0, r1), G lanes per row.
 template <int BR, typename T, int G>
-__global__ void __launch_bounds__(kThreads)
-k_gs_color(int64_t r0, int64_t r1, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+__device__ __forceinline__ void d_gs_color(int64_t r0, int64_t r1, const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
            const T *__restrict__ val, const int32_t *__restrict__ rowidx, const T *__restrict__ dblk,
-           const T *__restrict__ b, T *x, T omega, int backward) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+           const T *__restrict__ b, T *x, T omega, int backward, int bid_, int nb_) {
+  const int64_t t = (int64_t)bid_ * blockDim.x + threadIdx.x;
   const int64_t row = r0 + t / G;
   const int gl = (int)(t % G);
   const bool active = row < r1;
@@ -417,6 +574,26 @@ k_gs_color(int64_t r0, int64_t r1, const int32_t *__restrict__ rp, const int32_t
   gs_group_row<BR, G, T>(rp, col, val, x, row, active, gl, acc);
   if (active && gl == 0) gs_update<BR, T>(acc, rowidx[row], dblk, b, x, omega, backward != 0);
 }
+template <int BR, typename T, int G>
+struct KGsColor {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t r0;
+    int64_t r1;
+    const int32_t *rp;
+    const int32_t *col;
+    const T *val;
+    const int32_t *rowidx;
+    const T *dblk;
+    const T *b;
+    T *x;
+    T omega;
+    int backward;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_gs_color<BR, T, G>(a.r0, a.r1, a.rp, a.col, a.val, a.rowidx, a.dblk, a.b, a.x, a.omega, a.backward, bid, nb);
+  }
+};
 
 // All colours and sweeps of a small level in one CTA: x lives in shared
 // memory for the whole launch (loaded first, written back last), so the
@@ -424,11 +601,10 @@ k_gs_color(int64_t r0, int64_t r1, const int32_t *__restrict__ rp, const int32_t
 // groups of G lanes stride over the rows of a colour.  Every thread reaches
 // every barrier (uniform loops, no early exit).
 template <int BR, typename T, int G>
-__global__ void __launch_bounds__(kGsCtaThreads)
-k_gs_small(int nc, int64_t n, const int32_t *__restrict__ coff, const int32_t *__restrict__ rp,
+__device__ __forceinline__ void d_gs_small(int nc, int64_t n, const int32_t *__restrict__ coff, const int32_t *__restrict__ rp,
            const int32_t *__restrict__ col, const T *__restrict__ val, const int32_t *__restrict__ rowidx,
            const T *__restrict__ dblk, const T *__restrict__ b, T *__restrict__ x, T omega, int sweeps,
-           int backward) {
+           int backward, int bid_, int nb_) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
   const int tid = threadIdx.x;
@@ -465,16 +641,37 @@ k_gs_small(int nc, int64_t n, const int32_t *__restrict__ coff, const int32_t *_
     }
   for (int64_t k = tid; k < n * BR; k += blockDim.x) x[k] = xs[k];
 }
+template <int BR, typename T, int G>
+struct KGsSmall {
+  static constexpr int kMaxThreads = kGsCtaThreads;
+  struct Args {
+    int nc;
+    int64_t n;
+    const int32_t *coff;
+    const int32_t *rp;
+    const int32_t *col;
+    const T *val;
+    const int32_t *rowidx;
+    const T *dblk;
+    const T *b;
+    T *x;
+    T omega;
+    int sweeps;
+    int backward;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_gs_small<BR, T, G>(a.nc, a.n, a.coff, a.rp, a.col, a.val, a.rowidx, a.dblk, a.b, a.x, a.omega, a.sweeps, a.backward, bid, nb);
+  }
+};
 
 // x = inv b for the explicit inverse of a coarsest matrix (row-major, float64):
 // b staged in shared memory as float64, one warp per row, fixed butterfly sum.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_inv_apply(int n, const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x) {
+__device__ __forceinline__ void d_inv_apply(int n, const double *__restrict__ inv, const T *__restrict__ b, T *__restrict__ x, int bid_, int nb_) {
   extern __shared__ double bs[];
   for (int j = threadIdx.x; j < n; j += blockDim.x) bs[j] = (double)b[j];
   __syncthreads();
-  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int row = bid_ * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const double *a = inv + (int64_t)row * n;
@@ -484,16 +681,44 @@ k_inv_apply(int n, const double *__restrict__ inv, const T *__restrict__ b, T *_
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) x[row] = (T)acc;
 }
+template <typename T>
+struct KInvApply {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int n;
+    const double *inv;
+    const T *b;
+    T *x;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_inv_apply<T>(a.n, a.inv, a.b, a.x, bid, nb);
+  }
+};
 
 template <typename T>
-__global__ void k_smooth_first(int64_t n, const T *__restrict__ dinv, const T *__restrict__ b,
-                               T *__restrict__ x, T *__restrict__ d, T c2) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+__device__ __forceinline__ void d_smooth_first(int64_t n, const T *__restrict__ dinv, const T *__restrict__ b,
+                               T *__restrict__ x, T *__restrict__ d, T c2, int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x) {
     const T dd = c2 * dinv[i] * b[i];
     d[i] = dd;
     x[i] = dd;
   }
 }
+template <typename T>
+struct KSmoothFirst {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    int64_t n;
+    const T *dinv;
+    const T *b;
+    T *x;
+    T *d;
+    T c2;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_smooth_first<T>(a.n, a.dinv, a.b, a.x, a.d, a.c2, bid, nb);
+  }
+};
 
 // Dense LU solve in one CTA, blocked by 32: one warp solves each 32 x 32
 // diagonal block with shuffles, then all warps update the rows below (above)
@@ -501,9 +726,8 @@ __global__ void k_smooth_first(int64_t n, const T *__restrict__ dinv, const T *_
 // factors when they fit (staged == 1), which keeps the warp's sequential
 // steps off global-memory latency.
 template <typename T>
-__global__ void __launch_bounds__(512)
-k_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ perm,
-           const T *__restrict__ b, T *__restrict__ x, int staged) {
+__device__ __forceinline__ void d_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ perm,
+           const T *__restrict__ b, T *__restrict__ x, int staged, int bid_, int nb_) {
   extern __shared__ double sm[];
   double *y = sm;
   const int tid = threadIdx.x, nt = blockDim.x, warp = tid >> 5, lane = tid & 31;
@@ -574,30 +798,95 @@ k_lu_solve(int n, const double *__restrict__ lu_g, const int32_t *__restrict__ p
   }
   for (int i = tid; i < n; i += nt) x[i] = (T)y[i];
 }
+template <typename T>
+struct KLuSolve {
+  static constexpr int kMaxThreads = 512;
+  struct Args {
+    int n;
+    const double *lu_g;
+    const int32_t *perm;
+    const T *b;
+    T *x;
+    int staged;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_lu_solve<T>(a.n, a.lu_g, a.perm, a.b, a.x, a.staged, bid, nb);
+  }
+};
 
 template <typename T>
-__global__ void k_fill(T *x, int64_t n, T v) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__device__ __forceinline__ void d_fill(T *x, int64_t n, T v, int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x)
     x[i] = v;
 }
+template <typename T>
+struct KFill {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    T *x;
+    int64_t n;
+    T v;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_fill<T>(a.x, a.n, a.v, bid, nb);
+  }
+};
 
 template <typename T>
-__global__ void k_axpy_diag(T *__restrict__ x, const T *__restrict__ dinv, const T *__restrict__ t, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__device__ __forceinline__ void d_axpy_diag(T *__restrict__ x, const T *__restrict__ dinv, const T *__restrict__ t, int64_t n, int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x)
     x[i] -= dinv[i] * t[i];
 }
+template <typename T>
+struct KAxpyDiag {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    T *x;
+    const T *dinv;
+    const T *t;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_axpy_diag<T>(a.x, a.dinv, a.t, a.n, bid, nb);
+  }
+};
 
 template <typename T>
-__global__ void k_axpy(T *__restrict__ y, const T *__restrict__ x, T a, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__device__ __forceinline__ void d_axpy(T *__restrict__ y, const T *__restrict__ x, T a, int64_t n, int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x)
     y[i] += a * x[i];
 }
+template <typename T>
+struct KAxpy {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    T *y;
+    const T *x;
+    T a;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_axpy<T>(a.y, a.x, a.a, a.n, bid, nb);
+  }
+};
 
 template <typename TI, typename TO>
-__global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__device__ __forceinline__ void d_convert(const TI *__restrict__ in, TO *__restrict__ out, int64_t n, int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x)
     out[i] = (TO)in[i];
 }
+template <typename TI, typename TO>
+struct KConvert {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const TI *in;
+    TO *out;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_convert<TI, TO>(a.in, a.out, a.n, bid, nb);
+  }
+};
 
 __global__ void k_sell_widths(const int32_t *__restrict__ rp, int64_t nbr, int32_t *__restrict__ rl,
                               int32_t *__restrict__ w) {
@@ -641,10 +930,48 @@ __global__ void k_sell_fill(const int32_t *__restrict__ rp, const int32_t *__res
   }
 }
 
-__global__ void k_scale(const double *x, double a, double *y, int64_t n) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+__device__ __forceinline__ void d_scale(const double *x, double a, double *y, int64_t n, int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x)
     y[i] = a * x[i];
 }
+struct KScale {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const double *x;
+    double a;
+    double *y;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_scale(a.x, a.a, a.y, a.n, bid, nb);
+  }
+};
+
+// v = a v (in place) and out = v converted to TO: the normalisation of a new
+// Krylov vector fused with the copy the preconditioner reads
+template <typename TO>
+__device__ __forceinline__ void d_scale_convert(double *__restrict__ v, double a, TO *__restrict__ out, int64_t n,
+                                                int bid_, int nb_) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x) {
+    const double t = a * v[i];
+    v[i] = t;
+    out[i] = (TO)t;
+  }
+}
+template <typename TO>
+struct KScaleConvert {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    double *v;
+    double a;
+    TO *out;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_scale_convert<TO>(a.v, a.a, a.out, a.n, bid, nb);
+  }
+};
+
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
 #pragma unroll
@@ -682,7 +1009,8 @@ __device__ __forceinline__ void tile_dots(const double *__restrict__ V, int64_t 
   }
 }
 
-__device__ __forceinline__ void store_dots(int k, int nblk, double (&acc)[kMaxQ / 8], double *__restrict__ partial) {
+__device__ __forceinline__ void store_dots(int k, int nblk, double (&acc)[kMaxQ / 8], double *__restrict__ partial,
+                                           int bid) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int m = 0; m < kMaxQ / 8; ++m) {
@@ -691,18 +1019,17 @@ __device__ __forceinline__ void store_dots(int k, int nblk, double (&acc)[kMaxQ 
       double v = acc[m];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) partial[(int64_t)q * nblk + blockIdx.x] = v;
+      if (lane == 0) partial[(int64_t)q * nblk + bid] = v;
     }
   }
 }
 
 // h_q = V_q . w for q < k (w may be one of the rows of V)
-__global__ void __launch_bounds__(kThreads)
-k_mdot(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ w, int64_t n,
-       double *__restrict__ partial, int nblk) {
+__device__ __forceinline__ void d_mdot(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ w, int64_t n,
+       double *__restrict__ partial, int nblk, int bid_, int nb_) {
   __shared__ double ws[kTile];
   const int64_t chunk = (n + nblk - 1) / nblk;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t lo = (int64_t)bid_ * chunk;
   const int64_t hi = min(n, lo + chunk);
   double acc[kMaxQ / 8];
 #pragma unroll
@@ -714,19 +1041,33 @@ k_mdot(const double *__restrict__ V, int64_t ldv, int k, const double *__restric
     tile_dots(V, ldv, k, t0, cnt, ws, acc);
     __syncthreads();
   }
-  store_dots(k, nblk, acc, partial);
+  store_dots(k, nblk, acc, partial, bid_);
 }
+struct KMdot {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const double *V;
+    int64_t ldv;
+    int k;
+    const double *w;
+    int64_t n;
+    double *partial;
+    int nblk;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_mdot(a.V, a.ldv, a.k, a.w, a.n, a.partial, a.nblk, bid, nb);
+  }
+};
 
 // w <- w - sum_q V_q h_q, then partial dots V_q . w_new (CGS2 second pass)
-__global__ void __launch_bounds__(kThreads)
-k_cgs_fused(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ h, double *__restrict__ w,
-            int64_t n, double *__restrict__ partial, int nblk) {
+__device__ __forceinline__ void d_cgs_fused(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ h, double *__restrict__ w,
+            int64_t n, double *__restrict__ partial, int nblk, int bid_, int nb_) {
   __shared__ double ws[kTile];
   __shared__ double hs[kMaxQ];
   for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
   __syncthreads();
   const int64_t chunk = (n + nblk - 1) / nblk;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t lo = (int64_t)bid_ * chunk;
   const int64_t hi = min(n, lo + chunk);
   double acc[kMaxQ / 8];
 #pragma unroll
@@ -746,27 +1087,55 @@ k_cgs_fused(const double *__restrict__ V, int64_t ldv, int k, const double *__re
     tile_dots(V, ldv, k, t0, cnt, ws, acc);
     __syncthreads();
   }
-  store_dots(k, nblk, acc, partial);
+  store_dots(k, nblk, acc, partial, bid_);
 }
+struct KCgsFused {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const double *V;
+    int64_t ldv;
+    int k;
+    const double *h;
+    double *w;
+    int64_t n;
+    double *partial;
+    int nblk;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_cgs_fused(a.V, a.ldv, a.k, a.h, a.w, a.n, a.partial, a.nblk, bid, nb);
+  }
+};
 
-__global__ void k_reduce_partials(const double *__restrict__ partial, int nblk, double *__restrict__ out) {
+__device__ __forceinline__ void d_reduce_partials(const double *__restrict__ partial, int k, int nblk, double *__restrict__ out, int bid_, int nb_) {
   __shared__ double sh[32];
-  const double *p = partial + (int64_t)blockIdx.x * nblk;
+  if (bid_ >= k) return;
+  const double *p = partial + (int64_t)bid_ * nblk;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nblk; i += blockDim.x) acc += p[i];
   const double s = block_sum(acc, sh);
-  if (threadIdx.x == 0) out[blockIdx.x] = s;
+  if (threadIdx.x == 0) out[bid_] = s;
 }
+struct KReducePartials {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const double *partial;
+    int k;
+    int nblk;
+    double *out;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_reduce_partials(a.partial, a.k, a.nblk, a.out, bid, nb);
+  }
+};
 
-__global__ void __launch_bounds__(kThreads)
-k_cgs_update(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ h,
-             double *__restrict__ w, int64_t n, double *__restrict__ partial, int nblk) {
+__device__ __forceinline__ void d_cgs_update(const double *__restrict__ V, int64_t ldv, int k, const double *__restrict__ h,
+             double *__restrict__ w, int64_t n, double *__restrict__ partial, int nblk, int bid_, int nb_) {
   __shared__ double hs[64];
   __shared__ double sh[32];
   for (int q = threadIdx.x; q < k; q += blockDim.x) hs[q] = h[q];
   __syncthreads();
   const int64_t chunk = (n + nblk - 1) / nblk;
-  const int64_t lo = (int64_t)blockIdx.x * chunk;
+  const int64_t lo = (int64_t)bid_ * chunk;
   const int64_t hi = min(n, lo + chunk);
   double nrm = 0.0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
@@ -778,21 +1147,51 @@ k_cgs_update(const double *__restrict__ V, int64_t ldv, int k, const double *__r
   }
   if (partial != nullptr) {
     const double t = block_sum(nrm, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    if (threadIdx.x == 0) partial[bid_] = t;
   }
 }
+struct KCgsUpdate {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const double *V;
+    int64_t ldv;
+    int k;
+    const double *h;
+    double *w;
+    int64_t n;
+    double *partial;
+    int nblk;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_cgs_update(a.V, a.ldv, a.k, a.h, a.w, a.n, a.partial, a.nblk, bid, nb);
+  }
+};
 
-__global__ void k_gemv_add(const double *__restrict__ Z, int64_t ldz, int k, const double *__restrict__ y,
-                           double *__restrict__ x, int64_t n) {
+__device__ __forceinline__ void d_gemv_add(const double *__restrict__ Z, int64_t ldz, int k, const double *__restrict__ y,
+                           double *__restrict__ x, int64_t n, int bid_, int nb_) {
   __shared__ double ys[64];
   for (int q = threadIdx.x; q < k; q += blockDim.x) ys[q] = y[q];
   __syncthreads();
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x) {
     double s = 0.0;
     for (int q = 0; q < k; ++q) s += Z[(int64_t)q * ldz + i] * ys[q];
     x[i] += s;
   }
 }
+struct KGemvAdd {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    const double *Z;
+    int64_t ldz;
+    int k;
+    const double *y;
+    double *x;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_gemv_add(a.Z, a.ldz, a.k, a.y, a.x, a.n, bid, nb);
+  }
+};
 
 inline unsigned ew_grid(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
@@ -867,6 +1266,13 @@ double fp64_rate(cudaStream_t s) {
   }
 
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
+void set_recorder(Recorder *r) { g_rec = r; }
+
+cudaError_t launch_multi(const RecOp &op, unsigned grid, size_t smem, const void *tab, const MsBlock *map,
+                         const int *active, cudaStream_t s) {
+  void *args[3] = {(void *)&tab, (void *)&map, (void *)&active};
+  return cudaLaunchKernel(op.fn, dim3(grid), dim3(op.threads), args, smem, s);
+}
 HookBypass::HookBypass() { ++g_hook_off; }
 HookBypass::~HookBypass() { --g_hook_off; }
 
@@ -878,8 +1284,10 @@ void init() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
   std::lock_guard<std::mutex> lock(mu);
   if (done[dev]) return;
-  cudaFuncSetAttribute(k_lu_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-  cudaFuncSetAttribute(k_lu_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_solo<KLuSolve<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_solo<KLuSolve<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_multi<KLuSolve<float>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_multi<KLuSolve<double>>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   done[dev] = true;
 }
 
@@ -894,27 +1302,27 @@ void spmv(const Sell &A, const T *x, T *y, T alpha, T beta, const T *z, cudaStre
   if (A.kind == 1) {
     if (cta) {
       MFS_BLOCK_DISPATCH(A.br, A.bc,
-                         (k_spmv_cta<BR_, BC_, T><<<(unsigned)A.nbr, kThreads, 0, s>>>(
-                             A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
+                         (go<KSpmvCta<BR_, BC_, T>>((unsigned)A.nbr, kThreads, 0, s, {
+                             A.nbr, A.sp, A.col, v, x, y, alpha, beta, z})));
     } else {
       MFS_BLOCK_DISPATCH(A.br, A.bc,
-                         (k_spmv_warp<BR_, BC_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
-                             A.nbr, A.sp, A.col, v, x, y, alpha, beta, z)));
+                         (go<KSpmvWarp<BR_, BC_, T>>(grid_for(A.nbr * 32), kThreads, 0, s, {
+                             A.nbr, A.sp, A.col, v, x, y, alpha, beta, z})));
     }
     return;
   }
   if (A.unroll == 4) {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
-                       (k_spmv<BR_, BC_, T, 4><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+                       (go<KSpmvSell<BR_, BC_, T, 4>>(grid_for(A.nbr, kSellThreads), kSellThreads, 0, s, {
+                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z})));
   } else if (A.unroll == 8) {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
-                       (k_spmv<BR_, BC_, T, 8><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+                       (go<KSpmvSell<BR_, BC_, T, 8>>(grid_for(A.nbr, kSellThreads), kSellThreads, 0, s, {
+                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z})));
   } else {
     MFS_BLOCK_DISPATCH(A.br, A.bc,
-                       (k_spmv<BR_, BC_, T, 2><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z)));
+                       (go<KSpmvSell<BR_, BC_, T, 2>>(grid_for(A.nbr, kSellThreads), kSellThreads, 0, s, {
+                           A.nbr, A.sp, A.rl, A.col, v, x, y, alpha, beta, z})));
   }
 }
 
@@ -956,14 +1364,14 @@ void spmv_rows(const RowMerged &R, const double *x, double *y, cudaStream_t s) {
   const int b3[3] = {R.b[0], R.b[1], R.nb > 2 ? R.b[2] : 0};
   const unsigned grid = (unsigned)A.nslices;  // H > 1: one slice per CTA
   if (R.split == 4) {
-    MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2, 4><<<grid, 128, 0, s>>>(
-                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+    MFS_ROWS_DISPATCH(A.br, b3, (go<KSpmvRows<R_, X0, X1, X2, 4>>(grid, 128, 0, s, {
+                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y})));
   } else if (R.split == 2) {
-    MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2, 2><<<grid, 64, 0, s>>>(
-                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+    MFS_ROWS_DISPATCH(A.br, b3, (go<KSpmvRows<R_, X0, X1, X2, 2>>(grid, 64, 0, s, {
+                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y})));
   } else {
-    MFS_ROWS_DISPATCH(A.br, b3, (k_spmv_rows<R_, X0, X1, X2, 1><<<grid_for(A.nbr, 64), 64, 0, s>>>(
-                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y)));
+    MFS_ROWS_DISPATCH(A.br, b3, (go<KSpmvRows<R_, X0, X1, X2, 1>>(grid_for(A.nbr, 64), 64, 0, s, {
+                                    A.nbr, A.sp, A.rl, A.col, A.v64, x0, x1, x2, y})));
   }
 }
 
@@ -975,19 +1383,19 @@ void smooth_step(const Sell &A, const T *dinv, const T *b, const T *x, T *xout, 
   HookScope hs(s, K_SMOOTH, matrix_bytes<T>(A) + (double)sizeof(T) * (A.ncols() + 5.0 * A.nrows()),
                sparse_sig<T>(A), A.nbr, 2.0 * A.nnzb * A.br * A.bc + 6.0 * A.nrows());
   if (A.kind == 1) {
-    MFS_SQUARE_DISPATCH(A.br, (k_smooth_warp<BR_, T><<<grid_for(A.nbr * 32), kThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.col, v, dinv, b, x, xout, d, c1, c2)));
+    MFS_SQUARE_DISPATCH(A.br, (go<KSmoothWarp<BR_, T>>(grid_for(A.nbr * 32), kThreads, 0, s, {
+                                  A.nbr, A.sp, A.col, v, dinv, b, x, xout, d, c1, c2})));
     return;
   }
   if (A.unroll == 4) {
-    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 4><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+    MFS_SQUARE_DISPATCH(A.br, (go<KSmoothSell<BR_, T, 4>>(grid_for(A.nbr, kSellThreads), kSellThreads, 0, s, {
+                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2})));
   } else if (A.unroll == 8) {
-    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 8><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+    MFS_SQUARE_DISPATCH(A.br, (go<KSmoothSell<BR_, T, 8>>(grid_for(A.nbr, kSellThreads), kSellThreads, 0, s, {
+                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2})));
   } else {
-    MFS_SQUARE_DISPATCH(A.br, (k_smooth<BR_, T, 2><<<grid_for(A.nbr, kSellThreads), kSellThreads, 0, s>>>(
-                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2)));
+    MFS_SQUARE_DISPATCH(A.br, (go<KSmoothSell<BR_, T, 2>>(grid_for(A.nbr, kSellThreads), kSellThreads, 0, s, {
+                                  A.nbr, A.sp, A.rl, A.col, v, dinv, b, x, xout, d, c1, c2})));
   }
 }
 
@@ -995,7 +1403,7 @@ template <typename T>
 void smooth_first(int64_t n, const T *dinv, const T *b, T *x, T *d, T c2, cudaStream_t s) {
   if (n == 0) return;
   HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 1, n, 2.0 * n);
-  k_smooth_first<T><<<ew_grid(n), kThreads, 0, s>>>(n, dinv, b, x, d, c2);
+  go<KSmoothFirst<T>>(ew_grid(n), kThreads, 0, s, {n, dinv, b, x, d, c2});
 }
 
 #define MFS_GS_G_DISPATCH(GV, CALL)                              \
@@ -1025,8 +1433,8 @@ void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int s
                      (double)g.cnnzb[c] * (A.br * A.bc * sizeof(T) + sizeof(int32_t)) +
                          (double)sizeof(T) * (g.cnnzb[c] * A.bc + (A.br + 2.0) * A.br * nr) + 8.0 * nr,
                      sig, nr, 2.0 * g.cnnzb[c] * A.br * A.bc + 2.0 * A.br * A.br * nr);
-        MFS_GS_G_DISPATCH(g.G, MFS_SQUARE_DISPATCH(A.br, (k_gs_color<BR_, T, G_><<<grid_for(nr * G_), kThreads, 0, s>>>(
-                                                             r0, r1, A.sp, A.col, v, g.rowidx, dblk, b, x, omega, bw))));
+        MFS_GS_G_DISPATCH(g.G, MFS_SQUARE_DISPATCH(A.br, (go<KGsColor<BR_, T, G_>>(grid_for(nr * G_), kThreads, 0, s, {
+                                                             r0, r1, A.sp, A.col, v, g.rowidx, dblk, b, x, omega, bw}))));
       }
     return;
   }
@@ -1036,9 +1444,9 @@ void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int s
                sig, A.nbr, sweeps * (2.0 * A.nnzb * A.br * A.bc + 2.0 * A.br * A.nrows()));
   const int nc = g.ncolors();
   const size_t shm = (size_t)A.nrows() * sizeof(T);
-  MFS_GS_G_DISPATCH(g.G, MFS_SQUARE_DISPATCH(A.br, (k_gs_small<BR_, T, G_><<<1, kGsCtaThreads, shm, s>>>(
+  MFS_GS_G_DISPATCH(g.G, MFS_SQUARE_DISPATCH(A.br, (go<KGsSmall<BR_, T, G_>>(1, kGsCtaThreads, shm, s, {
                                                        nc, A.nbr, g.coff, A.sp, A.col, v, g.rowidx, dblk, b, x,
-                                                       omega, sweeps, bw))));
+                                                       omega, sweeps, bw}))));
 }
 
 template <typename T>
@@ -1047,8 +1455,8 @@ void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   if (lu.inv) {
     HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + 2.0 * sizeof(T) * lu.n, 2, lu.n, 2.0 * lu.n * (double)lu.n);
     constexpr int kRowsPerCta = kThreads / 32;
-    k_inv_apply<T><<<(unsigned)((lu.n + kRowsPerCta - 1) / kRowsPerCta), kThreads, (size_t)lu.n * sizeof(double), s>>>(
-        lu.n, lu.inv, b, x);
+    go<KInvApply<T>>((unsigned)((lu.n + kRowsPerCta - 1) / kRowsPerCta), kThreads, (size_t)lu.n * sizeof(double), s, {
+        lu.n, lu.inv, b, x});
     return;
   }
   HookScope hs(s, K_COARSE, 8.0 * lu.n * (double)lu.n + (4.0 + 2 * sizeof(T)) * lu.n, 1, lu.n,
@@ -1057,23 +1465,23 @@ void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   const int staged = (size_t)lu.n * (lu.n + 1) * sizeof(double) <= 200 * 1024 ? 1 : 0;
   const size_t smem = (size_t)lu.n * (staged ? lu.n + 1 : 1) * sizeof(double);
   const int threads = lu.n <= 64 ? 256 : 512;
-  k_lu_solve<T><<<1, threads, smem, s>>>(lu.n, lu.lu, lu.perm, b, x, staged);
+  go<KLuSolve<T>>(1, threads, smem, s, {lu.n, lu.lu, lu.perm, b, x, staged});
 }
 
 template <typename T>
 void fill(T *x, int64_t n, T v, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, (double)n * sizeof(T), 2, n, 0.0);
-  if (n) k_fill<T><<<ew_grid(n), kThreads, 0, s>>>(x, n, v);
+  if (n) go<KFill<T>>(ew_grid(n), kThreads, 0, s, {x, n, v});
 }
 template <typename T>
 void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, 4.0 * n * sizeof(T), 3, n, 2.0 * n);
-  if (n) k_axpy_diag<T><<<ew_grid(n), kThreads, 0, s>>>(x, dinv, t, n);
+  if (n) go<KAxpyDiag<T>>(ew_grid(n), kThreads, 0, s, {x, dinv, t, n});
 }
 template <typename T>
 void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, 3.0 * n * sizeof(T), 4, n, 2.0 * n);
-  if (n) k_axpy<T><<<ew_grid(n), kThreads, 0, s>>>(y, x, a, n);
+  if (n) go<KAxpy<T>>(ew_grid(n), kThreads, 0, s, {y, x, a, n});
 }
 void sell_widths(const int32_t *rp, int64_t nbr, int32_t *rl, int32_t *w, cudaStream_t s) {
   if (nbr) k_sell_widths<<<grid_for(nbr), kThreads, 0, s>>>(rp, nbr, rl, w);
@@ -1090,11 +1498,19 @@ void sell_fill(const int32_t *rp, const int32_t *ci, int nsrc, const double *v0,
 template <typename TI, typename TO>
 void convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, (double)n * (sizeof(TI) + sizeof(TO)), 5, n, 0.0);
-  if (n) k_convert<TI, TO><<<ew_grid(n), kThreads, 0, s>>>(in, out, n);
+  if (n) go<KConvert<TI, TO>>(ew_grid(n), kThreads, 0, s, {in, out, n});
 }
+template <typename TO>
+void scale_convert(double *v, double a, TO *out, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, (16.0 + sizeof(TO)) * n, 7, n, (double)n);
+  if (n) go<KScaleConvert<TO>>(ew_grid(n), kThreads, 0, s, {v, a, out, n});
+}
+template void scale_convert<float>(double *, double, float *, int64_t, cudaStream_t);
+template void scale_convert<double>(double *, double, double *, int64_t, cudaStream_t);
+
 void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, 16.0 * n, 6, n, (double)n);
-  if (n) k_scale<<<ew_grid(n), kThreads, 0, s>>>(x, a, y, n);
+  if (n) go<KScale>(ew_grid(n), kThreads, 0, s, {x, a, y, n});
 }
 
 int mdot_blocks(int64_t n) {
@@ -1107,29 +1523,30 @@ int mdot_blocks(int64_t n) {
 void mdot(const double *V, int64_t ldv, int k, const double *w, int64_t n, double *partial, int nblk,
           cudaStream_t s) {
   HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 1), 1, n, 2.0 * n * k);
-  k_mdot<<<nblk, kThreads, 0, s>>>(V, ldv, k, w, n, partial, nblk);
+  go<KMdot>(nblk, kThreads, 0, s, {V, ldv, k, w, n, partial, nblk});
 }
 
 void reduce_partials(const double *partial, int k, int nblk, double *out, cudaStream_t s) {
   HookScope hs(s, K_ARNOLDI, 8.0 * (double)k * nblk, 2, k, (double)k * nblk);
-  k_reduce_partials<<<k, kThreads, 0, s>>>(partial, nblk, out);
+  // recorded launches take a grid that does not depend on k (blocks >= k return)
+  go<KReducePartials>(g_rec ? (unsigned)kMaxQ : (unsigned)k, kThreads, 0, s, {partial, k, nblk, out});
 }
 
 void cgs_fused(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n, double *partial,
                int nblk, cudaStream_t s) {
   HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 3, n, 4.0 * n * k);
-  k_cgs_fused<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
+  go<KCgsFused>(nblk, kThreads, 0, s, {V, ldv, k, h, w, n, partial, nblk});
 }
 
 void cgs_update(const double *V, int64_t ldv, int k, const double *h, double *w, int64_t n,
                 double *partial, int nblk, cudaStream_t s) {
   HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 4, n, 2.0 * n * k + 2.0 * n);
-  k_cgs_update<<<nblk, kThreads, 0, s>>>(V, ldv, k, h, w, n, partial, nblk);
+  go<KCgsUpdate>(nblk, kThreads, 0, s, {V, ldv, k, h, w, n, partial, nblk});
 }
 
 void gemv_add(const double *Z, int64_t ldz, int k, const double *y, double *x, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_ARNOLDI, 8.0 * n * (k + 2), 5, n, 2.0 * n * k);
-  k_gemv_add<<<ew_grid(n), kThreads, 0, s>>>(Z, ldz, k, y, x, n);
+  go<KGemvAdd>(ew_grid(n), kThreads, 0, s, {Z, ldz, k, y, x, n});
 }
 
 #define MFS_INST(T)                                                                                   \
@@ -1147,6 +1564,7 @@ MFS_INST(float)
 template void convert<double, float>(const double *, float *, int64_t, cudaStream_t);
 template void convert<float, double>(const float *, double *, int64_t, cudaStream_t);
 template void convert<double, double>(const double *, double *, int64_t, cudaStream_t);
+template void convert<float, float>(const float *, float *, int64_t, cudaStream_t);
 
 }  // namespace dev
 }  // namespace mfs

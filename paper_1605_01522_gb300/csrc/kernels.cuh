@@ -63,6 +63,34 @@ struct HookBypass {
 // one-time device settings (call before any stream capture)
 void init();
 
+// Launch recording, for running many independent systems' launches as one
+// grid per step.  While a thread has a recorder, every launcher below appends
+// its launch (the multi-system form of its kernel, grid, block, dynamic
+// shared memory, argument block and accounting) instead of issuing it.
+struct RecOp {
+  const void *fn = nullptr;  // multi-system kernel
+  unsigned grid = 0, threads = 0;
+  size_t smem = 0;
+  std::vector<unsigned char> args;  // the kernel's argument block for this launch
+  int cls = 0, sig = 0;
+  int64_t rows = 0;
+  double bytes = 0.0, flops = 0.0;
+};
+struct Recorder {
+  std::vector<RecOp> ops;
+};
+void set_recorder(Recorder *r);
+// CTA c of a multi-system launch runs block bid (of nb) of table entry t,
+// which belongs to system g
+struct MsBlock {
+  int t, bid, nb, g;
+};
+// issue `grid` CTAs of op's multi-system kernel: tab = device array of
+// argument blocks (op.args layout, consecutive), map = grid entries,
+// active = per-system flags (0: skip) or null
+cudaError_t launch_multi(const RecOp &op, unsigned grid, size_t smem, const void *tab, const MsBlock *map,
+                         const int *active, cudaStream_t s);
+
 template <typename T> inline const T *vals(const Sell &A);
 template <> inline const double *vals<double>(const Sell &A) { return A.v64; }
 template <> inline const float *vals<float>(const Sell &A) { return A.v32; }
@@ -153,8 +181,10 @@ double fp64_rate(cudaStream_t s);
 template <typename T> void fill(T *x, int64_t n, T v, cudaStream_t s);
 template <typename T> void axpy_diag(T *x, const T *dinv, const T *t, int64_t n, cudaStream_t s);  // x -= dinv*t
 template <typename T> void axpy(T *y, const T *x, T a, int64_t n, cudaStream_t s);                 // y += a x
-template <typename TI, typename TO> void convert(const TI *in, TO *out, int64_t n, cudaStream_t s);
+template <typename TI, typename TO> void convert(const TI *in, TO *out, int64_t n, cudaStream_t s);  // also a copy (TI = TO)
 void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s);                      // y = a x
+// v = a v and out = (TO) v in one pass
+template <typename TO> void scale_convert(double *v, double a, TO *out, int64_t n, cudaStream_t s);
 
 // Arnoldi (float64).  V holds k row vectors of length n, row q at V + q*ldv.
 int mdot_blocks(int64_t n);

@@ -647,7 +647,7 @@ template <typename T> struct Precond {
   // after the coarse correction (Gauss-Seidel then sweeps backward)
   void smooth(FL<T> &f, const T *rhs, T *x, bool zero, bool post = false) {
     if (smoother == MFS_GS) {
-      if (zero) MFS_CUDA(cudaMemsetAsync(x, 0, f.n * sizeof(T), s));
+      if (zero) dev::fill<T>(x, f.n, T(0), s);
       dev::gs_sweeps<T>(f.gs, f.dblk, rhs, x, gs_omega, gs_sweeps, post, s);
       return;
     }
@@ -665,7 +665,7 @@ template <typename T> struct Precond {
       dev::smooth_step<T>(f.A, f.dinv, rhs, cur, oth, f.d, f.c1[k], f.c2[k], s);
       std::swap(cur, oth);
     }
-    if (cur != x) MFS_CUDA(cudaMemcpyAsync(x, cur, f.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    if (cur != x) dev::convert<T, T>(cur, x, f.n, s);
   }
 
   // Algorithm 1 for field i of group g from level l, zero initial guess
@@ -751,11 +751,11 @@ template <typename T> struct Precond {
     if (l == g.L - 1) {
       for (int i = 0; i < g.nf; ++i)
         if (b[i] != g.lv[l][i].bv)
-          MFS_CUDA(cudaMemcpyAsync(g.lv[l][i].bv, b[i], g.lv[l][i].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+          dev::convert<T, T>(b[i], g.lv[l][i].bv, g.lv[l][i].n, s);
       dev::lu_solve<T>(g.cc, g.cb, g.cx, s);
       for (int i = 0; i < g.nf; ++i)
         if (x[i] != g.lv[l][i].xv)
-          MFS_CUDA(cudaMemcpyAsync(x[i], g.lv[l][i].xv, g.lv[l][i].n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+          dev::convert<T, T>(g.lv[l][i].xv, x[i], g.lv[l][i].n, s);
       return;
     }
     level_smooth(g, l, b, x, true);
@@ -846,10 +846,10 @@ template <typename T> struct Precond {
       }
       for (int j : G1) {
         FL<T> &f = g.lv[l][j];
-        if (zero) MFS_CUDA(cudaMemcpyAsync(x[j], f.e, f.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        if (zero) dev::convert<T, T>(f.e, x[j], f.n, s);
         else dev::axpy<T>(x[j], f.e, T(1), f.n, s);
       }
-      if (zero) MFS_CUDA(cudaMemcpyAsync(x[k], sk.e, sk.n * sizeof(T), cudaMemcpyDeviceToDevice, s));
+      if (zero) dev::convert<T, T>(sk.e, x[k], sk.n, s);
       else dev::axpy<T>(x[k], sk.e, T(1), sk.n, s);
       zero = false;
     }
@@ -1143,6 +1143,78 @@ template <typename F> void run_graph(mfs_handle *h, int j, F &&body, bool prof) 
   if (prof) h->prof->pending.push_back(&g.recs);
 }
 
+// Host side of FGMRES(m): the Hessenberg columns, their Givens rotations,
+// the least-squares right-hand side g and the back substitution (shared by
+// the single-system loop and the fused batch, so both do the same
+// arithmetic in the same order).
+struct KrylovLS {
+  int m = 0;
+  std::vector<double> H, cs, sn, g, y;
+  double r0 = 0.0, est = 1.0, hn = 0.0;
+  int iters = 0, jend = 0;
+  bool happy = false;
+  explicit KrylovLS(int m_ = 0) : m(m_), H((size_t)(m_ + 1) * m_), cs(m_), sn(m_), g(m_ + 1), y(m_) {}
+  void start_cycle(double beta) {
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    jend = 0;
+  }
+  // column j from the Arnoldi sums hp (h1 at [0, j], |w|^2 before the
+  // projections at [j + 1], h2 at [64, 64 + j], |w|^2 after at [128]);
+  // false when a sum is not finite
+  bool column(const double *hp, int j) {
+    const double nw0 = std::sqrt(hp[j + 1]);
+    hn = std::sqrt(hp[128]);
+    if (!std::isfinite(hn) || !std::isfinite(nw0)) return false;
+    double *Hj = H.data() + (size_t)j * (m + 1);  // column j
+    for (int k = 0; k <= j; ++k) Hj[k] = hp[k] + hp[64 + k];
+    Hj[j + 1] = hn;
+    for (int k = 0; k < j; ++k) {
+      const double a = Hj[k], c = Hj[k + 1];
+      Hj[k] = cs[k] * a + sn[k] * c;
+      Hj[k + 1] = -sn[k] * a + cs[k] * c;
+    }
+    if (Hj[j + 1] == 0.0) {
+      cs[j] = 1.0;
+      sn[j] = 0.0;
+    } else {
+      const double rr = std::hypot(Hj[j], Hj[j + 1]);
+      cs[j] = Hj[j] / rr;
+      sn[j] = Hj[j + 1] / rr;
+    }
+    Hj[j] = cs[j] * Hj[j] + sn[j] * Hj[j + 1];
+    Hj[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    ++iters;
+    jend = j + 1;
+    est = std::fabs(g[j + 1]) / r0;
+    happy = hn <= 1e-14 * nw0;
+    return true;
+  }
+  void back_substitute() {
+    for (int k = jend - 1; k >= 0; --k) {
+      double sum = g[k];
+      for (int q = k + 1; q < jend; ++q) sum -= H[(size_t)q * (m + 1) + k] * y[q];
+      y[k] = sum / H[(size_t)k * (m + 1) + k];
+    }
+  }
+};
+
+// one CGS2 Arnoldi step on w = A z_j against V_0..V_j: the sums of the host
+// update land in hd (see KrylovLS::column)
+void arnoldi(mfs_handle *h, int j, double *w, double *hd, cudaStream_t s) {
+  const int64_t n = h->n;
+  // CGS2: h1 = V^T w (and |w|^2), w -= V h1, h2 = V^T w, w -= V h2 (and |w|^2)
+  dev::mdot(h->V, n, j + 2, w, n, h->partial, h->nblk, s);
+  dev::reduce_partials(h->partial, j + 2, h->nblk, hd, s);
+  dev::cgs_fused(h->V, n, j + 1, hd, w, n, h->partial, h->nblk, s);
+  dev::reduce_partials(h->partial, j + 1, h->nblk, hd + 64, s);
+  dev::cgs_update(h->V, n, j + 1, hd + 64, w, n, h->partial, h->nblk, s);
+  dev::reduce_partials(h->partial, 1, h->nblk, hd + 128, s);
+}
+
 int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info, bool prof) {
   const int64_t n = h->n;
   const int m = h->m;
@@ -1153,8 +1225,8 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
   dev::axpy<double>(r, b, -1.0, n, s);
   dev::scale(r, -1.0, r, n, s);
   const double r0 = std::sqrt(dot_host(h, r, r));
-  int iters = 0, restarts = 0;
-  double est = 1.0, relres = 0.0;
+  int restarts = 0;
+  double relres = 0.0;
   if (r0 == 0.0) {
     info->iters = 0;
     info->converged = 1;
@@ -1163,15 +1235,13 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     return MFS_OK;
   }
   if (!std::isfinite(r0)) return MFS_ERR_BREAKDOWN;
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
+  KrylovLS ls(m);
+  ls.r0 = r0;
   double *hp = h->hpin;
   while (true) {
     const double beta = std::sqrt(dot_host(h, r, r));
     dev::scale(r, 1.0 / beta, h->V, n, s);
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = beta;
-    int jend = 0;
+    ls.start_cycle(beta);
     for (int j = 0; j < m; ++j) {
       double *vj = h->V + (int64_t)j * n;
       double *zj = h->Z + (int64_t)j * n;
@@ -1179,70 +1249,457 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
       auto body = [&]() {
         precond_apply(h, vj, zj);
         matvec(h, zj, w);
-        // CGS2: h1 = V^T w (and |w|^2), w -= V h1, h2 = V^T w, w -= V h2 (and |w|^2)
-        dev::mdot(h->V, n, j + 2, w, n, h->partial, h->nblk, s);
-        dev::reduce_partials(h->partial, j + 2, h->nblk, h->hdev, s);
-        dev::cgs_fused(h->V, n, j + 1, h->hdev, w, n, h->partial, h->nblk, s);
-        dev::reduce_partials(h->partial, j + 1, h->nblk, h->hdev + 64, s);
-        dev::cgs_update(h->V, n, j + 1, h->hdev + 64, w, n, h->partial, h->nblk, s);
-        dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + 128, s);
+        arnoldi(h, j, w, h->hdev, s);
         MFS_CUDA(cudaMemcpyAsync(hp, h->hdev, 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
       };
       if (h->use_graphs) run_graph(h, j, body, prof);
       else body();
       MFS_CUDA(cudaStreamSynchronize(s));
       if (prof) h->prof->collect();
-      const double nw0 = std::sqrt(hp[j + 1]);
-      const double hn = std::sqrt(hp[128]);
-      if (!std::isfinite(hn) || !std::isfinite(nw0)) return MFS_ERR_BREAKDOWN;
-      double *Hj = H.data() + (size_t)j * (m + 1);  // column j
-      for (int k = 0; k <= j; ++k) Hj[k] = hp[k] + hp[64 + k];
-      Hj[j + 1] = hn;
-      for (int k = 0; k < j; ++k) {
-        const double a = Hj[k], c = Hj[k + 1];
-        Hj[k] = cs[k] * a + sn[k] * c;
-        Hj[k + 1] = -sn[k] * a + cs[k] * c;
-      }
-      if (Hj[j + 1] == 0.0) {
-        cs[j] = 1.0;
-        sn[j] = 0.0;
-      } else {
-        const double rr = std::hypot(Hj[j], Hj[j + 1]);
-        cs[j] = Hj[j] / rr;
-        sn[j] = Hj[j + 1] / rr;
-      }
-      Hj[j] = cs[j] * Hj[j] + sn[j] * Hj[j + 1];
-      Hj[j + 1] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++iters;
-      jend = j + 1;
-      est = std::fabs(g[j + 1]) / r0;
-      const bool happy = hn <= 1e-14 * nw0;
-      if (est <= tol || happy || iters >= h->prm.max_iters) break;
-      dev::scale(w, 1.0 / hn, w, n, s);
+      if (!ls.column(hp, j)) return MFS_ERR_BREAKDOWN;
+      if (ls.est <= tol || ls.happy || ls.iters >= h->prm.max_iters) break;
+      dev::scale(w, 1.0 / ls.hn, w, n, s);
     }
-    for (int k = jend - 1; k >= 0; --k) {
-      double sum = g[k];
-      for (int q = k + 1; q < jend; ++q) sum -= H[(size_t)q * (m + 1) + k] * y[q];
-      y[k] = sum / H[(size_t)k * (m + 1) + k];
-    }
-    MFS_CUDA(cudaMemcpyAsync(h->ydev, y.data(), jend * sizeof(double), cudaMemcpyHostToDevice, s));
-    dev::gemv_add(h->Z, n, jend, h->ydev, x, n, s);
+    ls.back_substitute();
+    MFS_CUDA(cudaMemcpyAsync(h->ydev, ls.y.data(), ls.jend * sizeof(double), cudaMemcpyHostToDevice, s));
+    dev::gemv_add(h->Z, n, ls.jend, h->ydev, x, n, s);
     matvec(h, x, r);
     dev::axpy<double>(r, b, -1.0, n, s);
     dev::scale(r, -1.0, r, n, s);
     relres = std::sqrt(dot_host(h, r, r)) / r0;
     if (!std::isfinite(relres)) return MFS_ERR_BREAKDOWN;
-    if (relres <= tol || iters >= h->prm.max_iters) break;
+    if (relres <= tol || ls.iters >= h->prm.max_iters) break;
     ++restarts;
   }
-  info->iters = iters;
+  info->iters = ls.iters;
   info->restarts = restarts;
   info->true_relres = relres;
-  info->est_relres = est;
+  info->est_relres = ls.est;
   info->converged = relres <= tol ? 1 : 0;
   return info->converged ? MFS_OK : MFS_ERR_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// Fused batch: the FGMRES iterations of many independent systems advance in
+// lockstep, each step of an iteration being ONE launch over all systems.
+// Every system's launch sequence (its preconditioner application, recorded
+// once from the same code that issues a solo solve, plus the Krylov steps,
+// re-recorded every iteration with that iteration's vectors) is merged with
+// the others' into multi-system launches: kernel K runs the blocks of every
+// system's launch of K in one grid, each CTA reading its system's argument
+// block from a table (dev::launch_multi).  The merged launches form one CUDA
+// graph per batch, replayed once per iteration; a per-system flag stops the
+// CTAs of systems that have finished.  Each system's kernels, arguments and
+// order are the ones of its solo solve, so its result is the solo result bit
+// for bit.  Restarts and the end of a cycle (x update, true residual) run as
+// ordinary launches for the systems concerned.
+// ---------------------------------------------------------------------------
+
+// Merge per-system launch sequences: repeatedly take the kernel (and block
+// size) shared by most systems' next launches - ties to the systems with
+// more launches left - and issue it for all of them at once; each system's
+// launches keep their order.  groups[g] = (system, index) of merged launch g.
+static void merge_sequences(const std::vector<const std::vector<dev::RecOp> *> &seqs,
+                            std::vector<std::vector<std::pair<int, int>>> &groups) {
+  const size_t ns = seqs.size();
+  std::vector<size_t> p(ns, 0);
+  while (true) {
+    std::map<std::pair<const void *, unsigned>, std::pair<int, size_t>> cnt;
+    for (size_t k = 0; k < ns; ++k) {
+      if (p[k] >= seqs[k]->size()) continue;
+      const dev::RecOp &op = (*seqs[k])[p[k]];
+      auto &c = cnt[{op.fn, op.threads}];
+      c.first += 1;
+      c.second = std::max(c.second, seqs[k]->size() - p[k]);
+    }
+    if (cnt.empty()) break;
+    auto best = cnt.begin();
+    for (auto it = cnt.begin(); it != cnt.end(); ++it)
+      if (it->second.first > best->second.first ||
+          (it->second.first == best->second.first && it->second.second > best->second.second))
+        best = it;
+    std::vector<std::pair<int, int>> grp;
+    for (size_t k = 0; k < ns; ++k) {
+      if (p[k] >= seqs[k]->size()) continue;
+      const dev::RecOp &op = (*seqs[k])[p[k]];
+      if (op.fn == best->first.first && op.threads == best->first.second) {
+        grp.push_back({(int)k, (int)p[k]});
+        ++p[k];
+      }
+    }
+    groups.push_back(std::move(grp));
+  }
+}
+
+struct FusedBatch {
+  std::vector<mfs_handle *> hs;
+  int nsys = 0;
+  cudaStream_t s = nullptr;
+  Arena ar;
+  struct Launch {
+    dev::RecOp proto;       // kernel and block size
+    unsigned grid = 0;      // CTAs over all entries
+    size_t smem = 0;        // largest entry's dynamic shared memory
+    size_t tab = 0, map = 0, asz = 0;
+    int nent = 0;
+  };
+  std::vector<Launch> launches;  // in issue order: heads, preconditioners, tails
+  // per system: (launch, entry) of each of its head / tail launches
+  std::vector<std::vector<std::pair<int, int>>> head_at, tail_at;
+  unsigned char *htab = nullptr;  // pinned host copy of every argument table
+  size_t tab_bytes = 0, patch_bytes = 0;
+  unsigned char *dtab = nullptr;
+  dev::MsBlock *dmap = nullptr;
+  int *dactive = nullptr, *hactive = nullptr;
+  double *hb = nullptr, *hbpin = nullptr, *ypin = nullptr;  // Arnoldi sums (136 per system), y (64 per system)
+  std::vector<double *> vin, zout;  // float64 systems: fixed preconditioner input / output
+  cudaGraphExec_t exec = nullptr;
+  FusedBatch() = default;
+  FusedBatch(const FusedBatch &) = delete;
+  ~FusedBatch() {
+    if (s) cudaStreamSynchronize(s);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (htab) cudaFreeHost(htab);
+    if (hactive) cudaFreeHost(hactive);
+    if (hbpin) cudaFreeHost(hbpin);
+    if (ypin) cudaFreeHost(ypin);
+    if (s) cudaStreamDestroy(s);
+  }
+  double *sums(int k) { return hb + (int64_t)k * 136; }
+
+  // launches of system k before its preconditioner: v_j = a v_j and the
+  // preconditioner's copy of it
+  void record_head(int k, int j, double a, dev::Recorder &rec) {
+    mfs_handle *h = hs[k];
+    double *vj = h->V + (int64_t)j * h->n;
+    dev::set_recorder(&rec);
+    if (h->p32) dev::scale_convert<float>(vj, a, h->in32, h->n, s);
+    else dev::scale_convert<double>(vj, a, vin[k], h->n, s);
+    dev::set_recorder(nullptr);
+  }
+  void record_precond(int k, dev::Recorder &rec) {
+    mfs_handle *h = hs[k];
+    dev::set_recorder(&rec);
+    if (h->p32) h->p32->apply(h->in32, h->out32);
+    else h->p64->apply(vin[k], zout[k]);
+    dev::set_recorder(nullptr);
+  }
+  // after it: z_j, w = A z_j, CGS2 against V_0..V_j
+  void record_tail(int k, int j, dev::Recorder &rec) {
+    mfs_handle *h = hs[k];
+    double *zj = h->Z + (int64_t)j * h->n;
+    double *w = h->V + (int64_t)(j + 1) * h->n;
+    dev::set_recorder(&rec);
+    if (h->p32) dev::convert<float, double>(h->out32, zj, h->n, s);
+    else dev::convert<double, double>(zout[k], zj, h->n, s);
+    matvec(h, zj, w);
+    arnoldi(h, j, w, sums(k), s);
+    dev::set_recorder(nullptr);
+  }
+
+  // merge one segment; its launches go to `launches`, its tables at the
+  // current end of the table layout
+  void add_segment(std::vector<dev::Recorder> &recs, std::vector<std::vector<std::pair<int, int>>> *at,
+                   std::vector<unsigned char> &tabs, std::vector<dev::MsBlock> &maps) {
+    std::vector<const std::vector<dev::RecOp> *> seqs;
+    for (auto &r : recs) seqs.push_back(&r.ops);
+    std::vector<std::vector<std::pair<int, int>>> groups;
+    merge_sequences(seqs, groups);
+    if (at) {
+      at->assign(nsys, {});
+      for (int k = 0; k < nsys; ++k) (*at)[k].resize(recs[k].ops.size());
+    }
+    for (auto &grp : groups) {
+      Launch L;
+      const dev::RecOp &p0 = recs[grp[0].first].ops[grp[0].second];
+      L.proto = p0;
+      L.proto.args.clear();
+      L.asz = p0.args.size();
+      L.nent = (int)grp.size();
+      L.tab = (tabs.size() + 15) / 16 * 16;
+      tabs.resize(L.tab + L.asz * grp.size());
+      L.map = maps.size();
+      for (size_t e = 0; e < grp.size(); ++e) {
+        const dev::RecOp &op = recs[grp[e].first].ops[grp[e].second];
+        if (op.args.size() != L.asz) throw CudaError(MFS_ERR_INVALID, "fused batch: argument blocks differ");
+        std::memcpy(tabs.data() + L.tab + e * L.asz, op.args.data(), L.asz);
+        for (unsigned b = 0; b < op.grid; ++b) maps.push_back({(int)e, (int)b, (int)op.grid, grp[e].first});
+        L.grid += op.grid;
+        L.smem = std::max(L.smem, op.smem);
+        if (at) (*at)[grp[e].first][grp[e].second] = {(int)launches.size(), (int)e};
+      }
+      launches.push_back(std::move(L));
+    }
+  }
+
+  void build(mfs_handle *const *hv, int n) {
+    hs.assign(hv, hv + n);
+    nsys = n;
+    MFS_CUDA(cudaSetDevice(hs[0]->device));
+    MFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    vin.assign(nsys, nullptr);
+    zout.assign(nsys, nullptr);
+    for (int k = 0; k < nsys; ++k)
+      if (!hs[k]->p32) {
+        vin[k] = ar.zeros<double>(hs[k]->n);
+        zout[k] = ar.zeros<double>(hs[k]->n);
+      }
+    hb = ar.zeros<double>((int64_t)136 * nsys);
+    dactive = ar.zeros<int>(nsys);
+    MFS_CUDA(cudaMallocHost(&hbpin, (size_t)136 * nsys * sizeof(double)));
+    MFS_CUDA(cudaMallocHost(&ypin, (size_t)64 * nsys * sizeof(double)));
+    MFS_CUDA(cudaMallocHost(&hactive, (size_t)nsys * sizeof(int)));
+    std::vector<dev::Recorder> heads(nsys), pre(nsys), tails(nsys);
+    for (int k = 0; k < nsys; ++k) {
+      record_head(k, 0, 1.0, heads[k]);
+      record_precond(k, pre[k]);
+      record_tail(k, 0, tails[k]);
+    }
+    // tables of the per-iteration launches first (one upload per iteration)
+    std::vector<unsigned char> tabs;
+    std::vector<dev::MsBlock> maps;
+    add_segment(heads, &head_at, tabs, maps);
+    const size_t nhead = launches.size();
+    add_segment(tails, &tail_at, tabs, maps);
+    patch_bytes = tabs.size();
+    const size_t ntail_end = launches.size();
+    add_segment(pre, nullptr, tabs, maps);
+    tab_bytes = tabs.size();
+    // issue order: heads, preconditioners, tails
+    std::vector<Launch> order;
+    for (size_t i = 0; i < nhead; ++i) order.push_back(launches[i]);
+    for (size_t i = ntail_end; i < launches.size(); ++i) order.push_back(launches[i]);
+    std::vector<int> remap(launches.size());
+    for (size_t i = nhead; i < ntail_end; ++i) order.push_back(launches[i]);
+    for (size_t i = 0; i < nhead; ++i) remap[i] = (int)i;
+    const size_t npre = launches.size() - ntail_end;
+    for (size_t i = ntail_end; i < launches.size(); ++i) remap[i] = (int)(nhead + (i - ntail_end));
+    for (size_t i = nhead; i < ntail_end; ++i) remap[i] = (int)(nhead + npre + (i - nhead));
+    for (auto &v : head_at)
+      for (auto &pr : v) pr.first = remap[pr.first];
+    for (auto &v : tail_at)
+      for (auto &pr : v) pr.first = remap[pr.first];
+    launches.swap(order);
+    MFS_CUDA(cudaMallocHost(&htab, std::max<size_t>(tab_bytes, 16)));
+    std::memcpy(htab, tabs.data(), tab_bytes);
+    dtab = ar.alloc<unsigned char>((int64_t)std::max<size_t>(tab_bytes, 16));
+    dmap = ar.alloc<dev::MsBlock>((int64_t)std::max<size_t>(maps.size(), 1));
+    MFS_CUDA(cudaMemcpyAsync(dtab, htab, tab_bytes, cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(dmap, maps.data(), maps.size() * sizeof(dev::MsBlock), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaStreamSynchronize(s));
+    MFS_CUDA(cudaStreamSynchronize(0));
+    // one graph: every merged launch, then the Arnoldi sums to the host
+    cudaGraph_t graph = nullptr;
+    MFS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    cudaError_t err = cudaSuccess;
+    for (const Launch &L : launches) {
+      err = dev::launch_multi(L.proto, L.grid, L.smem, dtab + L.tab, dmap + L.map, dactive, s);
+      if (err != cudaSuccess) break;
+    }
+    if (err == cudaSuccess)
+      err = cudaMemcpyAsync(hbpin, hb, (size_t)136 * nsys * sizeof(double), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
+    MFS_CUDA(err);
+    MFS_CUDA(e2);
+    const cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    MFS_CUDA(e3);
+  }
+
+  // write system k's freshly recorded launches into its slots of the tables
+  void patch(const dev::Recorder &rec, const std::vector<std::pair<int, int>> &at) {
+    if (rec.ops.size() != at.size()) throw CudaError(MFS_ERR_INVALID, "fused batch: launch sequence changed");
+    for (size_t q = 0; q < rec.ops.size(); ++q) {
+      const Launch &L = launches[at[q].first];
+      if (rec.ops[q].args.size() != L.asz || rec.ops[q].fn != L.proto.fn)
+        throw CudaError(MFS_ERR_INVALID, "fused batch: launch changed between iterations");
+      std::memcpy(htab + L.tab + (size_t)at[q].second * L.asz, rec.ops[q].args.data(), L.asz);
+    }
+  }
+};
+
+// Process-wide cache of fused batches by their handle list (a batch holds
+// the handles' device addresses; mfs_free drops every batch of a handle).
+static std::mutex g_fused_mu;
+static std::vector<std::unique_ptr<FusedBatch>> g_fused;
+
+static void drop_fused(const mfs_handle *h) {
+  std::lock_guard<std::mutex> lock(g_fused_mu);
+  for (size_t i = 0; i < g_fused.size();)
+    if (std::find(g_fused[i]->hs.begin(), g_fused[i]->hs.end(), h) != g_fused[i]->hs.end())
+      g_fused.erase(g_fused.begin() + (long)i);
+    else
+      ++i;
+}
+
+static FusedBatch *fused_for(mfs_handle *const *hv, int n) {
+  std::lock_guard<std::mutex> lock(g_fused_mu);
+  for (auto &b : g_fused)
+    if (b->nsys == n && std::equal(b->hs.begin(), b->hs.end(), hv)) return b.get();
+  std::unique_ptr<FusedBatch> b(new FusedBatch());
+  b->build(hv, n);
+  if (g_fused.size() >= 4) g_fused.erase(g_fused.begin());
+  g_fused.push_back(std::move(b));
+  return g_fused.back().get();
+}
+
+// FGMRES of every system of the batch, lockstep (see FusedBatch).
+static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *x, double tol,
+                        std::vector<mfs_info> &info, std::vector<int> &status) {
+  const int ns = B.nsys;
+  cudaStream_t s = B.s;
+  std::vector<mfs_handle *> &hs = B.hs;
+  // every launch of the handles' own code goes to the batch stream meanwhile
+  std::vector<cudaStream_t> saved(ns);
+  for (int k = 0; k < ns; ++k) {
+    saved[k] = hs[k]->s;
+    hs[k]->s = s;
+    if (hs[k]->p32) hs[k]->p32->s = s;
+    if (hs[k]->p64) hs[k]->p64->s = s;
+  }
+  struct Restore {
+    std::vector<mfs_handle *> &hs;
+    std::vector<cudaStream_t> &saved;
+    ~Restore() {
+      for (size_t k = 0; k < hs.size(); ++k) {
+        hs[k]->s = saved[k];
+        if (hs[k]->p32) hs[k]->p32->s = saved[k];
+        if (hs[k]->p64) hs[k]->p64->s = saved[k];
+      }
+    }
+  } restore{hs, saved};
+  // the caller's vectors come from the legacy default stream
+  cudaEvent_t entry = nullptr;
+  MFS_CUDA(cudaEventCreateWithFlags(&entry, cudaEventDisableTiming));
+  MFS_CUDA(cudaEventRecord(entry, 0));
+  MFS_CUDA(cudaStreamWaitEvent(s, entry, 0));
+  cudaEventDestroy(entry);
+  for (int k = 0; k < ns; ++k) MFS_CUDA(cudaStreamSynchronize(saved[k]));
+  std::vector<const double *> b(ns);
+  std::vector<double *> xx(ns);
+  std::vector<char> hostx(ns, 0);
+  for (int k = 0; k < ns; ++k) {
+    mfs_handle *h = hs[k];
+    b[k] = rhs[k];
+    xx[k] = x[k];
+    if (!is_device_ptr(rhs[k])) {
+      MFS_CUDA(cudaMemcpyAsync(h->bd, rhs[k], h->n * sizeof(double), cudaMemcpyHostToDevice, s));
+      b[k] = h->bd;
+    }
+    if (!is_device_ptr(x[k])) {
+      MFS_CUDA(cudaMemcpyAsync(h->xd, x[k], h->n * sizeof(double), cudaMemcpyHostToDevice, s));
+      xx[k] = h->xd;
+      hostx[k] = 1;
+    }
+  }
+  // residual norms of the systems in `which` (r = b - A x, then |r|^2 into
+  // sums(k)[132]); one synchronisation for all
+  auto residuals = [&](const std::vector<int> &which, std::vector<double> &rn) {
+    for (int k : which) {
+      mfs_handle *h = hs[k];
+      matvec(h, xx[k], h->rd);
+      dev::axpy<double>(h->rd, b[k], -1.0, h->n, s);
+      dev::scale(h->rd, -1.0, h->rd, h->n, s);
+      dev::mdot(h->rd, 0, 1, h->rd, h->n, h->partial, h->nblk, s);
+      dev::reduce_partials(h->partial, 1, h->nblk, B.sums(k) + 132, s);
+    }
+    MFS_CUDA(cudaMemcpyAsync(B.hbpin, B.hb, (size_t)136 * ns * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MFS_CUDA(cudaStreamSynchronize(s));
+    for (int k : which) rn[k] = std::sqrt(B.hbpin[(int64_t)k * 136 + 132]);
+  };
+  std::vector<KrylovLS> ls;
+  for (int k = 0; k < ns; ++k) ls.emplace_back(hs[k]->m);
+  std::vector<int> j(ns, 0), restarts(ns, 0);
+  std::vector<double> a(ns, 1.0), rn(ns, 0.0), relres(ns, 0.0);
+  std::vector<char> active(ns, 0);
+  std::vector<int> all(ns);
+  for (int k = 0; k < ns; ++k) all[k] = k;
+  residuals(all, rn);
+  auto start_cycle = [&](int k, double beta) {
+    mfs_handle *h = hs[k];
+    dev::scale(h->rd, 1.0 / beta, h->V, h->n, s);
+    ls[k].start_cycle(beta);
+    j[k] = 0;
+    a[k] = 1.0;
+  };
+  auto finish = [&](int k, int rc) {
+    active[k] = 0;
+    status[k] = rc;
+    info[k].iters = ls[k].iters;
+    info[k].restarts = restarts[k];
+    info[k].true_relres = relres[k];
+    info[k].est_relres = ls[k].est;
+    info[k].converged = rc == MFS_OK ? 1 : 0;
+  };
+  for (int k = 0; k < ns; ++k) {
+    ls[k].r0 = rn[k];
+    if (rn[k] == 0.0) {
+      info[k].converged = 1;
+      status[k] = MFS_OK;
+    } else if (!std::isfinite(rn[k])) {
+      status[k] = MFS_ERR_BREAKDOWN;
+    } else {
+      active[k] = 1;
+      start_cycle(k, rn[k]);
+    }
+  }
+  dev::Recorder rec;
+  while (std::find(active.begin(), active.end(), 1) != active.end()) {
+    for (int k = 0; k < ns; ++k) {
+      B.hactive[k] = active[k];
+      if (!active[k]) continue;
+      rec.ops.clear();
+      B.record_head(k, j[k], a[k], rec);
+      B.patch(rec, B.head_at[k]);
+      rec.ops.clear();
+      B.record_tail(k, j[k], rec);
+      B.patch(rec, B.tail_at[k]);
+    }
+    MFS_CUDA(cudaMemcpyAsync(B.dtab, B.htab, B.patch_bytes, cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(B.dactive, B.hactive, ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaGraphLaunch(B.exec, s));
+    MFS_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> ending;
+    for (int k = 0; k < ns; ++k) {
+      if (!active[k]) continue;
+      if (!ls[k].column(B.hbpin + (int64_t)k * 136, j[k])) {
+        finish(k, MFS_ERR_BREAKDOWN);
+        continue;
+      }
+      if (ls[k].est <= tol || ls[k].happy || ls[k].iters >= hs[k]->prm.max_iters || j[k] + 1 == hs[k]->m) {
+        ending.push_back(k);
+      } else {
+        a[k] = 1.0 / ls[k].hn;
+        ++j[k];
+      }
+    }
+    if (ending.empty()) continue;
+    // end of a cycle: x += Z y, true residual; stop or restart
+    for (int k : ending) {
+      mfs_handle *h = hs[k];
+      ls[k].back_substitute();
+      double *yp = B.ypin + (int64_t)k * 64;
+      std::copy(ls[k].y.begin(), ls[k].y.begin() + ls[k].jend, yp);
+      MFS_CUDA(cudaMemcpyAsync(h->ydev, yp, ls[k].jend * sizeof(double), cudaMemcpyHostToDevice, s));
+      dev::gemv_add(h->Z, h->n, ls[k].jend, h->ydev, xx[k], h->n, s);
+    }
+    residuals(ending, rn);
+    for (int k : ending) {
+      relres[k] = rn[k] / ls[k].r0;
+      if (!std::isfinite(relres[k])) {
+        finish(k, MFS_ERR_BREAKDOWN);
+      } else if (relres[k] <= tol || ls[k].iters >= hs[k]->prm.max_iters) {
+        finish(k, relres[k] <= tol ? MFS_OK : MFS_ERR_NOT_CONVERGED);
+      } else {
+        ++restarts[k];
+        start_cycle(k, rn[k]);
+      }
+    }
+  }
+  for (int k = 0; k < ns; ++k)
+    if (hostx[k]) MFS_CUDA(cudaMemcpyAsync(x[k], xx[k], hs[k]->n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MFS_CUDA(cudaStreamSynchronize(s));
+  MFS_CUDA(cudaGetLastError());
 }
 
 HBsr to_hbsr(const mfs_block &b) {
@@ -1978,6 +2435,39 @@ int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, d
       if (hs[q] == hs[k]) return fail(MFS_ERR_INVALID, "a handle appears twice in one batch");
   }
   if (nsys == 0) return MFS_OK;
+  for (int k = 0; k < nsys; ++k) {
+    if (hs[k]->host_only) return fail(MFS_ERR_INVALID, "a handle of the batch was built with setup_only");
+    if (hs[k]->device != hs[0]->device) return fail(MFS_ERR_INVALID, "fused batch: handles on different devices");
+  }
+  if (nthreads == 0) {
+    std::vector<mfs_info> inf(nsys);
+    std::vector<int> st(nsys, MFS_OK);
+    const double t0 = now_ms();
+    try {
+      MFS_CUDA(cudaSetDevice(hs[0]->device));
+      FusedBatch *B = fused_for(hs, nsys);
+      fused_solve(*B, rhs, x, tol, inf, st);
+    } catch (const CudaError &e) {
+      return fail(e.code, e.what());
+    } catch (const std::bad_alloc &) {
+      return fail(MFS_ERR_OOM, "host allocation failed");
+    }
+    const double ms = now_ms() - t0;
+    int rc = MFS_OK;
+    for (int k = 0; k < nsys; ++k) {
+      inf[k].solve_ms = ms;
+      inf[k].setup_ms = hs[k]->setup_ms;
+      inf[k].levels[0] = hs[k]->host->hg0.nlevels();
+      inf[k].levels[1] = hs[k]->host->hg1.nlevels();
+      if (infos) infos[k] = inf[k];
+      if (status) status[k] = st[k];
+      if (st[k] != MFS_OK && rc == MFS_OK) {
+        rc = st[k];
+        g_last_error = "system " + std::to_string(k) + ": " + mfs_strerror(st[k]);
+      }
+    }
+    return rc;
+  }
   int nt = nthreads > 0 ? nthreads : 16;
   if (nt > nsys) nt = nsys;
   std::atomic<int> next(0);
@@ -2198,6 +2688,7 @@ int mfs_kernel_detail(mfs_handle *h, double *out, int cap) {
 
 void mfs_free(mfs_handle *h) {
   if (!h) return;
+  drop_fused(h);
   if (!h->host_only) {
     if (h->s) cudaStreamSynchronize(h->s);
     else cudaDeviceSynchronize();

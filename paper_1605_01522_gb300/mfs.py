@@ -32,7 +32,7 @@ EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_sol
            "mfs_export_csr", "mfs_export_array", "mfs_num_levels", "mfs_kernel_stats", "mfs_kernel_detail", "mfs_profile_filter", "mfs_free",
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
-_OTHER = {2: {1: "smooth_first", 2: "fill", 3: "axpy_diag", 4: "axpy", 5: "convert", 6: "scale"},
+_OTHER = {2: {1: "smooth_first", 2: "fill", 3: "axpy_diag", 4: "axpy", 5: "convert", 6: "scale", 7: "scale_convert"},
           3: {1: "lu_solve", 2: "coarse_inverse_apply"},
           4: {1: "mdot", 2: "reduce_partials", 3: "cgs_fused", 4: "cgs_update", 5: "gemv_add"}}
 
@@ -167,7 +167,7 @@ def dot_noalloc(x, y, n=None, stream=None):
     n = size(x) if n is None else n
     if n > min(size(x), size(y)):
         raise ValueError(f"dot_noalloc: n = {n} exceeds a vector's length ({size(x)}, {size(y)})")
-    if hasattr(x, "device") and hasattr(y, "device"):
+    if hasattr(x, "is_cuda") and hasattr(y, "is_cuda"):  # torch tensors
         import torch
         if x.device != y.device or (x.is_cuda and x.device.index != torch.cuda.current_device()):
             raise ValueError("dot_noalloc: x and y must be on the current CUDA device")
@@ -232,8 +232,11 @@ def _ptr(a):
 
 
 def solve_batch(solvers, rhs, xs=None, tol=1e-8, nthreads=0, check=True):
-    """Solve independent systems concurrently (mfs_solve_batch): solvers[k]
-    (distinct handles) with rhs[k]; returns (xs, infos, status)."""
+    """Solve independent systems together (mfs_solve_batch): solvers[k]
+    (distinct handles) with rhs[k]; nthreads = 0 runs the fused executor
+    (one multi-system launch per step, one CUDA graph per iteration),
+    nthreads > 0 that many host threads on per-handle streams; returns
+    (xs, infos, status)."""
     lib = load()
     n = len(solvers)
     if xs is None:
