@@ -79,7 +79,7 @@ enum mfs_status {
 
 enum mfs_precond { MFS_BGS_AMG = 0, MFS_SIMPLE = 1, MFS_AMG_BGS = 2, MFS_AMG_SIMPLE = 3, MFS_BGS_GS = 4 };
 enum mfs_bgs_order { MFS_BWD = 0, MFS_FWD = 1, MFS_SYM = 2 };
-enum mfs_nullspace { MFS_NS_CONST = 0, MFS_NS_RBM = 1 };
+enum mfs_nullspace { MFS_NS_CONST = 0, MFS_NS_RBM = 1, MFS_NS_USER = 2 };
 enum mfs_precision { MFS_FP64 = 0, MFS_FP32P = 1 };
 enum mfs_simple_approx { MFS_ABSROWSUM = 0, MFS_DIAG = 1 };
 enum mfs_smoother { MFS_CHEBYSHEV = 0, MFS_JACOBI = 1, MFS_GS = 2 };
@@ -104,7 +104,22 @@ typedef struct {
  * non-symmetric diagonal block (the paper's fluid field, Sec. 7.2): its
  * hierarchy takes Petrov-Galerkin transfers after Sala & Tuminaro (2008),
  * R != P^T (local damping parameters minimising ||A p_j|| in the D^-1 norm,
- * moved to the rows by a minimum; R from the same construction on A^T). */
+ * moved to the rows by a minimum; R from the same construction on A^T).
+ * The near-nullspace of smoothed aggregation (Sec. 3.3: the vectors the
+ * tentative prolongator reproduces) is the constants per dof
+ * (MFS_NS_CONST), the rigid-body modes (MFS_NS_RBM, rotations about each
+ * aggregate's centroid) or the caller's vectors (MFS_NS_USER): ns_user
+ * (host) holds ns_dim values per dof, dof-major (entry (d, q) at
+ * ns_user[d * ns_dim + q], d = node * dofs_per_node + component), with
+ * ns_dim and dofs_per_node in {1, 2, 3, 6}; the coarse levels have ns_dim
+ * dofs per aggregate.  ns_user / ns_dim are ignored for the other kinds.
+ * dirichlet (host, nnodes * dofs_per_node bytes, or NULL) flags dofs held by
+ * Dirichlet conditions that the caller has eliminated: a flagged dof's row
+ * must be the identity row across the field's block row (1 on the diagonal
+ * of A_ii, 0 everywhere else; MFS_ERR_INVALID otherwise).  The fine level's
+ * near-nullspace vectors are zero at flagged dofs (so the prolongator never
+ * moves them), and a node whose every dof is flagged stays out of every
+ * aggregate.  Copied by mfs_setup. */
 typedef struct {
   int64_t nnodes;
   int dofs_per_node;
@@ -113,6 +128,9 @@ typedef struct {
   int nullspace;          /* enum mfs_nullspace */
   double strength_theta;  /* strength-of-connection threshold, >= 0 */
   int petrov_galerkin;    /* 0: smoothed aggregation, R = P^T; 1: Petrov-Galerkin */
+  const double *ns_user;  /* MFS_NS_USER: nnodes * dofs_per_node * ns_dim values */
+  int ns_dim;             /* MFS_NS_USER: vectors in ns_user */
+  const uint8_t *dirichlet; /* NULL or nnodes * dofs_per_node flags (nonzero: Dirichlet dof) */
 } mfs_field;
 
 typedef struct {

@@ -16,7 +16,11 @@ steps below are the readings this project fixes:
    (ties: lower index); every neighbour of a root joins it; every remaining
    node joins, among its neighbours aggregated so far, the aggregate whose
    root has the highest priority.  Aggregates are numbered by root index.
-3. tentative prolongator: per aggregate, QR of the near-nullspace rows by
+   Nodes whose every dof is flagged as a Dirichlet dof by the caller lose
+   all their edges as well.
+3. tentative prolongator: per aggregate, QR of the near-nullspace rows (the
+   field's constants, rigid-body modes or the caller's vectors; zero rows at
+   flagged Dirichlet dofs) by
    column-wise Gram-Schmidt with one re-orthogonalisation, dropping a column
    whose remaining norm is below 1e-10 of its norm before projection; the
    Q columns fill P_tent and R becomes the coarse near-nullspace.
@@ -65,6 +69,16 @@ def strength_graph(A: sp.csr_matrix, b: int, theta: float) -> sp.csr_matrix:
     G = ((G + G.T) > 0).astype(np.float64).tocsr()
     G.sort_indices()
     return G
+
+
+def isolate_nodes(G: sp.csr_matrix, mask: np.ndarray) -> sp.csr_matrix:
+    """The strength graph without any edge of a masked node (a node whose
+    every dof is a Dirichlet dof stays out of every aggregate)."""
+    keep = sp.diags((~mask).astype(np.float64))
+    H = (keep @ G @ keep).tocsr()
+    H.eliminate_zeros()
+    H.sort_indices()
+    return H
 
 
 def aggregate(G: sp.csr_matrix, seed: int):
@@ -134,9 +148,11 @@ def fine_nullspace_rows(field_b: int, dim: int, kind: str, xyz: np.ndarray) -> n
     raise ValueError("rigid-body modes need b == dim")
 
 
-def nullspace_dim(field_b: int, dim: int, kind: str) -> int:
+def nullspace_dim(field_b: int, dim: int, kind: str, user=None) -> int:
     if kind == "const":
         return field_b
+    if kind == "user":
+        return int(user.shape[1])
     return 3 if dim == 2 else 6
 
 
@@ -160,10 +176,12 @@ def gram_schmidt_qr(B: np.ndarray):
     return Q, R
 
 
-def tentative_prolongator(agg, nagg, b, k, B=None, coords=None, kind=None, dim=None):
+def tentative_prolongator(agg, nagg, b, k, B=None, coords=None, kind=None, dim=None, user=None, dmask=None):
     """Step 3.  On the fine level B is None and the nullspace is formed from
-    node coordinates (centred per aggregate); on coarse levels B is the
-    previous level's coarse nullspace (n x k).  Returns (P_tent, B_coarse)."""
+    node coordinates (centred per aggregate), or taken from the caller's
+    vectors (kind "user": `user`, ndofs x k); on coarse levels B is the
+    previous level's coarse nullspace (n x k).  On the fine level the rows of
+    dofs flagged in dmask (Dirichlet dofs) are zero.  Returns (P_tent, B_coarse)."""
     n = len(agg) * b
     rows, cols, vals = [], [], []
     Bc = np.zeros((nagg * k, k))
@@ -174,12 +192,17 @@ def tentative_prolongator(agg, nagg, b, k, B=None, coords=None, kind=None, dim=N
         dofs = (nodes[:, None] * b + np.arange(b)[None, :]).ravel()
         if B is None and kind == "const":
             Ba = fine_nullspace_rows(b, dim, kind, np.zeros((len(nodes), 0)))
+        elif B is None and kind == "user":
+            Ba = np.array(user[dofs], dtype=np.float64)
         elif B is None:
             xyz = coords[nodes]
             xyz = xyz - xyz.mean(axis=0)
             Ba = fine_nullspace_rows(b, dim, kind, xyz)
         else:
             Ba = B[dofs]
+        if B is None and dmask is not None:
+            Ba = Ba.copy()
+            Ba[dmask[dofs]] = 0.0
         Q, R = gram_schmidt_qr(Ba)
         rr, cc = np.nonzero(np.ones_like(Q, bool))
         rows.append(dofs[rr])
@@ -220,15 +243,28 @@ class FieldLevel:
 
 
 class FieldSpec:
-    """What the setup needs to know about a field (mirrors the C-ABI field map)."""
+    """What the setup needs to know about a field (mirrors the C-ABI field
+    map): dofs per node, dimension, near-nullspace kind ("const", "rbm" or
+    "user" with the caller's vectors `user`, ndofs x k), node coordinates,
+    strength threshold, Petrov-Galerkin flag and optional per-dof Dirichlet
+    flags (`dirichlet`, bool per dof)."""
 
-    def __init__(self, b, dim, kind, coords=None, theta=0.0, pg=False):
+    def __init__(self, b, dim, kind, coords=None, theta=0.0, pg=False, user=None, dirichlet=None):
         self.b, self.dim, self.kind, self.coords, self.theta = b, dim, kind, coords, theta
         self.pg = pg
+        self.user = user
+        self.dirichlet = None if dirichlet is None else np.asarray(dirichlet, bool)
+
+    def node_mask(self):
+        """Nodes whose every dof is a flagged Dirichlet dof (or None)."""
+        if self.dirichlet is None:
+            return None
+        return self.dirichlet.reshape(-1, self.b).all(axis=1)
 
     @classmethod
     def of(cls, f):
-        return cls(f.b, f.dim, f.nullspace, f.coords, f.theta, getattr(f, "petrov_galerkin", False))
+        return cls(f.b, f.dim, f.nullspace, f.coords, f.theta, getattr(f, "petrov_galerkin", False),
+                   getattr(f, "ns_user", None), getattr(f, "dirichlet_dofs", None))
 
 
 # a scalar column counts in the row minimum of the damping parameters when its
@@ -286,13 +322,17 @@ def build_group(As, specs, max_levels, coarse_max, seed):
         nxt = []
         for fl, s in zip(levels[-1], specs):
             fl.lam = power_lambda(fl.A, fl.dinv, seed)
-            agg, roots, _ = aggregate(strength_graph(fl.A, fl.b, s.theta), seed)
+            G = strength_graph(fl.A, fl.b, s.theta)
+            if fine and s.node_mask() is not None:
+                G = isolate_nodes(G, s.node_mask())
+            agg, roots, _ = aggregate(G, seed)
             nagg = len(roots)
             if nagg == 0:
                 raise RuntimeError("aggregation produced no aggregate")
             if fine:
-                k = nullspace_dim(s.b, s.dim, s.kind)
-                Pt, Bc = tentative_prolongator(agg, nagg, fl.b, k, coords=s.coords, kind=s.kind, dim=s.dim)
+                k = nullspace_dim(s.b, s.dim, s.kind, s.user)
+                Pt, Bc = tentative_prolongator(agg, nagg, fl.b, k, coords=s.coords, kind=s.kind, dim=s.dim,
+                                               user=s.user, dmask=s.dirichlet)
             else:
                 k = fl.b
                 Pt, Bc = tentative_prolongator(agg, nagg, fl.b, k, B=fl.B)

@@ -17,8 +17,9 @@ struct Graph {
   std::vector<int32_t> ci;
 };
 
-// Strong-connection node graph (symmetrised, no self loops).
-Graph strength_graph(const HBsr &A, double theta) {
+// Strong-connection node graph (symmetrised, no self loops); nodes flagged
+// in `fixed` (if not empty) keep no edge.
+Graph strength_graph(const HBsr &A, double theta, const std::vector<uint8_t> &fixed) {
   const int64_t n = A.nbr;
   const int64_t bs = (int64_t)A.br * A.bc;
   std::vector<double> dnorm(n, 0.0);
@@ -36,6 +37,7 @@ Graph strength_graph(const HBsr &A, double theta) {
     for (int64_t a = A.rp[I]; a < A.rp[I + 1]; ++a) {
       const int32_t J = A.ci[a];
       if (J == I) continue;
+      if (!fixed.empty() && (fixed[I] || fixed[J])) continue;
       if (fro[a] > theta * std::sqrt(dnorm[I] * dnorm[J])) {
         adj[I].push_back(J);
         adj[J].push_back((int32_t)I);
@@ -139,6 +141,7 @@ void gs_qr(int m, int k, const std::vector<double> &B, std::vector<double> &Q, s
 
 int nullspace_dim(const FieldInfo &f) {
   if (f.ns == 0) return f.b;
+  if (f.ns == 2) return f.ns_dim;
   return f.dim == 2 ? 3 : 6;
 }
 
@@ -175,6 +178,11 @@ void tentative(const std::vector<int32_t> &agg, int64_t nagg, int b, int k, bool
     if (fine && f.ns == 0) {
       for (int64_t t = 0; t < cnt; ++t)
         for (int c = 0; c < b; ++c) Ba[(size_t)(t * b + c) * k + c] = 1.0;
+    } else if (fine && f.ns == 2) {
+      for (int64_t t = 0; t < cnt; ++t)
+        for (int c = 0; c < b; ++c)
+          for (int q = 0; q < k; ++q)
+            Ba[(size_t)(t * b + c) * k + q] = f.user_B[(size_t)(members[m0 + t] * b + c) * k + q];
     } else if (fine) {
       const int d = f.dim;
       double cen[3] = {0, 0, 0};
@@ -209,6 +217,11 @@ void tentative(const std::vector<int32_t> &agg, int64_t nagg, int b, int k, bool
           for (int q = 0; q < k; ++q)
             Ba[(size_t)(t * b + c) * k + q] = B[(size_t)(members[m0 + t] * b + c) * k + q];
     }
+    if (fine && !f.dirichlet.empty())  // no nullspace component at a Dirichlet dof
+      for (int64_t t = 0; t < cnt; ++t)
+        for (int c = 0; c < b; ++c)
+          if (f.dirichlet[(size_t)members[m0 + t] * b + c])
+            for (int q = 0; q < k; ++q) Ba[(size_t)(t * b + c) * k + q] = 0.0;
     gs_qr(m, k, Ba, Q, R);
     for (int64_t t = 0; t < cnt; ++t) {
       const int64_t I = members[m0 + t];
@@ -428,7 +441,7 @@ void build_group(HGroup &g, const std::vector<HBsr> &diag, const std::vector<Fie
       fl.lam = power_lambda(fl.A, fl.dinv, seed);
       tm[0] += now_s() - t;
       t = now_s();
-      Graph G = strength_graph(fl.A, f.theta);
+      Graph G = strength_graph(fl.A, f.theta, fine ? f.fixed_nodes() : std::vector<uint8_t>());
       tm[1] += now_s() - t;
       t = now_s();
       aggregate(G, seed, fl.agg, fl.nagg);

@@ -16,6 +16,7 @@
 //   the aggregate centroid; lambda_max(D^-1 A) by 10 power iterations from a
 //   SplitMix64 start vector; P = (I - 4/(3 lambda) D^-1 A) P_tent; R = P^T.
 #pragma once
+#include <cstdint>
 #include <map>
 #include <utility>
 #include <vector>
@@ -27,10 +28,23 @@ namespace mfs {
 struct FieldInfo {
   int64_t nnodes = 0;
   int b = 1, dim = 3;
-  int ns = 0;  // 0 constants, 1 rigid-body modes
+  int ns = 0;  // 0 constants, 1 rigid-body modes, 2 the caller's vectors (user_B)
+  int ns_dim = 0;              // ns == 2: vectors per dof
+  std::vector<double> user_B;  // ns == 2: nnodes * b * ns_dim, dof-major
+  std::vector<uint8_t> dirichlet;  // empty or nnodes * b flags of eliminated Dirichlet dofs
   double theta = 0.0;
   std::vector<double> coords;
   bool pg = false;  // Petrov-Galerkin transfers (non-symmetric block)
+  // nodes whose every dof is a flagged Dirichlet dof (empty: none flagged)
+  std::vector<uint8_t> fixed_nodes() const {
+    std::vector<uint8_t> m;
+    if (dirichlet.empty()) return m;
+    m.assign(nnodes, 1);
+    for (int64_t I = 0; I < nnodes; ++I)
+      for (int c = 0; c < b; ++c)
+        if (!dirichlet[I * b + c]) m[I] = 0;
+    return m;
+  }
 };
 
 struct HLevelField {

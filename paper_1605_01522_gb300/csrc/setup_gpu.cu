@@ -643,14 +643,17 @@ __global__ void k_block_fro(BV A, double *__restrict__ fro, double *__restrict__
   }
 }
 
+// fixed (or null): nodes that keep no edge (every dof a Dirichlet dof)
 __global__ void k_strong(BV A, const double *__restrict__ fro, const double *__restrict__ dn, double theta,
-                         const int32_t *__restrict__ srp, int32_t *__restrict__ cnt, int32_t *__restrict__ sci) {
+                         const uint8_t *__restrict__ fixed, const int32_t *__restrict__ srp,
+                         int32_t *__restrict__ cnt, int32_t *__restrict__ sci) {
   const int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= A.nbr) return;
   int c = 0;
   for (int a = A.rp[I]; a < A.rp[I + 1]; ++a) {
     const int J = A.ci[a];
     if (J == I) continue;
+    if (fixed && (fixed[I] || fixed[J])) continue;
     if (fro[a] > theta * sqrt(dn[I] * dn[J])) {
       if (sci) sci[srp[I] + c] = J;
       ++c;
@@ -660,16 +663,16 @@ __global__ void k_strong(BV A, const double *__restrict__ fro, const double *__r
 }
 
 // node graph of strong connections, symmetrised (pattern only)
-DB strength(const DB &A, double theta) {
+DB strength(const DB &A, double theta, const uint8_t *fixed) {
   DVec<double> fro(std::max<int64_t>(1, A.nnzb)), dn(A.nbr, true);
   k_block_fro<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p);
   DB S;
   S.shape(1, 1, A.nbr, A.nbr);
   DVec<int32_t> cnt(A.nbr);
-  k_strong<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p, theta, nullptr, cnt.p, nullptr);
+  k_strong<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p, theta, fixed, nullptr, cnt.p, nullptr);
   S.nnzb = counts_to_rowptr(cnt.p, A.nbr, S.rp.p);
   S.ci.resize(S.nnzb);
-  k_strong<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p, theta, S.rp.p, cnt.p, S.ci.p);
+  k_strong<<<nblocks(A.nbr), kT, 0, gstream()>>>(view(A), fro.p, dn.p, theta, fixed, S.rp.p, cnt.p, S.ci.p);
   GS_CUDA(cudaGetLastError());
   DB ST = transpose(S, false);
   return merge(1.0, S, 1.0, ST, false);
@@ -851,11 +854,14 @@ __global__ void k_agg_flag(const int32_t *__restrict__ agg, int64_t n, int32_t *
 
 // One warp per aggregate: near-nullspace rows into Q (in the P_tent value
 // slots of the members), two-pass Gram-Schmidt, R into Bc.
-// kind: 0 constants, 1 rigid-body modes from coords (fine), 2 rows of Bprev.
+// kind: 0 constants, 1 rigid-body modes from coords (fine), 2 rows of Bprev
+// (coarse levels, or the caller's vectors on the fine level); rows of dofs
+// flagged in dmask (fine level, or null) are zero.
 __global__ void k_tentative(const int32_t *__restrict__ start, const int32_t *__restrict__ members, int64_t nagg,
                             int b, int k, int kind, int dim, const double *__restrict__ coords,
-                            const double *__restrict__ Bprev, const int32_t *__restrict__ ptrp,
-                            int32_t *__restrict__ ptci, double *__restrict__ ptv, double *__restrict__ Bc) {
+                            const double *__restrict__ Bprev, const uint8_t *__restrict__ dmask,
+                            const int32_t *__restrict__ ptrp, int32_t *__restrict__ ptci, double *__restrict__ ptv,
+                            double *__restrict__ Bc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t a = (int64_t)blockIdx.x * (blockDim.x >> 5) + warp;
   if (a >= nagg) return;
@@ -892,6 +898,7 @@ __global__ void k_tentative(const int32_t *__restrict__ start, const int32_t *__
         } else {
           val = Bprev[((int64_t)I * b + c) * k + q];
         }
+        if (dmask && dmask[(int64_t)I * b + c]) val = 0.0;
         ptv[((int64_t)ptrp[I] * b + c) * k + q] = val;
       }
   }
@@ -1017,7 +1024,13 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       sync();
       tm[0] += now_s() - t;
       t = now_s();
-      DB G = strength(fl.A, f.theta);
+      DVec<uint8_t> fixed, dmask;
+      if (fine && !f.dirichlet.empty()) {
+        const std::vector<uint8_t> fx = f.fixed_nodes();
+        fixed.upload(fx.data(), (int64_t)fx.size());
+        dmask.upload(f.dirichlet.data(), (int64_t)f.dirichlet.size());
+      }
+      DB G = strength(fl.A, f.theta, fixed.p);
       sync();
       tm[1] += now_s() - t;
       t = now_s();
@@ -1026,7 +1039,7 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       if (fl.nagg == 0) throw SetupError(-7, "aggregation produced no aggregate");
       t = now_s();
       const int b = fl.A.br;
-      const int k = fine ? (f.ns == 0 ? f.b : (f.dim == 2 ? 3 : 6)) : b;
+      const int k = fine ? (f.ns == 0 ? f.b : (f.ns == 2 ? f.ns_dim : (f.dim == 2 ? 3 : 6))) : b;
       const int64_t n = fl.A.nbr;
       DVec<int32_t> cnt(fl.nagg, true), start(fl.nagg + 1), fillc(fl.nagg, true), members(n), flg(n);
       k_agg_count<<<nblocks(n), kT, 0, gstream()>>>(fl.agg.p, n, cnt.p);
@@ -1045,12 +1058,14 @@ void build_group_gpu(HGroup &g, const std::vector<HBsr> &diag, const std::vector
       Pt.nnzb = counts_to_rowptr(flg.p, n, Pt.rp.p);
       Pt.ci.resize(Pt.nnzb);
       Pt.v.resize(Pt.nnzb * b * k);
-      DVec<double> coords;
+      DVec<double> coords, userB;
       if (fine && f.ns == 1) coords.upload(f.coords.data(), (int64_t)f.coords.size());
+      if (fine && f.ns == 2) userB.upload(f.user_B.data(), (int64_t)f.user_B.size());
       nxt[i].B.resize(fl.nagg * k * k);
-      const int kind = fine ? (f.ns == 0 ? 0 : 1) : 2;
+      const int kind = fine ? (f.ns == 0 ? 0 : (f.ns == 1 ? 1 : 2)) : 2;
       k_tentative<<<(unsigned)((fl.nagg + 3) / 4), 128, 0, gstream()>>>(start.p, members.p, fl.nagg, b, k, kind, f.dim, coords.p,
-                                                          fl.B.p, Pt.rp.p, Pt.ci.p, Pt.v.p, nxt[i].B.p);
+                                                          fine && f.ns == 2 ? userB.p : fl.B.p, dmask.p, Pt.rp.p,
+                                                          Pt.ci.p, Pt.v.p, nxt[i].B.p);
       GS_CUDA(cudaGetLastError());
       sync();
       tm[3] += now_s() - t;

@@ -1354,6 +1354,9 @@ struct FusedBatch {
   double *hb = nullptr, *hbpin = nullptr, *ypin = nullptr;  // Arnoldi sums (136 per system), y (64 per system)
   std::vector<double *> vin, zout;  // float64 systems: fixed preconditioner input / output
   cudaGraphExec_t exec = nullptr;
+  size_t nhead = 0, npre = 0, ntail = 0;  // merged launches per segment
+  int64_t ctas = 0;                       // CTAs of one replay
+  double build_ms = 0.0;
   FusedBatch() = default;
   FusedBatch(const FusedBatch &) = delete;
   ~FusedBatch() {
@@ -1480,6 +1483,10 @@ struct FusedBatch {
     for (auto &v : tail_at)
       for (auto &pr : v) pr.first = remap[pr.first];
     launches.swap(order);
+    this->nhead = nhead;
+    this->npre = npre;
+    ntail = ntail_end - nhead;
+    for (const Launch &L : launches) ctas += L.grid;
     MFS_CUDA(cudaMallocHost(&htab, std::max<size_t>(tab_bytes, 16)));
     std::memcpy(htab, tabs.data(), tab_bytes);
     dtab = ar.alloc<unsigned char>((int64_t)std::max<size_t>(tab_bytes, 16));
@@ -1537,7 +1544,14 @@ static FusedBatch *fused_for(mfs_handle *const *hv, int n) {
   for (auto &b : g_fused)
     if (b->nsys == n && std::equal(b->hs.begin(), b->hs.end(), hv)) return b.get();
   std::unique_ptr<FusedBatch> b(new FusedBatch());
+  const double t0 = now_ms();
   b->build(hv, n);
+  b->build_ms = now_ms() - t0;
+  if (hv[0]->prm.verbose)
+    fprintf(stderr,
+            "mfs fused batch: %d systems, %zu + %zu + %zu merged launches per iteration (heads, preconditioners, "
+            "Krylov steps), %lld CTAs per replay, %.1f KB patched per iteration, built in %.1f ms\n",
+            n, b->nhead, b->npre, b->ntail, (long long)b->ctas, b->patch_bytes / 1024.0, b->build_ms);
   if (g_fused.size() >= 4) g_fused.erase(g_fused.begin());
   g_fused.push_back(std::move(b));
   return g_fused.back().get();
@@ -1644,7 +1658,17 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
     }
   }
   dev::Recorder rec;
+  const bool verbose = hs[0]->prm.verbose != 0;
+  cudaEvent_t ga = nullptr, gb = nullptr;
+  if (verbose) {
+    MFS_CUDA(cudaEventCreate(&ga));
+    MFS_CUDA(cudaEventCreate(&gb));
+  }
+  double t_host = 0.0, t_graph = 0.0, t_cycle = 0.0, t_all = now_ms();
+  int replays = 0;
+  std::vector<int> live_per_replay;
   while (std::find(active.begin(), active.end(), 1) != active.end()) {
+    const double th = now_ms();
     for (int k = 0; k < ns; ++k) {
       B.hactive[k] = active[k];
       if (!active[k]) continue;
@@ -1657,8 +1681,19 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
     }
     MFS_CUDA(cudaMemcpyAsync(B.dtab, B.htab, B.patch_bytes, cudaMemcpyHostToDevice, s));
     MFS_CUDA(cudaMemcpyAsync(B.dactive, B.hactive, ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    t_host += now_ms() - th;
+    if (verbose) MFS_CUDA(cudaEventRecord(ga, s));
     MFS_CUDA(cudaGraphLaunch(B.exec, s));
+    if (verbose) MFS_CUDA(cudaEventRecord(gb, s));
     MFS_CUDA(cudaStreamSynchronize(s));
+    ++replays;
+    if (verbose) {
+      float ms = 0.f;
+      MFS_CUDA(cudaEventElapsedTime(&ms, ga, gb));
+      t_graph += ms;
+      live_per_replay.push_back((int)std::count(active.begin(), active.end(), 1));
+    }
+    const double tc = now_ms();
     std::vector<int> ending;
     for (int k = 0; k < ns; ++k) {
       if (!active[k]) continue;
@@ -1673,7 +1708,10 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
         ++j[k];
       }
     }
-    if (ending.empty()) continue;
+    if (ending.empty()) {
+      t_cycle += now_ms() - tc;
+      continue;
+    }
     // end of a cycle: x += Z y, true residual; stop or restart
     for (int k : ending) {
       mfs_handle *h = hs[k];
@@ -1695,6 +1733,17 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
         start_cycle(k, rn[k]);
       }
     }
+    t_cycle += now_ms() - tc;
+  }
+  if (verbose) {
+    cudaEventDestroy(ga);
+    cudaEventDestroy(gb);
+    std::string live;
+    for (size_t q = 0; q < live_per_replay.size(); q += 5) live += " " + std::to_string(live_per_replay[q]);
+    fprintf(stderr,
+            "mfs fused solve: %d replays, %.2f ms total: graphs %.2f ms (GPU), host recording/patching %.2f ms, "
+            "Givens + cycle ends %.2f ms; live systems every 5th replay:%s\n",
+            replays, now_ms() - t_all, t_graph, t_host, t_cycle, live.c_str());
   }
   for (int k = 0; k < ns; ++k)
     if (hostx[k]) MFS_CUDA(cudaMemcpyAsync(x[k], xx[k], hs[k]->n * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -2019,6 +2068,8 @@ void build_host(mfs_handle *h, const std::map<std::pair<int, int>, HBsr> &blocks
         h->host->schur_diag.push_back(M);
         FieldInfo fi = info[k];
         fi.ns = 0;
+        fi.user_B.clear();
+        fi.dirichlet.clear();
         sinfo.push_back(fi);
       } else {
         h->host->schur_off[{l2[k], l2[l]}] = M;
@@ -2209,8 +2260,20 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
         if (!f.coords || f.dim != f.dofs_per_node || (f.dim != 2 && f.dim != 3))
           throw SetupError(MFS_ERR_INVALID, "rigid-body modes need coords and dofs_per_node == dim in {2,3}");
         info[i].coords.assign(f.coords, f.coords + f.nnodes * f.dim);
+      } else if (f.nullspace == MFS_NS_USER) {
+        auto shape_ok = [](int v) { return v == 1 || v == 2 || v == 3 || v == 6; };
+        if (!f.ns_user || !shape_ok(f.ns_dim) || !shape_ok(f.dofs_per_node))
+          throw SetupError(MFS_ERR_INVALID, "MFS_NS_USER needs ns_user and ns_dim, dofs_per_node in {1, 2, 3, 6}");
+        info[i].ns_dim = f.ns_dim;
+        info[i].user_B.assign(f.ns_user, f.ns_user + f.nnodes * f.dofs_per_node * f.ns_dim);
+        for (double v : info[i].user_B)
+          if (!std::isfinite(v)) throw SetupError(MFS_ERR_INVALID, "non-finite value in ns_user");
       } else if (f.nullspace != MFS_NS_CONST) {
         throw SetupError(MFS_ERR_INVALID, "bad nullspace kind");
+      }
+      if (f.dirichlet) {
+        info[i].dirichlet.resize(f.nnodes * f.dofs_per_node);
+        for (size_t d = 0; d < info[i].dirichlet.size(); ++d) info[i].dirichlet[d] = f.dirichlet[d] ? 1 : 0;
       }
       h->fsize.push_back(f.nnodes * f.dofs_per_node);
       h->foff[i + 1] = h->foff[i] + h->fsize[i];
@@ -2228,6 +2291,26 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     }
     for (int i = 0; i < nfields; ++i)
       if (!hb.count({i, i})) throw SetupError(MFS_ERR_INVALID, "missing diagonal block");
+    // a flagged Dirichlet dof's row is the identity across its block row
+    for (int i = 0; i < nfields; ++i) {
+      const std::vector<uint8_t> &dm = info[i].dirichlet;
+      if (dm.empty()) continue;
+      for (auto &kv : hb) {
+        if (kv.first.first != i) continue;
+        const HBsr &B = kv.second;
+        const bool diag = kv.first.second == i;
+        for (int64_t I = 0; I < B.nbr; ++I)
+          for (int64_t a = B.rp[I]; a < B.rp[I + 1]; ++a)
+            for (int c = 0; c < B.br; ++c) {
+              if (!dm[I * B.br + c]) continue;
+              for (int q = 0; q < B.bc; ++q) {
+                const double want = diag && B.ci[a] == I && q == c ? 1.0 : 0.0;
+                if (B.v[(a * B.br + c) * B.bc + q] != want)
+                  throw SetupError(MFS_ERR_INVALID, "a flagged Dirichlet dof's row is not an identity row");
+              }
+            }
+      }
+    }
     // one upload of the input blocks, shared by the GPU setup and the fine layouts
     std::unique_ptr<Arena> raw_arena;
     std::map<std::pair<int, int>, RawDev> rd;

@@ -83,6 +83,8 @@ class Field:
     theta: float = 0.0     # strength-of-connection threshold used for this field
     dirichlet_nodes: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int64))
     petrov_galerkin: bool = False  # non-symmetric block: Petrov-Galerkin transfers (R != P^T)
+    ns_user: np.ndarray = None     # nullspace "user": caller's near-nullspace vectors (ndofs x k)
+    dirichlet_dofs: np.ndarray = None  # optional per-dof flags of eliminated Dirichlet dofs (bool)
 
     @property
     def ndofs(self) -> int:

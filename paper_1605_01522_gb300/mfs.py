@@ -18,7 +18,7 @@ MAX_FIELDS = 8
 OK, ERR_INVALID, ERR_CUDA, ERR_OOM, ERR_SINGULAR, ERR_NOT_CONVERGED, ERR_BREAKDOWN, ERR_SETUP = 0, -1, -2, -3, -4, -5, -6, -7
 BGS_AMG, SIMPLE, AMG_BGS, AMG_SIMPLE, BGS_GS = 0, 1, 2, 3, 4
 BWD, FWD, SYM = 0, 1, 2
-NS_CONST, NS_RBM = 0, 1
+NS_CONST, NS_RBM, NS_USER = 0, 1, 2
 FP64, FP32P = 0, 1
 ABSROWSUM, DIAG = 0, 1
 CHEBYSHEV, JACOBI, GS = 0, 1, 2
@@ -61,7 +61,8 @@ class Block(C.Structure):
 class FieldDesc(C.Structure):
     _fields_ = [("nnodes", C.c_int64), ("dofs_per_node", C.c_int), ("dim", C.c_int),
                 ("coords", C.POINTER(C.c_double)), ("nullspace", C.c_int),
-                ("strength_theta", C.c_double), ("petrov_galerkin", C.c_int)]
+                ("strength_theta", C.c_double), ("petrov_galerkin", C.c_int),
+                ("ns_user", C.POINTER(C.c_double)), ("ns_dim", C.c_int), ("dirichlet", C.POINTER(C.c_uint8))]
 
 
 class Params(C.Structure):
@@ -273,9 +274,20 @@ class Solver:
         for i, f in enumerate(system.fields):
             co = np.ascontiguousarray(f.coords, np.float64)
             keep.append(co)
-            fields[i] = FieldDesc(f.nnodes, f.b, f.dim, co.ctypes.data_as(C.POINTER(C.c_double)),
-                                  NS_RBM if f.nullspace == "rbm" else NS_CONST, f.theta,
-                                  1 if getattr(f, "petrov_galerkin", False) else 0)
+            kind = {"rbm": NS_RBM, "user": NS_USER}.get(f.nullspace, NS_CONST)
+            nsu, nsd = None, 0
+            if kind == NS_USER:
+                nsu = np.ascontiguousarray(f.ns_user, np.float64)
+                nsd = int(nsu.shape[1])
+                keep.append(nsu)
+            dm = getattr(f, "dirichlet_dofs", None)
+            if dm is not None:
+                dm = np.ascontiguousarray(dm, np.uint8)
+                keep.append(dm)
+            fields[i] = FieldDesc(f.nnodes, f.b, f.dim, co.ctypes.data_as(C.POINTER(C.c_double)), kind, f.theta,
+                                  1 if getattr(f, "petrov_galerkin", False) else 0,
+                                  nsu.ctypes.data_as(C.POINTER(C.c_double)) if nsu is not None else None, nsd,
+                                  dm.ctypes.data_as(C.POINTER(C.c_uint8)) if dm is not None else None)
         h = C.c_void_p()
         rc = lib.mfs_setup(blocks, len(system.blocks), fields, system.nfields, C.byref(prm), C.byref(h))
         if rc != OK:
