@@ -650,7 +650,9 @@ def run_batch(args, rank, world):
     t0 = time.perf_counter()
     sizes, mats, rhs = inputs.batch_workload(args.nsys, 12, 48, 3)
     t1 = time.perf_counter()
-    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, **solver_kw(args)) for ne, sy in mats.items()}
+    # layouts tuned for throughput (many systems on the GPU at once)
+    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, layout_tune=1, **solver_kw(args))
+            for ne, sy in mats.items()}
     solvers, used = [], set()
     for ne in sizes.tolist():
         solvers.append(base[ne] if ne not in used else base[ne].clone())

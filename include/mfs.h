@@ -169,6 +169,14 @@ typedef struct {
   int rows_split;                    /* threads per block row of the float64 coupled matvec
                                         (merged row layout): 0 (default) = timed at setup
                                         among 1, 2 and 4; or 1, 2, 4 to fix it */
+  int layout_tune;                   /* sparse layouts of matrices with >= 2048 block rows:
+                                        0 (default) = the fastest of SELL-32 (2, 4 or 8
+                                        slots in flight) and one warp per row, each timed
+                                        alone (best for one solve at a time: a mid-size
+                                        matrix cannot fill the GPU by itself); 1 = the
+                                        fastest SELL-32 variant only (best when many
+                                        systems run together, mfs_solve_batch, where the
+                                        GPU is full and throughput counts) */
 } mfs_params;
 
 typedef struct {

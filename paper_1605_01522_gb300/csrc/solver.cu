@@ -296,6 +296,8 @@ template <typename T> static float time_spmv(const dev::Sell &S, cudaStream_t st
 
 static std::mutex g_tune_mu;
 static std::map<std::tuple<int, int, int64_t, int64_t, int>, int> g_tune;
+// mfs_params.layout_tune of the setup running on this thread
+static thread_local int g_layout_tune = 0;
 
 // Layout candidates of the autotuner: 0 SELL-32 with 2 slots in flight,
 // 1 with 4, 2 plain BSR with one warp per row, 3 SELL-32 with 8 slots in
@@ -308,7 +310,8 @@ static int tune_pick(const dev::Sell &a, const dev::Sell &b, bool want32, cudaSt
   float t[4];
   t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
   t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
-  t[2] = want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st);
+  // throughput tuning leaves the one-warp-per-row layout out
+  t[2] = g_layout_tune == 1 ? 1e30f : (want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st));
   t[3] = !small ? 1e30f : (want32 ? time_spmv<float>(a8, st) : time_spmv<double>(a8, st));
   int best = 0;
   for (int c = 1; c < 4; ++c)
@@ -336,7 +339,7 @@ static dev::Sell tune_keep(Arena &ar, dev::Sell &a, dev::Sell &b, int best) {
 
 static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32) {
   if (A.nbr < kTuneMinRows) return upload_layout(ar, A, want64, want32, 1);
-  const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb(), want32 ? 1 : 0);
+  const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb(), (want32 ? 1 : 0) + 2 * g_layout_tune);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
@@ -373,7 +376,7 @@ static dev::Sell upload_sell(Arena &ar, const HBsr &A, bool want64, bool want32)
 static dev::Sell upload_sell_dev(Arena &ar, const RawDev &A, bool want64, bool want32, cudaStream_t st) {
   const RawDev *src[1] = {&A};
   if (A.nbr < kTuneMinRows) return upload_layout_dev(ar, src, 1, want64, want32, 1, st);
-  const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb, want32 ? 1 : 0);
+  const auto key = std::make_tuple(A.br, A.bc, (int64_t)A.nbr, (int64_t)A.nnzb, (want32 ? 1 : 0) + 2 * g_layout_tune);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune.find(key);
@@ -1527,8 +1530,10 @@ struct FusedBatch {
 
 // Process-wide cache of fused batches by their handle list (a batch holds
 // the handles' device addresses; mfs_free drops every batch of a handle).
+// (never destroyed itself: at process exit the CUDA runtime may already be
+// gone, so the batches' streams and pinned buffers are left to the OS)
 static std::mutex g_fused_mu;
-static std::vector<std::unique_ptr<FusedBatch>> g_fused;
+static std::vector<std::unique_ptr<FusedBatch>> &g_fused = *new std::vector<std::unique_ptr<FusedBatch>>();
 
 static void drop_fused(const mfs_handle *h) {
   std::lock_guard<std::mutex> lock(g_fused_mu);
@@ -2228,7 +2233,8 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       (p.precond == MFS_BGS_GS && p.smoother != MFS_GS) ||
       (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
       (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS) ||
-      (p.rows_split != 0 && p.rows_split != 1 && p.rows_split != 2 && p.rows_split != 4))
+      (p.rows_split != 0 && p.rows_split != 1 && p.rows_split != 2 && p.rows_split != 4) ||
+      (p.layout_tune != 0 && p.layout_tune != 1))
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;
@@ -2238,6 +2244,10 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
   }
   const double t0 = now_ms();
   std::unique_ptr<mfs_handle> h(new mfs_handle());
+  struct TuneMode {  // the layout tuning mode of this setup, for this thread
+    explicit TuneMode(int m) { g_layout_tune = m; }
+    ~TuneMode() { g_layout_tune = 0; }
+  } tune_mode(p.layout_tune);
   try {
     h->prm = p;
     h->nf = nfields;

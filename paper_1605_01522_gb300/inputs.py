@@ -41,7 +41,7 @@ import itertools
 import numpy as np
 
 __all__ = [
-    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d", "constrained_box", "fsi_box",
+    "BSR", "Field", "BlockSystem", "thermo_elastic_2d", "coupled_box_3d", "constrained_box", "fsi_box", "roller_box",
     "batch_sizes_log_uniform", "batch_workload", "system_rhs",
 ]
 
@@ -374,6 +374,66 @@ def coupled_box_3d(ne=64, nfields=3, alpha=1e-2, beta=1e-3, E=1.0, nu=0.3, k=1.0
     return BlockSystem(fields, blocks, _seeded_rhs(fields, seed, dnodes),
                        name=f"coupled_box_3d_ne{ne}_f{nfields}",
                        meta=dict(ne=ne, nfields=nfields, alpha=alpha, seed=seed))
+
+
+def _eliminate_dofs(grid, blocks, masks):
+    """Symmetric elimination of single dofs: masks[i] flags the dofs of field
+    i (per dof, node-major); their rows and columns are zeroed in every block
+    and the diagonal entry of A_ii set to 1."""
+    rows = np.repeat(np.arange(grid.nnodes), np.diff(grid.rowptr))
+    for (i, j), m in blocks.items():
+        ri = masks[i].reshape(grid.nnodes, m.br)[rows]        # (nnzb, br)
+        cj = masks[j].reshape(grid.nnodes, m.bc)[grid.colind]  # (nnzb, bc)
+        m.vals[ri[:, :, None] | cj[:, None, :]] = 0.0
+        if i == j:
+            on = rows == grid.colind
+            for c in range(m.br):
+                sel = on & ri[:, c]
+                m.vals[sel, c, c] = 1.0
+
+
+def roller_box(ne=12, user_nullspace=False, seed=6):
+    """2-field 3D box (elasticity + heat, the couplings of coupled_box_3d)
+    with symmetry conditions: on each face x_d = 0 only the displacement
+    component u_d is held (so edge and corner nodes hold 2 or 3 components),
+    T = 0 on x = 0.  The held dofs are eliminated symmetrically and flagged
+    per dof (Field.dirichlet_dofs).  user_nullspace: the elasticity field
+    gives its rigid-body modes (rotations about the origin) as caller
+    vectors (nullspace "user") instead of the built-in kind."""
+    g = _Grid(ne, 3)
+    h = 1.0 / ne
+    Ke, Kl, Me, Ce = q1_element_matrices(3, h)
+    blocks = {
+        (0, 0): g.bsr(g.assemble(Ke, 3, 3), 3, 3),
+        (1, 1): g.bsr(g.assemble(Kl + Me / 0.1, 1, 1), 1, 1),
+        (0, 1): g.bsr(g.assemble(1e-2 * Ce, 3, 1), 3, 1),
+        (1, 0): g.bsr(g.assemble(1e-3 * Ce.T, 1, 3), 1, 3),
+    }
+    m0 = np.zeros((g.nnodes, 3), bool)
+    for d in range(3):
+        m0[g.ijk[:, d] == 0, d] = True
+    m1 = g.ijk[:, 0] == 0
+    masks = [m0.ravel(), m1.copy()]
+    _eliminate_dofs(g, blocks, masks)
+    fields = [Field("elasticity", 3, g.nnodes, 3, g.coords, "rbm", 0.0, np.zeros(0, np.int64)),
+              Field("heat", 1, g.nnodes, 3, g.coords, "const", 0.0, np.nonzero(m1)[0])]
+    fields[0].dirichlet_dofs = masks[0]
+    fields[1].dirichlet_dofs = masks[1]
+    if user_nullspace:
+        x, y, z = g.coords[:, 0], g.coords[:, 1], g.coords[:, 2]
+        B = np.zeros((g.nnodes, 3, 6))
+        B[:, 0, 0] = B[:, 1, 1] = B[:, 2, 2] = 1.0
+        B[:, 1, 3], B[:, 2, 3] = -z, y
+        B[:, 0, 4], B[:, 2, 4] = z, -x
+        B[:, 0, 5], B[:, 1, 5] = -y, x
+        fields[0].nullspace = "user"
+        fields[0].ns_user = B.reshape(3 * g.nnodes, 6)
+    rng = np.random.default_rng(seed)
+    rhs = rng.standard_normal(4 * g.nnodes)
+    rhs[:3 * g.nnodes][masks[0]] = 0.0
+    rhs[3 * g.nnodes:][masks[1]] = 0.0
+    return BlockSystem(fields, blocks, rhs, name=f"roller_box_ne{ne}{'_user' if user_nullspace else ''}",
+                       meta=dict(ne=ne, seed=seed))
 
 
 def constrained_box(ne=64, nfields=3, patches=(2, 2), seed=5, **kw):

@@ -44,6 +44,10 @@ def _small(name):
         return inputs.constrained_box(ne=9), dict(max_levels=3, coarse_max=100)
     if name == "oseen":
         return inputs.fsi_box(ne=8, wind=(0.1, 0.05, 0.0)), dict(max_levels=3, coarse_max=100)
+    if name == "roll":
+        return inputs.roller_box(ne=9), dict(max_levels=3, coarse_max=100)
+    if name == "rollu":
+        return inputs.roller_box(ne=9, user_nullspace=True), dict(max_levels=3, coarse_max=100)
     raise KeyError(name)
 
 
@@ -119,7 +123,12 @@ PG = [("oseen", "simple", dict(simple_group=[0, 0, 0, 1], simple_approx="diag"))
       ("oseen", "bgs_amg", {})]
 
 
-@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED + GS + PG)
+# symmetry conditions flagged per dof (1-3 held components per node), with the
+# built-in or a caller-supplied rigid-body nullspace
+ROLLER = [("roll", "bgs_amg", {}), ("rollu", "bgs_amg", {}), ("rollu", "amg_bgs", {}), ("roll", "simple", {})]
+
+
+@pytest.mark.parametrize("name,pc,extra", CASES + AMG_SIMPLE + NESTED + GS + PG + ROLLER)
 def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
     s, kw = _small(name)
     with mfs.Solver(s, precond=pc, **kw, **extra) as lib:
@@ -133,7 +142,7 @@ def test_apply_fp64_matches_oracle_on_same_hierarchy(name, pc, extra):
 
 
 @pytest.mark.parametrize("name,pc,extra", [c for c in CASES if c[0] != "3d2" or c[1] == "simple"][:8] + FSI
-                         + AMG_SIMPLE[:4] + NESTED + GS + PG[:2])
+                         + AMG_SIMPLE[:4] + NESTED + GS + PG[:2] + ROLLER)
 def test_solve_fp64_iterations_match_oracle(name, pc, extra):
     s, kw = _small(name)
     ro, D = _oracle_solve(s, kw, pc, extra)

@@ -28,6 +28,9 @@ SYSTEMS = {
     "2d": (lambda: inputs.thermo_elastic_2d(ne=20), dict(max_levels=3, coarse_max=0)),
     "3d3": (lambda: inputs.coupled_box_3d(ne=11, nfields=3), dict(max_levels=4, coarse_max=100)),
     "3d2": (lambda: inputs.coupled_box_3d(ne=17, nfields=2), dict(max_levels=4, coarse_max=200)),
+    # per-dof Dirichlet flags (symmetry conditions), built-in / caller rigid-body modes
+    "roll": (lambda: inputs.roller_box(ne=13), dict(max_levels=4, coarse_max=100)),
+    "rollu": (lambda: inputs.roller_box(ne=13, user_nullspace=True), dict(max_levels=4, coarse_max=100)),
 }
 
 

@@ -198,3 +198,52 @@ def test_setup_rejects_bad_input():
         mfs.Solver(s, setup_only=1, precond="bgs_gs")  # needs the Gauss-Seidel smoother
     with pytest.raises(mfs.MfsError):
         mfs.Solver(s, setup_only=1, smoother="gs", gs_omega=2.0)
+
+
+@pytest.mark.parametrize("user", [False, True])
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs"])
+def test_dirichlet_flags_and_user_nullspace_match_oracle(user, pc):
+    """Symmetry conditions (1-3 held components per node) flagged per dof,
+    rigid-body modes built in or given by the caller: aggregates, P, R and
+    the Galerkin blocks of the host setup equal the oracle's; flagged dofs
+    have zero prolongator rows."""
+    s = inputs.roller_box(ne=7, user_nullspace=user)
+    kw = dict(max_levels=3, coarse_max=100)
+    lib = mfs.Solver(s, precond=pc, setup_only=1, seed=7, **kw)
+    A = s.scipy_blocks()
+    specs = [amg.FieldSpec.of(f) for f in s.fields]
+    assert specs[0].dirichlet is not None and (specs[0].kind == "user") == user
+    M = precond.Preconditioner(A, specs, precond.Params(pc, seed=7, **kw))
+    lv = M.groups[0].levels
+    assert lib.num_levels(0) == len(lv) == 3
+    for l in range(len(lv)):
+        for i in range(s.nfields):
+            assert _rel(lib.export_csr("A", 0, l, i, i), lv[l][i].A) < TOL
+            if l < len(lv) - 1:
+                assert np.array_equal(lib.export_array("agg", 0, l, i), lv[l][i].agg)
+                P = lib.export_csr("P", 0, l, i)
+                assert _rel(P, lv[l][i].P) < TOL
+                if l == 0:
+                    assert abs(P[np.nonzero(s.fields[i].dirichlet_dofs)[0]]).max() == 0.0
+    # the corner node holds all three components and is left unaggregated
+    assert lib.export_array("agg", 0, 0, 0)[0] == -1
+    lib.close()
+
+
+def test_dirichlet_flag_on_a_non_identity_row_is_refused():
+    s = inputs.coupled_box_3d(ne=4, nfields=2)
+    m = np.zeros(s.fields[0].ndofs, bool)
+    m[3 * 31 + 1] = True  # node (1, 1, 1), interior: its row is not an identity row
+    s.fields[0].dirichlet_dofs = m
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(s, setup_only=1, max_levels=2, coarse_max=10)
+    assert e.value.code == mfs.ERR_INVALID and "identity" in str(e.value)
+
+
+def test_user_nullspace_shape_is_checked():
+    s = inputs.coupled_box_3d(ne=4, nfields=2)
+    s.fields[1].nullspace = "user"
+    s.fields[1].ns_user = np.ones((s.fields[1].ndofs, 4))  # 4 vectors: no 1x4 block kernels
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(s, setup_only=1, max_levels=2, coarse_max=10)
+    assert e.value.code == mfs.ERR_INVALID
