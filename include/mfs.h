@@ -221,15 +221,17 @@ int mfs_clone(const struct mfs_handle *src, void *stream, struct mfs_handle **ou
  * of one setup allowed; any sizes, field counts, preconditioners and
  * precisions), each A_k x_k = rhs_k to tol as mfs_solve does; rhs / x host
  * or device.  Not in the paper: it batches many of the Sec. 3-4 solves.
- *  nthreads == 0: fused.  The systems' FGMRES iterations advance together;
+ *  nthreads <= 0: fused.  The systems' FGMRES iterations advance together;
  *    every step of an iteration (each kernel of each system's preconditioner
  *    application, matvec and Arnoldi pass) runs as ONE launch over all
- *    systems that take that kernel, driven by per-system argument tables,
- *    and the steps of an iteration are one CUDA graph replayed once per
- *    iteration on a library stream; systems that finish stop taking part.
- *    The graph and tables are built on the first call with a handle list
- *    and kept for later calls with the same list (until one of its handles
- *    is freed).
+ *    systems of a group that take that kernel, driven by per-system argument
+ *    tables, and the steps of an iteration are one CUDA graph replayed once
+ *    per iteration on a library stream; systems that finish stop taking
+ *    part.  The systems are split into -nthreads groups of similar sizes
+ *    (0: one group per 32 systems, at most 8) whose launches run
+ *    concurrently.  The graph and tables are built on the first call with a
+ *    handle list and kept for later calls with the same list and grouping
+ *    (until one of its handles is freed).
  *  nthreads > 0: that many host threads each drive one handle's FGMRES at
  *    a time on the handle's own stream, so the systems' kernels overlap.
  * Either way every result is bit-for-bit the one mfs_solve gives for that
@@ -258,7 +260,8 @@ int mfs_dot(struct mfs_handle *h, const double *x, const double *y, double *out)
  * roofline of the float64 kernels (the coupled matvec and the Arnoldi
  * passes of Sec. 3.1's GMRES), which GB300's FP64 pipe bounds.  Launches
  * independent FMA chains on every SM on `stream` (NULL = legacy default
- * stream), timed by CUDA events, best of 5 after one warm-up; synchronous.
+ * stream) in five launch shapes (8-32 chains per thread, 256-1024 threads
+ * per CTA), timed by CUDA events, best rate after a warm-up; synchronous.
  * Errors: MFS_ERR_INVALID for a NULL output, MFS_ERR_CUDA. */
 int mfs_fp64_rate(double *tflops, void *stream);
 

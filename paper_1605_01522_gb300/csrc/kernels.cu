@@ -6,9 +6,11 @@
 // per slot and every reduction has a fixed order.
 #include "kernels.cuh"
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <mutex>
+#include <type_traits>
 
 namespace mfs {
 namespace dev {
@@ -70,8 +72,19 @@ __global__ void __launch_bounds__(K::kMaxThreads) k_solo(const __grid_constant__
   K::run(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
+// CTAs per SM the multi-system form of K must fit (K::kMinBlocks, default 1):
+// its arguments come from a table instead of the constant bank, which costs
+// registers; the one-thread-per-row SELL kernels are held to the 32 registers
+// of their single-system form so that as many CTAs stay resident
+template <class K, class = void> struct MinBlocks {
+  static constexpr int value = 1;
+};
+template <class K> struct MinBlocks<K, std::void_t<decltype(K::kMinBlocks)>> {
+  static constexpr int value = K::kMinBlocks;
+};
+
 template <class K>
-__global__ void __launch_bounds__(K::kMaxThreads)
+__global__ void __launch_bounds__(K::kMaxThreads, MinBlocks<K>::value)
 k_multi(const typename K::Args *__restrict__ tab, const MsBlock *__restrict__ map, const int *__restrict__ active) {
   const MsBlock m = map[blockIdx.x];
   if (active != nullptr && active[m.g] == 0) return;
@@ -396,6 +409,7 @@ __device__ __forceinline__ void d_spmv(int64_t nbr, const int32_t *__restrict__ 
 template <int BR, int BC, typename T, int U>
 struct KSpmvSell {
   static constexpr int kMaxThreads = kThreads;
+  static constexpr int kMinBlocks = BR * BC <= 9 ? 8 : 1;  // multi-system form: <= 32 registers
   struct Args {
     int64_t nbr;
     const int32_t *sp;
@@ -512,6 +526,7 @@ __device__ __forceinline__ void d_smooth(int64_t nbr, const int32_t *__restrict_
 template <int BR, typename T, int U>
 struct KSmoothSell {
   static constexpr int kMaxThreads = kThreads;
+  static constexpr int kMinBlocks = BR <= 3 ? 8 : 1;  // multi-system form: <= 32 registers
   struct Args {
     int64_t nbr;
     const int32_t *sp;
@@ -1199,49 +1214,59 @@ inline unsigned ew_grid(int64_t n) {
   return (unsigned)(g > 0 ? g : 1);
 }
 
-// FP64 FMA throughput probe: kFmaChains independent chains a = a * m + c per
-// thread; the sum is stored only when it equals a value it cannot take
-// (m, c are runtime values), so no chain can be dropped by the compiler.
-constexpr int kFmaChains = 8;
+// FP64 FMA throughput probe: C independent chains a = a * m + c per thread;
+// the sum is stored only when it equals a value it cannot take (m, c are
+// runtime values), so no chain can be dropped by the compiler.
 __device__ double g_fp64_sink;
-__global__ void __launch_bounds__(256) k_fp64_rate(int iters, double m, double c) {
-  double a[kFmaChains];
+template <int C>
+__global__ void __launch_bounds__(1024) k_fp64_rate(int iters, double m, double c) {
+  double a[C];
 #pragma unroll
-  for (int k = 0; k < kFmaChains; ++k) a[k] = 1e-3 * threadIdx.x + k;
+  for (int k = 0; k < C; ++k) a[k] = 1e-3 * threadIdx.x + k;
   for (int it = 0; it < iters; ++it)
 #pragma unroll
-    for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], m, c);
+    for (int k = 0; k < C; ++k) a[k] = fma(a[k], m, c);
   double s = 0.0;
 #pragma unroll
-  for (int k = 0; k < kFmaChains; ++k) s += a[k];
+  for (int k = 0; k < C; ++k) s += a[k];
   if (s == -12345.678) g_fp64_sink = s;
 }
 
 }  // namespace
 
+// best rate over a few launch shapes (chains per thread, CTA size, CTAs per
+// SM): the highest FMA throughput the part delivers, not one shape's
 double fp64_rate(cudaStream_t s) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return -1.0;
-  const int ctas = sms * 8, threads = 256, iters = 4096;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return -1.0;
-  float best = 1e30f;
+  struct Shape {
+    int chains, threads, per_sm;
+  };
+  const Shape shapes[] = {{8, 256, 8}, {16, 256, 8}, {16, 512, 4}, {32, 256, 4}, {8, 1024, 2}};
+  double best = 0.0;
   bool ok = true;
-  for (int r = 0; r < 6 && ok; ++r) {
-    ok = cudaEventRecord(e0, s) == cudaSuccess;
-    k_fp64_rate<<<ctas, threads, 0, s>>>(iters, 0.999999, 1e-7);
-    ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
-    float ms = 0.f;
-    ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
-    if (ok && r > 0 && ms < best) best = ms;  // the first launch is a warm-up
+  for (const Shape &sh : shapes) {
+    const int ctas = sms * sh.per_sm, iters = 65536 / sh.chains;
+    for (int r = 0; r < 4 && ok; ++r) {
+      ok = cudaEventRecord(e0, s) == cudaSuccess;
+      if (sh.chains == 8) k_fp64_rate<8><<<ctas, sh.threads, 0, s>>>(iters, 0.999999, 1e-7);
+      else if (sh.chains == 16) k_fp64_rate<16><<<ctas, sh.threads, 0, s>>>(iters, 0.999999, 1e-7);
+      else k_fp64_rate<32><<<ctas, sh.threads, 0, s>>>(iters, 0.999999, 1e-7);
+      ok = ok && cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+      float ms = 0.f;
+      ok = ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+      const double flops = 2.0 * sh.chains * (double)iters * sh.threads * ctas;
+      if (ok && r > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3) / 1e12);  // r = 0 warms up
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!ok || cudaGetLastError() != cudaSuccess) return -1.0;
-  const double flops = 2.0 * kFmaChains * (double)iters * threads * ctas;
-  return flops / (best * 1e-3) / 1e12;
+  return best;
 }
 
 #define MFS_BLOCK_DISPATCH(BRV, BCV, CALL)                                      \

@@ -173,8 +173,8 @@ void sell_fill(const int32_t *rp, const int32_t *ci, int nsrc, const double *v0,
                const double *v2, const int *bcs, int br, int64_t nbr, const int32_t *sp, int32_t *col,
                double *v64, float *v32, cudaStream_t s);
 
-// Measured FP64 FMA rate of this device in TFLOP/s (best of 5 timed launches
-// of independent FMA chains on every SM, CUDA events on s); < 0 on error.
+// Measured FP64 FMA rate of this device in TFLOP/s (independent FMA chains
+// on every SM, best over a few launch shapes, CUDA events on s); < 0 on error.
 double fp64_rate(cudaStream_t s);
 
 // elementwise helpers

@@ -1345,6 +1345,7 @@ struct FusedBatch {
     size_t smem = 0;        // largest entry's dynamic shared memory
     size_t tab = 0, map = 0, asz = 0;
     int nent = 0;
+    std::vector<int> sys;  // the system of each entry
   };
   std::vector<Launch> launches;  // in issue order: heads, preconditioners, tails
   // per system: (launch, entry) of each of its head / tail launches
@@ -1403,14 +1404,22 @@ struct FusedBatch {
     dev::set_recorder(nullptr);
   }
 
-  // merge one segment; its launches go to `launches`, its tables at the
-  // current end of the table layout
+  // merge one segment group by group; its launches go to `launches`, its
+  // tables at the current end of the table layout
   void add_segment(std::vector<dev::Recorder> &recs, std::vector<std::vector<std::pair<int, int>>> *at,
-                   std::vector<unsigned char> &tabs, std::vector<dev::MsBlock> &maps) {
-    std::vector<const std::vector<dev::RecOp> *> seqs;
-    for (auto &r : recs) seqs.push_back(&r.ops);
+                   std::vector<unsigned char> &tabs, std::vector<dev::MsBlock> &maps,
+                   const std::vector<std::vector<int>> &sysgroups) {
     std::vector<std::vector<std::pair<int, int>>> groups;
-    merge_sequences(seqs, groups);
+    for (const auto &members : sysgroups) {
+      std::vector<const std::vector<dev::RecOp> *> seqs;
+      for (int k : members) seqs.push_back(&recs[k].ops);
+      std::vector<std::vector<std::pair<int, int>>> g;
+      merge_sequences(seqs, g);
+      for (auto &grp : g) {
+        for (auto &e : grp) e.first = members[e.first];
+        groups.push_back(std::move(grp));
+      }
+    }
     if (at) {
       at->assign(nsys, {});
       for (int k = 0; k < nsys; ++k) (*at)[k].resize(recs[k].ops.size());
@@ -1433,14 +1442,41 @@ struct FusedBatch {
         L.grid += op.grid;
         L.smem = std::max(L.smem, op.smem);
         if (at) (*at)[grp[e].first][grp[e].second] = {(int)launches.size(), (int)e};
+        L.sys.push_back(grp[e].first);
       }
       launches.push_back(std::move(L));
     }
   }
 
-  void build(mfs_handle *const *hv, int n) {
+  // systems in `ngroups` groups of about equal dof totals, each of systems
+  // of similar size (sorted by size, cut into consecutive runs): the
+  // launches of one group are merged; different groups' launches run
+  // concurrently (independent chains of the graph)
+  std::vector<std::vector<int>> make_groups(int ngroups) const {
+    std::vector<int> order(nsys);
+    for (int k = 0; k < nsys; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
+    double total = 0.0;
+    for (int k = 0; k < nsys; ++k) total += (double)hs[k]->n;
+    std::vector<std::vector<int>> g(1);
+    double acc = 0.0;
+    for (int k : order) {
+      if (!g.back().empty() && acc >= total * (double)g.size() / ngroups && (int)g.size() < ngroups)
+        g.emplace_back();
+      g.back().push_back(k);
+      acc += (double)hs[k]->n;
+    }
+    for (auto &m : g) std::sort(m.begin(), m.end());
+    return g;
+  }
+
+  int ngroups_used = 1;
+
+  void build(mfs_handle *const *hv, int n, int ngroups) {
     hs.assign(hv, hv + n);
     nsys = n;
+    ngroups_used = std::max(1, std::min(ngroups, n));
+    const std::vector<std::vector<int>> sysgroups = make_groups(ngroups_used);
     MFS_CUDA(cudaSetDevice(hs[0]->device));
     MFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     vin.assign(nsys, nullptr);
@@ -1464,12 +1500,12 @@ struct FusedBatch {
     // tables of the per-iteration launches first (one upload per iteration)
     std::vector<unsigned char> tabs;
     std::vector<dev::MsBlock> maps;
-    add_segment(heads, &head_at, tabs, maps);
+    add_segment(heads, &head_at, tabs, maps, sysgroups);
     const size_t nhead = launches.size();
-    add_segment(tails, &tail_at, tabs, maps);
+    add_segment(tails, &tail_at, tabs, maps, sysgroups);
     patch_bytes = tabs.size();
     const size_t ntail_end = launches.size();
-    add_segment(pre, nullptr, tabs, maps);
+    add_segment(pre, nullptr, tabs, maps, sysgroups);
     tab_bytes = tabs.size();
     // issue order: heads, preconditioners, tails
     std::vector<Launch> order;
@@ -1498,22 +1534,45 @@ struct FusedBatch {
     MFS_CUDA(cudaMemcpyAsync(dmap, maps.data(), maps.size() * sizeof(dev::MsBlock), cudaMemcpyHostToDevice, s));
     MFS_CUDA(cudaStreamSynchronize(s));
     MFS_CUDA(cudaStreamSynchronize(0));
-    // one graph: every merged launch, then the Arnoldi sums to the host
+    // one graph: every merged launch, then the Arnoldi sums to the host.  A
+    // launch depends on the previous launches of the systems it serves, so
+    // launches over disjoint sets of systems may run at the same time; each
+    // system's own launches keep their order.
     cudaGraph_t graph = nullptr;
-    MFS_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    cudaError_t err = cudaSuccess;
+    MFS_CUDA(cudaGraphCreate(&graph, 0));
+    struct GraphGuard {
+      cudaGraph_t &g;
+      ~GraphGuard() {
+        if (g) cudaGraphDestroy(g);
+      }
+    } guard{graph};
+    std::vector<cudaGraphNode_t> last(nsys, nullptr);
+    std::vector<cudaGraphNode_t> deps;
     for (const Launch &L : launches) {
-      err = dev::launch_multi(L.proto, L.grid, L.smem, dtab + L.tab, dmap + L.map, dactive, s);
-      if (err != cudaSuccess) break;
+      deps.clear();
+      for (int k : L.sys)
+        if (last[k] && std::find(deps.begin(), deps.end(), last[k]) == deps.end()) deps.push_back(last[k]);
+      const void *tab = dtab + L.tab;
+      const dev::MsBlock *map = dmap + L.map;
+      const int *act = dactive;
+      void *kargs[3] = {(void *)&tab, (void *)&map, (void *)&act};
+      cudaKernelNodeParams kp{};
+      kp.func = const_cast<void *>(L.proto.fn);
+      kp.gridDim = dim3(L.grid);
+      kp.blockDim = dim3(L.proto.threads);
+      kp.sharedMemBytes = (unsigned)L.smem;
+      kp.kernelParams = kargs;
+      cudaGraphNode_t node = nullptr;
+      MFS_CUDA(cudaGraphAddKernelNode(&node, graph, deps.data(), deps.size(), &kp));
+      for (int k : L.sys) last[k] = node;
     }
-    if (err == cudaSuccess)
-      err = cudaMemcpyAsync(hbpin, hb, (size_t)136 * nsys * sizeof(double), cudaMemcpyDeviceToHost, s);
-    const cudaError_t e2 = cudaStreamEndCapture(s, &graph);
-    MFS_CUDA(err);
-    MFS_CUDA(e2);
-    const cudaError_t e3 = cudaGraphInstantiate(&exec, graph, 0);
-    cudaGraphDestroy(graph);
-    MFS_CUDA(e3);
+    deps.clear();
+    for (cudaGraphNode_t n : last)
+      if (n && std::find(deps.begin(), deps.end(), n) == deps.end()) deps.push_back(n);
+    cudaGraphNode_t copy = nullptr;
+    MFS_CUDA(cudaGraphAddMemcpyNode1D(&copy, graph, deps.data(), deps.size(), hbpin, hb,
+                                      (size_t)136 * nsys * sizeof(double), cudaMemcpyDeviceToHost));
+    MFS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
   }
 
   // write system k's freshly recorded launches into its slots of the tables
@@ -1544,19 +1603,20 @@ static void drop_fused(const mfs_handle *h) {
       ++i;
 }
 
-static FusedBatch *fused_for(mfs_handle *const *hv, int n) {
+static FusedBatch *fused_for(mfs_handle *const *hv, int n, int ngroups) {
   std::lock_guard<std::mutex> lock(g_fused_mu);
   for (auto &b : g_fused)
-    if (b->nsys == n && std::equal(b->hs.begin(), b->hs.end(), hv)) return b.get();
+    if (b->nsys == n && b->ngroups_used == std::max(1, std::min(ngroups, n)) && std::equal(b->hs.begin(), b->hs.end(), hv))
+      return b.get();
   std::unique_ptr<FusedBatch> b(new FusedBatch());
   const double t0 = now_ms();
-  b->build(hv, n);
+  b->build(hv, n, ngroups);
   b->build_ms = now_ms() - t0;
   if (hv[0]->prm.verbose)
     fprintf(stderr,
-            "mfs fused batch: %d systems, %zu + %zu + %zu merged launches per iteration (heads, preconditioners, "
-            "Krylov steps), %lld CTAs per replay, %.1f KB patched per iteration, built in %.1f ms\n",
-            n, b->nhead, b->npre, b->ntail, (long long)b->ctas, b->patch_bytes / 1024.0, b->build_ms);
+            "mfs fused batch: %d systems in %d groups, %zu + %zu + %zu merged launches per iteration (heads, "
+            "preconditioners, Krylov steps), %lld CTAs per replay, %.1f KB patched per iteration, built in %.1f ms\n",
+            n, b->ngroups_used, b->nhead, b->npre, b->ntail, (long long)b->ctas, b->patch_bytes / 1024.0, b->build_ms);
   if (g_fused.size() >= 4) g_fused.erase(g_fused.begin());
   g_fused.push_back(std::move(b));
   return g_fused.back().get();
@@ -2532,13 +2592,15 @@ int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, d
     if (hs[k]->host_only) return fail(MFS_ERR_INVALID, "a handle of the batch was built with setup_only");
     if (hs[k]->device != hs[0]->device) return fail(MFS_ERR_INVALID, "fused batch: handles on different devices");
   }
-  if (nthreads == 0) {
+  if (nthreads <= 0) {
+    // fused: -nthreads groups, or (0) one group per 32 systems, at most 8
+    const int ngroups = nthreads < 0 ? -nthreads : std::max(1, std::min(8, (nsys + 31) / 32));
     std::vector<mfs_info> inf(nsys);
     std::vector<int> st(nsys, MFS_OK);
     const double t0 = now_ms();
     try {
       MFS_CUDA(cudaSetDevice(hs[0]->device));
-      FusedBatch *B = fused_for(hs, nsys);
+      FusedBatch *B = fused_for(hs, nsys, ngroups);
       fused_solve(*B, rhs, x, tol, inf, st);
     } catch (const CudaError &e) {
       return fail(e.code, e.what());
@@ -2561,7 +2623,7 @@ int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, d
     }
     return rc;
   }
-  int nt = nthreads > 0 ? nthreads : 16;
+  int nt = nthreads;
   if (nt > nsys) nt = nsys;
   std::atomic<int> next(0);
   std::vector<int> st(nsys, MFS_OK);

@@ -234,10 +234,10 @@ def _ptr(a):
 
 def solve_batch(solvers, rhs, xs=None, tol=1e-8, nthreads=0, check=True):
     """Solve independent systems together (mfs_solve_batch): solvers[k]
-    (distinct handles) with rhs[k]; nthreads = 0 runs the fused executor
-    (one multi-system launch per step, one CUDA graph per iteration),
-    nthreads > 0 that many host threads on per-handle streams; returns
-    (xs, infos, status)."""
+    (distinct handles) with rhs[k]; nthreads <= 0 runs the fused executor
+    (one multi-system launch per step and group of systems, one CUDA graph
+    per iteration; -nthreads groups, 0 = automatic), nthreads > 0 that many
+    host threads on per-handle streams; returns (xs, infos, status)."""
     lib = load()
     n = len(solvers)
     if xs is None:

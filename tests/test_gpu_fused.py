@@ -9,7 +9,7 @@ different level counts and sparse layouts) in one batch, 2- and 3-field
 systems mixed, BGS(AMG) / AMG(BGS) / SIMPLE, float64 and float32
 preconditioners, Gauss-Seidel smoothing, restarts at different iterations, a
 system that stops at max_iters, a zero right-hand side, host vectors, graph
-reuse by a second call, and the full 256-system batch of 2-field 3D boxes
+reuse by a second call, one group and three concurrent groups, and the full 256-system batch of 2-field 3D boxes
 (n_e log-uniform in [12, 48]) against solo solves and the FP64 oracle's
 iteration counts.  Needs a GB300.
 """
@@ -53,9 +53,11 @@ def _solo(solvers, rhs, x0=None):
 
 
 def _check_fused(solvers, rhs, solo, reps=2, x0=None):
-    for _ in range(reps):
+    # one group, then three groups of similar sizes (concurrent chains)
+    for rep in range(reps + 1):
         xs = [torch.zeros_like(b) if x0 is None else x0[k].clone() for k, b in enumerate(rhs)]
-        xs, infos, status = mfs.solve_batch(solvers, rhs, xs, tol=1e-8, nthreads=0, check=False)
+        xs, infos, status = mfs.solve_batch(solvers, rhs, xs, tol=1e-8, nthreads=-1 if rep < reps else -3,
+                                            check=False)
         for k in range(len(solvers)):
             assert status[k] == solo[k][2], k
             assert infos[k]["iters"] == solo[k][1], (k, infos[k]["iters"], solo[k][1])
