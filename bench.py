@@ -648,10 +648,19 @@ def run_batch(args, rank, world):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
     t0 = time.perf_counter()
-    sizes, mats, rhs = inputs.batch_workload(args.nsys, 12, 48, 3)
+    if args.batch_kind == "te2d":
+        # many copies of the 3,267-dof 2D thermo-elastic system, fresh right-hand sides
+        te = inputs.thermo_elastic_2d(ne=32, seed=0)
+        sizes = np.full(args.nsys, 32)
+        mats = {32: te}
+        rhs = [inputs.system_rhs(te, 6000 + k) for k in range(args.nsys)]
+        kw = dict(max_levels=3, coarse_max=0)
+    else:
+        sizes, mats, rhs = inputs.batch_workload(args.nsys, 12, 48, 3)
+        kw = solver_kw(args)
     t1 = time.perf_counter()
     # layouts tuned for throughput (many systems on the GPU at once)
-    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, layout_tune=1, **solver_kw(args))
+    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, layout_tune=1, **kw)
             for ne, sy in mats.items()}
     solvers, used = [], set()
     for ne in sizes.tolist():
@@ -696,12 +705,32 @@ def run_batch(args, rank, world):
         seq.append(time.perf_counter() - ta)
     value = args.nsys * args.steps / sum(times)
     iters = [i["iters"] for i in infos]
+    # roofline of the whole batch: algorithmic bytes of every kernel of every
+    # system's solve (per mesh size: one profiled solo solve, bytes per
+    # iteration) over the batch time
+    per_iter = {}
+    for ne, sy in mats.items():
+        with mfs.Solver(sy, precond=args.precond, precision=args.precision, layout_tune=1, profile=1, **kw) as sv:
+            k = sizes.tolist().index(ne)
+            _, inf, _ = sv.solve(bs[k], torch.zeros_like(bs[k]), tol=1e-8)
+            per_iter[ne] = sum(v[2] for v in sv.kernel_stats(reset=True).values()) / max(1, inf["iters"])
+    batch_bytes = sum(per_iter[ne] * it for ne, it in zip(sizes.tolist(), iters))
+    hbm_peak, peak_kind = measured_hbm_peak()
+    gbps = batch_bytes / statistics.mean(times) / 1e9
+    roof = {"bound": "hbm", "achieved": gbps, "peak": hbm_peak, "unit": "GB/s", "frac": gbps / hbm_peak,
+            "peak_kind": peak_kind, "traffic": None,
+            "kernel": "the whole batch: algorithmic bytes of every kernel of every solve (per mesh size from a "
+                      "profiled solo solve, per iteration, times each system's iterations) / mean step time",
+            "bytes_per_step": batch_bytes}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "fp32p" else "f64",
             "data": "synthetic",
-            "config": {"workload": f"batch of {args.nsys} independent 2-field 3D coupled boxes, n_e log-uniform "
-                                   f"in [12,48], {args.precond.upper()} {args.precision.upper()}, FGMRES(50), rtol 1e-8 each",
+            "config": {"workload": (f"batch of {args.nsys} independent 2-field 3D coupled boxes, n_e log-uniform "
+                                    f"in [12,48]" if args.batch_kind == "box2" else
+                                    f"batch of {args.nsys} 2-field thermo-elastic 2D systems (32x32 Q1, 3,267 dofs, "
+                                    f"3 SA-AMG levels) with different right-hand sides")
+                                   + f", {args.precond.upper()} {args.precision.upper()}, FGMRES(50), rtol 1e-8 each",
                        "step": "one mfs_solve_batch over all systems (host-timed, synchronous)",
                        "executor": "fused: one multi-system launch per step, one CUDA graph per FGMRES iteration"
                                    if args.threads == 0 else f"{args.threads} host threads on per-handle streams",
@@ -711,7 +740,8 @@ def run_batch(args, rank, world):
                        "iters_mean": statistics.mean(iters), "iters_max": max(iters),
                        "sequential_solves_per_s": args.nsys / sum(seq),
                        "batch_speedup_vs_sequential": value / (args.nsys / sum(seq)),
-                       "generate_s": round(t1 - t0, 1), "setup_and_clone_s": round(t2 - t1, 1)}}
+                       "generate_s": round(t1 - t0, 1), "setup_and_clone_s": round(t2 - t1, 1)},
+            "roofline": roof}
     print(json.dumps(line), flush=True)
     for sv in solvers:
         sv.close()
@@ -789,6 +819,8 @@ def main():
     ap.add_argument("--simple-pred", default="bgs_amg", choices=["bgs_amg", "amg_bgs"],
                     help="SIMPLE's predictor solver: BGS(AMG) sweep or AMG(BGS) V-cycle")
     ap.add_argument("--nsys", type=int, default=256)
+    ap.add_argument("--batch-kind", default="box2", choices=["box2", "te2d"],
+                    help="batch: the 256 2-field 3D boxes, or copies of the 2D thermo-elastic system")
     ap.add_argument("--threads", type=int, default=0,
                     help="batch: 0 = fused executor, > 0 = that many host threads on per-handle streams; "
                          "serve: worker threads (0 = 16)")

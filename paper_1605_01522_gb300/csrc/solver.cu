@@ -1361,16 +1361,21 @@ struct FusedBatch {
   size_t nhead = 0, npre = 0, ntail = 0;  // merged launches per segment
   int64_t ctas = 0;                       // CTAs of one replay
   double build_ms = 0.0;
+  bool own_stream = true;
+  // plans over the systems still running, once at most half of this plan's
+  // are (keyed by their positions in this plan; kept for later calls)
+  std::map<std::vector<int>, std::unique_ptr<FusedBatch>> subs;
   FusedBatch() = default;
   FusedBatch(const FusedBatch &) = delete;
   ~FusedBatch() {
+    subs.clear();
     if (s) cudaStreamSynchronize(s);
     if (exec) cudaGraphExecDestroy(exec);
     if (htab) cudaFreeHost(htab);
     if (hactive) cudaFreeHost(hactive);
     if (hbpin) cudaFreeHost(hbpin);
     if (ypin) cudaFreeHost(ypin);
-    if (s) cudaStreamDestroy(s);
+    if (s && own_stream) cudaStreamDestroy(s);
   }
   double *sums(int k) { return hb + (int64_t)k * 136; }
 
@@ -1472,13 +1477,20 @@ struct FusedBatch {
 
   int ngroups_used = 1;
 
-  void build(mfs_handle *const *hv, int n, int ngroups) {
+  // stream: the stream to run on (a sub-plan takes its parent's), or null
+  // for a new library stream
+  void build(mfs_handle *const *hv, int n, int ngroups, cudaStream_t stream = nullptr) {
     hs.assign(hv, hv + n);
     nsys = n;
     ngroups_used = std::max(1, std::min(ngroups, n));
     const std::vector<std::vector<int>> sysgroups = make_groups(ngroups_used);
     MFS_CUDA(cudaSetDevice(hs[0]->device));
-    MFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    if (stream) {
+      s = stream;
+      own_stream = false;
+    } else {
+      MFS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    }
     vin.assign(nsys, nullptr);
     zout.assign(nsys, nullptr);
     for (int k = 0; k < nsys; ++k)
@@ -1573,6 +1585,18 @@ struct FusedBatch {
     MFS_CUDA(cudaGraphAddMemcpyNode1D(&copy, graph, deps.data(), deps.size(), hbpin, hb,
                                       (size_t)136 * nsys * sizeof(double), cudaMemcpyDeviceToHost));
     MFS_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  }
+
+  // the plan over this plan's systems at positions `live` (built on first use)
+  FusedBatch *sub(const std::vector<int> &live) {
+    auto it = subs.find(live);
+    if (it != subs.end()) return it->second.get();
+    if (subs.size() >= 16) subs.clear();
+    std::vector<mfs_handle *> hv;
+    for (int p : live) hv.push_back(hs[p]);
+    std::unique_ptr<FusedBatch> b(new FusedBatch());
+    b->build(hv.data(), (int)hv.size(), std::max(1, std::min(ngroups_used, ((int)hv.size() + 31) / 32)), s);
+    return subs.emplace(live, std::move(b)).first->second.get();
   }
 
   // write system k's freshly recorded launches into its slots of the tables
@@ -1723,6 +1747,11 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
     }
   }
   dev::Recorder rec;
+  // current plan and the global system at each of its positions
+  FusedBatch *P = &B;
+  std::vector<int> gidx(ns);
+  for (int k = 0; k < ns; ++k) gidx[k] = k;
+  int switches = 0;
   const bool verbose = hs[0]->prm.verbose != 0;
   cudaEvent_t ga = nullptr, gb = nullptr;
   if (verbose) {
@@ -1734,21 +1763,36 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
   std::vector<int> live_per_replay;
   while (std::find(active.begin(), active.end(), 1) != active.end()) {
     const double th = now_ms();
-    for (int k = 0; k < ns; ++k) {
-      B.hactive[k] = active[k];
+    // once at most half of the current plan's systems run, move to the plan
+    // over the running ones (fewer CTAs that would only check their flag)
+    {
+      std::vector<int> live;
+      for (int p = 0; p < P->nsys; ++p)
+        if (active[gidx[p]]) live.push_back(p);
+      if (P->nsys >= 16 && 2 * (int)live.size() <= P->nsys) {
+        std::vector<int> g2;
+        for (int p : live) g2.push_back(gidx[p]);
+        P = P->sub(live);
+        gidx.swap(g2);
+        ++switches;
+      }
+    }
+    for (int p = 0; p < P->nsys; ++p) {
+      const int k = gidx[p];
+      P->hactive[p] = active[k];
       if (!active[k]) continue;
       rec.ops.clear();
-      B.record_head(k, j[k], a[k], rec);
-      B.patch(rec, B.head_at[k]);
+      P->record_head(p, j[k], a[k], rec);
+      P->patch(rec, P->head_at[p]);
       rec.ops.clear();
-      B.record_tail(k, j[k], rec);
-      B.patch(rec, B.tail_at[k]);
+      P->record_tail(p, j[k], rec);
+      P->patch(rec, P->tail_at[p]);
     }
-    MFS_CUDA(cudaMemcpyAsync(B.dtab, B.htab, B.patch_bytes, cudaMemcpyHostToDevice, s));
-    MFS_CUDA(cudaMemcpyAsync(B.dactive, B.hactive, ns * sizeof(int), cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(P->dtab, P->htab, P->patch_bytes, cudaMemcpyHostToDevice, s));
+    MFS_CUDA(cudaMemcpyAsync(P->dactive, P->hactive, P->nsys * sizeof(int), cudaMemcpyHostToDevice, s));
     t_host += now_ms() - th;
     if (verbose) MFS_CUDA(cudaEventRecord(ga, s));
-    MFS_CUDA(cudaGraphLaunch(B.exec, s));
+    MFS_CUDA(cudaGraphLaunch(P->exec, s));
     if (verbose) MFS_CUDA(cudaEventRecord(gb, s));
     MFS_CUDA(cudaStreamSynchronize(s));
     ++replays;
@@ -1760,9 +1804,10 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
     }
     const double tc = now_ms();
     std::vector<int> ending;
-    for (int k = 0; k < ns; ++k) {
+    for (int p = 0; p < P->nsys; ++p) {
+      const int k = gidx[p];
       if (!active[k]) continue;
-      if (!ls[k].column(B.hbpin + (int64_t)k * 136, j[k])) {
+      if (!ls[k].column(P->hbpin + (int64_t)p * 136, j[k])) {
         finish(k, MFS_ERR_BREAKDOWN);
         continue;
       }
@@ -1806,9 +1851,9 @@ static void fused_solve(FusedBatch &B, const double *const *rhs, double *const *
     std::string live;
     for (size_t q = 0; q < live_per_replay.size(); q += 5) live += " " + std::to_string(live_per_replay[q]);
     fprintf(stderr,
-            "mfs fused solve: %d replays, %.2f ms total: graphs %.2f ms (GPU), host recording/patching %.2f ms, "
-            "Givens + cycle ends %.2f ms; live systems every 5th replay:%s\n",
-            replays, now_ms() - t_all, t_graph, t_host, t_cycle, live.c_str());
+            "mfs fused solve: %d replays (%d plan switches), %.2f ms total: graphs %.2f ms (GPU), host "
+            "recording/patching %.2f ms, Givens + cycle ends %.2f ms; live systems every 5th replay:%s\n",
+            replays, switches, now_ms() - t_all, t_graph, t_host, t_cycle, live.c_str());
   }
   for (int k = 0; k < ns; ++k)
     if (hostx[k]) MFS_CUDA(cudaMemcpyAsync(x[k], xx[k], hs[k]->n * sizeof(double), cudaMemcpyDeviceToHost, s));
