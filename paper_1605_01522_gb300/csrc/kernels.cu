@@ -1208,6 +1208,161 @@ struct KGemvAdd {
   }
 };
 
+// The tail of a single-field V-cycle (Algorithm 1 on the level above the
+// coarsest and the coarse solve) in ONE CTA, for levels small enough that
+// their vectors live in shared memory: Chebyshev / Jacobi pre-smoothing from
+// zero, residual, restriction, the coarsest solve through the explicit
+// inverse, prolongation and post-smoothing, separated by __syncthreads
+// instead of kernel boundaries.  Every step reduces a row exactly as the
+// separate launches do (one warp per block row, lanes striding over the
+// row's blocks, the same xor butterfly; the inverse applied in float64), so
+// the result is the one of the step-by-step V-cycle bit for bit.
+constexpr int kTailThreads = 1024;
+constexpr int kTailMaxSteps = 8;
+
+template <typename T> struct TailArgs {
+  int64_t n, nbr, nc, ncbr;  // level dofs / block rows; coarse dofs / block rows
+  const int32_t *arp, *acol;
+  const T *aval, *dinv;
+  const int32_t *rrp, *rcol;
+  const T *rval;  // R: ncbr block rows of BC x BR blocks
+  const int32_t *prp, *pcol;
+  const T *pval;  // P: nbr block rows of BR x BC blocks
+  const double *inv;  // nc x nc row-major inverse of the coarsest matrix
+  const T *b;
+  T *x;
+  int ns;  // smoothing steps per application
+  T c1[kTailMaxSteps], c2[kTailMaxSteps];
+};
+
+// row sums of a plain-BSR block row against x in shared memory (the
+// arithmetic of bsr_warp_row)
+template <int BR, int BC, typename T>
+__device__ __forceinline__ void tail_row(const int32_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                         const T *__restrict__ val, const T *x, int64_t row, int lane,
+                                         T (&acc)[BR]) {
+  const int lo = rp[row], hi = rp[row + 1];
+#pragma unroll
+  for (int r = 0; r < BR; ++r) acc[r] = T(0);
+  for (int k = lo + lane; k < hi; k += 32) {
+    const int64_t c = __ldg(col + k);
+    T xv[BC];
+#pragma unroll
+    for (int q = 0; q < BC; ++q) xv[q] = x[c * BC + q];
+    T blk[BR * BC];
+    ldg_block<BR * BC, T>(val + (int64_t)k * (BR * BC), blk);
+#pragma unroll
+    for (int r = 0; r < BR; ++r)
+#pragma unroll
+      for (int q = 0; q < BC; ++q) acc[r] += blk[r * BC + q] * xv[q];
+  }
+#pragma unroll
+  for (int r = 0; r < BR; ++r)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc[r] += __shfl_xor_sync(0xffffffffu, acc[r], o);
+}
+
+// one smoothing step in shared memory: xo = x + d, d = c1 d + c2 dinv (b - A x)
+template <int BR, typename T>
+__device__ __forceinline__ void tail_smooth(const TailArgs<T> &a, const T *b, const T *x, T *xo, T *d, T c1, T c2) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t row = warp; row < a.nbr; row += kTailThreads / 32) {
+    T acc[BR];
+    tail_row<BR, BR, T>(a.arp, a.acol, a.aval, x, row, lane, acc);
+    if (lane < BR) {
+      const int64_t i = row * BR + lane;
+      const T res = b[i] - pick<BR, T>(acc, lane);
+      const T dd = c1 * d[i] + c2 * a.dinv[i] * res;
+      d[i] = dd;
+      xo[i] = x[i] + dd;
+    }
+  }
+  __syncthreads();
+}
+
+template <int BR, int BC, typename T>
+__device__ __forceinline__ void d_vcycle_tail(const TailArgs<T> &a) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  double *bc = reinterpret_cast<double *>(tail_smem);  // coarse right-hand side (float64 copy)
+  T *xc = reinterpret_cast<T *>(bc + a.nc);
+  T *bcT = xc + a.nc;
+  T *b = bcT + a.nc;
+  T *x0 = b + a.n;
+  T *x1 = x0 + a.n;
+  T *d = x1 + a.n;
+  T *r = d + a.n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int64_t i = tid; i < a.n; i += kTailThreads) b[i] = a.b[i];
+  __syncthreads();
+  // pre-smoothing from zero: the first step d = x = c2 dinv b, then steps
+  for (int64_t i = tid; i < a.n; i += kTailThreads) {
+    const T dd = a.c2[0] * a.dinv[i] * b[i];
+    d[i] = dd;
+    x0[i] = dd;
+  }
+  __syncthreads();
+  T *cur = x0, *oth = x1;
+  for (int k = 1; k < a.ns; ++k) {
+    tail_smooth<BR, T>(a, b, cur, oth, d, a.c1[k], a.c2[k]);
+    T *t = cur;
+    cur = oth;
+    oth = t;
+  }
+  // residual r = b - A x  (as y = -1 * A x + 1 * b)
+  for (int64_t row = warp; row < a.nbr; row += kTailThreads / 32) {
+    T acc[BR];
+    tail_row<BR, BR, T>(a.arp, a.acol, a.aval, cur, row, lane, acc);
+    if (lane < BR) {
+      const int64_t i = row * BR + lane;
+      r[i] = T(-1) * pick<BR, T>(acc, lane) + T(1) * b[i];
+    }
+  }
+  __syncthreads();
+  // restriction bc = R r
+  for (int64_t row = warp; row < a.ncbr; row += kTailThreads / 32) {
+    T acc[BC];
+    tail_row<BC, BR, T>(a.rrp, a.rcol, a.rval, r, row, lane, acc);
+    if (lane < BC) bcT[row * BC + lane] = T(1) * pick<BC, T>(acc, lane);
+  }
+  __syncthreads();
+  // coarsest solve through the explicit inverse, in float64
+  for (int64_t j = tid; j < a.nc; j += kTailThreads) bc[j] = (double)bcT[j];
+  __syncthreads();
+  for (int64_t row = warp; row < a.nc; row += kTailThreads / 32) {
+    const double *ar = a.inv + row * a.nc;
+    double acc = 0.0;
+    for (int64_t j = lane; j < a.nc; j += 32) acc += __ldg(ar + j) * bc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) xc[row] = (T)acc;
+  }
+  __syncthreads();
+  // prolongation x += P xc  (as y = 1 * P xc + 1 * x)
+  for (int64_t row = warp; row < a.nbr; row += kTailThreads / 32) {
+    T acc[BR];
+    tail_row<BR, BC, T>(a.prp, a.pcol, a.pval, xc, row, lane, acc);
+    if (lane < BR) {
+      const int64_t i = row * BR + lane;
+      cur[i] = T(1) * pick<BR, T>(acc, lane) + T(1) * cur[i];
+    }
+  }
+  __syncthreads();
+  // post-smoothing from the corrected x
+  for (int k = 0; k < a.ns; ++k) {
+    tail_smooth<BR, T>(a, b, cur, oth, d, a.c1[k], a.c2[k]);
+    T *t = cur;
+    cur = oth;
+    oth = t;
+  }
+  for (int64_t i = tid; i < a.n; i += kTailThreads) a.x[i] = cur[i];
+}
+template <int BR, int BC, typename T>
+struct KVcycleTail {
+  static constexpr int kMaxThreads = kTailThreads;
+  using Args = TailArgs<T>;
+  static __device__ __forceinline__ void run(const Args &a, int, int) { d_vcycle_tail<BR, BC, T>(a); }
+};
+
 inline unsigned ew_grid(int64_t n) {
   int64_t g = (n + kThreads - 1) / kThreads;
   if (g > 152 * 16) g = 152 * 16;
@@ -1492,6 +1647,57 @@ void lu_solve(const DenseLU &lu, const T *b, T *x, cudaStream_t s) {
   const int threads = lu.n <= 64 ? 256 : 512;
   go<KLuSolve<T>>(1, threads, smem, s, {lu.n, lu.lu, lu.perm, b, x, staged});
 }
+
+size_t tail_smem_bytes(int64_t n, int64_t nc, size_t tsize) {
+  return (size_t)nc * (sizeof(double) + 2 * tsize) + (size_t)n * 5 * tsize;
+}
+
+bool tail_supported(int br, int bc) { return br == bc && (br == 1 || br == 2 || br == 3 || br == 6); }
+
+bool cta_rows(const Sell &A) { return A.kind == 1 && A.nbr <= kCtaRowsMax && A.nnzb >= kCtaRowBlocks * A.nbr; }
+
+template <typename T>
+void vcycle_tail(const Sell &A, const T *dinv, const Sell &R, const Sell &P, const DenseLU &lu, int ns,
+                 const T *c1, const T *c2, const T *b, T *x, cudaStream_t s) {
+  TailArgs<T> a{};
+  a.n = A.nrows();
+  a.nbr = A.nbr;
+  a.nc = lu.n;
+  a.ncbr = R.nbr;
+  a.arp = A.sp;
+  a.acol = A.col;
+  a.aval = vals<T>(A);
+  a.dinv = dinv;
+  a.rrp = R.sp;
+  a.rcol = R.col;
+  a.rval = vals<T>(R);
+  a.prp = P.sp;
+  a.pcol = P.col;
+  a.pval = vals<T>(P);
+  a.inv = lu.inv;
+  a.b = b;
+  a.x = x;
+  a.ns = ns;
+  for (int k = 0; k < ns && k < kTailMaxSteps; ++k) {
+    a.c1[k] = c1[k];
+    a.c2[k] = c2[k];
+  }
+  const size_t smem = tail_smem_bytes(a.n, a.nc, sizeof(T));
+  const double bytes = ns * 2.0 * matrix_bytes<T>(A) + matrix_bytes<T>(A) + matrix_bytes<T>(R) + matrix_bytes<T>(P) +
+                       8.0 * lu.n * (double)lu.n + 2.0 * sizeof(T) * A.nrows();
+  HookScope hs(s, K_COARSE, bytes, 3, A.nbr, 0.0);
+  switch (A.br) {
+    case 1: go<KVcycleTail<1, 1, T>>(1, kTailThreads, smem, s, a); break;
+    case 2: go<KVcycleTail<2, 2, T>>(1, kTailThreads, smem, s, a); break;
+    case 3: go<KVcycleTail<3, 3, T>>(1, kTailThreads, smem, s, a); break;
+    case 6: go<KVcycleTail<6, 6, T>>(1, kTailThreads, smem, s, a); break;
+    default: break;
+  }
+}
+template void vcycle_tail<float>(const Sell &, const float *, const Sell &, const Sell &, const DenseLU &, int,
+                                 const float *, const float *, const float *, float *, cudaStream_t);
+template void vcycle_tail<double>(const Sell &, const double *, const Sell &, const Sell &, const DenseLU &, int,
+                                  const double *, const double *, const double *, double *, cudaStream_t);
 
 template <typename T>
 void fill(T *x, int64_t n, T v, cudaStream_t s) {

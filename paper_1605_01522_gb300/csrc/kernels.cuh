@@ -155,6 +155,21 @@ template <typename T>
 void gs_sweeps(const GsLevel &g, const T *dblk, const T *b, T *x, T omega, int sweeps, bool backward,
                cudaStream_t s);
 
+// Tail of a single-field V-cycle in one CTA (Algorithm 1 from the level
+// above the coarsest down through the coarse solve and back): A (level l,
+// plain BSR, br x br blocks), its inverse point diagonal, R (to the coarsest,
+// br x br blocks), P, the coarsest inverse (lu.inv, required), ns smoothing
+// steps with coefficients c1, c2 (host arrays, ns <= 8), x = V-cycle(b) from
+// zero.  Same arithmetic as the step-by-step launches.  Shared memory:
+// tail_smem_bytes, which the caller keeps within 48 KB.
+bool tail_supported(int br, int bc);
+// true when spmv runs this plain-BSR matrix with one CTA per row (few, long rows)
+bool cta_rows(const Sell &A);
+size_t tail_smem_bytes(int64_t n, int64_t nc, size_t tsize);
+template <typename T>
+void vcycle_tail(const Sell &A, const T *dinv, const Sell &R, const Sell &P, const DenseLU &lu, int ns,
+                 const T *c1, const T *c2, const T *b, T *x, cudaStream_t s);
+
 // x = LU^-1 b  (dense; b, x of type T, arithmetic in float64): with lu.inv one
 // warp per row of the explicit inverse, else one CTA of triangular sweeps
 template <typename T>

@@ -618,6 +618,7 @@ template <typename T> static void alloc_group_work(Arena &ar, DGroup<T> &g) {
 template <typename T> struct Precond {
   int kind = 0, nf = 0, order = 0, sweeps = 1;
   int smoother = MFS_CHEBYSHEV, gs_sweeps = 1;
+  bool use_tail = true;  // one-CTA V-cycle tails where they apply
   T gs_omega = T(0.79);
   std::vector<int64_t> fsize, foff;
   DGroup<T> g0, g1;
@@ -671,11 +672,29 @@ template <typename T> struct Precond {
     if (cur != x) dev::convert<T, T>(cur, x, f.n, s);
   }
 
+  // the level above the coarsest, small enough that one CTA runs the rest of
+  // the V-cycle (dev::vcycle_tail) with the same arithmetic
+  bool tail_ok(const DGroup<T> &g, int i, int l) const {
+    if (!use_tail || smoother == MFS_GS || l != g.L - 2) return false;
+    const FL<T> &f = g.lv[l][i];
+    const dev::DenseLU &lu = g.cf[i];
+    const dev::Sell &A = f.A, &R = f.R, &P = f.P;
+    if (!lu.inv || lu.n == 0 || A.kind != 1 || R.kind != 1 || P.kind != 1) return false;
+    if (dev::cta_rows(A) || dev::cta_rows(R) || dev::cta_rows(P)) return false;
+    if (!dev::tail_supported(A.br, R.br) || R.bc != A.br || P.br != A.br || P.bc != R.br) return false;
+    if (f.c1.size() > 8 || lu.n != R.nrows()) return false;
+    return dev::tail_smem_bytes(A.nrows(), lu.n, sizeof(T)) <= 48 * 1024;
+  }
+
   // Algorithm 1 for field i of group g from level l, zero initial guess
   void vcycle(DGroup<T> &g, int i, int l, const T *rhs, T *x) {
     FL<T> &f = g.lv[l][i];
     if (l == g.L - 1) {
       dev::lu_solve<T>(g.cf[i], rhs, x, s);
+      return;
+    }
+    if (tail_ok(g, i, l)) {
+      dev::vcycle_tail<T>(f.A, f.dinv, f.R, f.P, g.cf[i], (int)f.c1.size(), f.c1.data(), f.c2.data(), rhs, x, s);
       return;
     }
     FL<T> &c = g.lv[l + 1][i];
@@ -2205,6 +2224,7 @@ void upload_precond(mfs_handle *h, Arena &mat, Precond<T> &P, const std::map<std
   P.s = h->s;
   auto fine_sell = [&](int i, int j) { return h->A64.at({i, j}); };
   P.smoother = p.smoother;
+  P.use_tail = p.vcycle_tail != 0;
   P.gs_sweeps = p.gs_sweeps;
   P.gs_omega = (T)p.gs_omega;
   if (p.precond == MFS_BGS_AMG || p.precond == MFS_AMG_BGS || p.precond == MFS_AMG_SIMPLE ||
@@ -2320,6 +2340,7 @@ void mfs_default_params(mfs_params *p) {
   p->cuda_stream = nullptr;
   p->verbose = 0;
   p->setup_device = 1;
+  p->vcycle_tail = 1;
 }
 
 int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int nfields,
@@ -2339,7 +2360,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
       (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS) ||
       (p.rows_split != 0 && p.rows_split != 1 && p.rows_split != 2 && p.rows_split != 4) ||
-      (p.layout_tune != 0 && p.layout_tune != 1))
+      (p.layout_tune != 0 && p.layout_tune != 1) || (p.vcycle_tail != 0 && p.vcycle_tail != 1))
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;

@@ -33,7 +33,7 @@ EXPORTS = ["mfs_default_params", "mfs_setup", "mfs_solve", "mfs_clone", "mfs_sol
            "mfs_strerror", "mfs_last_error"]
 KERNEL_CLASSES = ["spmv", "smooth", "vector", "coarse_lu", "arnoldi"]
 _OTHER = {2: {1: "smooth_first", 2: "fill", 3: "axpy_diag", 4: "axpy", 5: "convert", 6: "scale", 7: "scale_convert"},
-          3: {1: "lu_solve", 2: "coarse_inverse_apply"},
+          3: {1: "lu_solve", 2: "coarse_inverse_apply", 3: "vcycle_tail"},
           4: {1: "mdot", 2: "reduce_partials", 3: "cgs_fused", 4: "cgs_update", 5: "gemv_add"}}
 
 
@@ -75,7 +75,7 @@ class Params(C.Structure):
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
                 ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int),
                 ("simple_pred", C.c_int), ("gs_sweeps", C.c_int), ("gs_omega", C.c_double),
-                ("rows_split", C.c_int), ("layout_tune", C.c_int)]
+                ("rows_split", C.c_int), ("layout_tune", C.c_int), ("vcycle_tail", C.c_int)]
 
 
 class Info(C.Structure):

@@ -232,3 +232,21 @@ def test_zero_diagonal_block_is_refused():
     with mfs.Solver(s, precond="simple", **kw) as lib:
         _, info, rc = lib.solve(_cuda(s.rhs), tol=1e-8)
         assert rc == mfs.OK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32p"])
+@pytest.mark.parametrize("name,pc", [("3d", "bgs_amg"), ("2d", "bgs_amg"), ("3d", "simple"), ("roll", "bgs_amg")])
+def test_vcycle_tail_is_the_stepwise_vcycle_bit_for_bit(name, pc, prec):
+    """The one-CTA tail (level above the coarsest + coarse solve, shared-memory
+    vectors) reduces every row as the per-step launches do, so applications
+    and whole solves equal the step-by-step V-cycle exactly; the profiled
+    solve shows that the tail ran."""
+    s, kw = _small(name)
+    v = _cuda(np.random.default_rng(5).standard_normal(s.ndofs))
+    with mfs.Solver(s, precond=pc, precision=prec, vcycle_tail=0, **kw) as a, \
+            mfs.Solver(s, precond=pc, precision=prec, vcycle_tail=1, profile=1, **kw) as b:
+        assert torch.equal(a.apply(v), b.apply(v))
+        xa, ia, _ = a.solve(_cuda(s.rhs), tol=1e-8)
+        xb, ib, _ = b.solve(_cuda(s.rhs), tol=1e-8)
+        assert ia["iters"] == ib["iters"] and torch.equal(xa, xb)
+        assert any(r[0] == "vcycle_tail" for r in b.kernel_detail())
