@@ -182,11 +182,13 @@ def kernel_source_digest(kernel):
     import hashlib
     import re
     src = open(os.path.join(ROOT, "paper_1605_01522_gb300", "csrc", "kernels.cu")).read()
-    fn = {"smooth_sell": ["sell_row", "k_smooth"], "spmv_sell": ["sell_row", "k_spmv"],
-          "smooth_sell4": ["sell_row", "k_smooth"], "spmv_sell4": ["sell_row", "k_spmv"],
-          "smooth_sell8": ["sell_row", "k_smooth"], "spmv_sell8": ["sell_row", "k_spmv"],
-          "spmv_rows": ["k_spmv_rows"], "smooth_warp": ["bsr_warp_row", "k_smooth_warp"],
-          "spmv_warp": ["bsr_warp_row", "k_spmv_warp"]}.get(kernel.split("<")[0])
+    fn = {"smooth_sell": ["sell_row", "d_smooth"], "spmv_sell": ["sell_row", "d_spmv"],
+          "smooth_sell4": ["sell_row", "d_smooth"], "spmv_sell4": ["sell_row", "d_spmv"],
+          "smooth_sell8": ["sell_row", "d_smooth"], "spmv_sell8": ["sell_row", "d_spmv"],
+          "spmv_rows": ["d_spmv_rows"], "smooth_warp": ["bsr_warp_row", "d_smooth_warp"],
+          "spmv_warp": ["bsr_warp_row", "d_spmv_warp"]}.get(kernel.split("<")[0])
+    if fn:
+        fn = fn + ["k_solo"]  # the single-system kernel wrapper every launch goes through
     if not fn:
         return None
     h = hashlib.sha256()
