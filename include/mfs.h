@@ -177,12 +177,13 @@ typedef struct {
                                         fastest SELL-32 variant only (best when many
                                         systems run together, mfs_solve_batch, where the
                                         GPU is full and throughput counts) */
-  int vcycle_tail;                   /* 1 (default): a single-field V-cycle whose level above
-                                        the coarsest is small (<= 48 KB of vectors, one warp
-                                        per block row, explicit coarse inverse) runs that
-                                        level and the coarse solve as ONE single-CTA launch
-                                        (same arithmetic, bit for bit); 0: one launch per
-                                        step (Algorithm 1 as written) */
+  int vcycle_tail;                   /* 1: a single-field V-cycle whose level above the
+                                        coarsest is small (<= 48 KB of vectors, one warp per
+                                        block row, explicit coarse inverse) runs that level
+                                        and the coarse solve as ONE single-CTA launch (same
+                                        arithmetic, bit for bit); 0 (default): one launch per
+                                        step (Algorithm 1 as written) - on GB300 the one-SM
+                                        tail is no faster than the launches it replaces */
 } mfs_params;
 
 typedef struct {
@@ -198,7 +199,7 @@ typedef struct {
 
 /* Fill *p with the defaults listed above (BGS(AMG), backward, 1 sweep,
  * SIMPLE groups all zero = predictor is every field but the last, SIMPLEC, 4 levels, coarse_max 1000,
- * Chebyshev degree 2, GMRES(50), FP64, seed 7, GPU setup, V-cycle tails on). */
+ * Chebyshev degree 2, GMRES(50), FP64, seed 7, GPU setup, V-cycle tails off). */
 void mfs_default_params(mfs_params *p);
 
 /* Build the hierarchy for the block system (Sec. 4: blocks A_ij with the

@@ -618,7 +618,7 @@ template <typename T> static void alloc_group_work(Arena &ar, DGroup<T> &g) {
 template <typename T> struct Precond {
   int kind = 0, nf = 0, order = 0, sweeps = 1;
   int smoother = MFS_CHEBYSHEV, gs_sweeps = 1;
-  bool use_tail = true;  // one-CTA V-cycle tails where they apply
+  bool use_tail = false;  // one-CTA V-cycle tails where they apply (mfs_params.vcycle_tail)
   T gs_omega = T(0.79);
   std::vector<int64_t> fsize, foff;
   DGroup<T> g0, g1;
@@ -2340,7 +2340,7 @@ void mfs_default_params(mfs_params *p) {
   p->cuda_stream = nullptr;
   p->verbose = 0;
   p->setup_device = 1;
-  p->vcycle_tail = 1;
+  p->vcycle_tail = 0;
 }
 
 int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int nfields,
