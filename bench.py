@@ -768,6 +768,7 @@ def run_serve(args, rank, world):
     reuse = rng.random(args.requests) < 0.3
     workers = args.threads or 16
     srv = serving.Server(hbm_budget=int(args.hbm_gb * (1 << 30)), workers=workers, max_setups=args.max_setups,
+                         fused=args.serve_fused,
                          precond=args.precond, precision=args.precision, **solver_kw(args))
     t0 = time.perf_counter()
     t = t0
@@ -787,6 +788,7 @@ def run_serve(args, rank, world):
             "config": {"workload": f"serving: {args.requests} Poisson requests at {args.rate}/s, 2- or 3-field 3D boxes, "
                                    f"n_e in {sizes}, 30 % reuse a resident hierarchy, HBM budget {args.hbm_gb} GB, "
                                    f"{workers} workers, at most {args.max_setups} setups at once, "
+                                   f"{'fused batched solves' if args.serve_fused else 'one stream per request'}, "
                                    f"{args.precond.upper()} {args.precision.upper()}, rtol 1e-8",
                        **st}}
     print(json.dumps(line), flush=True)
@@ -831,6 +833,8 @@ def main():
     ap.add_argument("--hbm-gb", type=float, default=150.0)
     ap.add_argument("--max-setups", type=int, default=8, help="serve: setups in flight at once")
     ap.add_argument("--serve-sizes", default="16,24,32,48,64")
+    ap.add_argument("--serve-fused", action="store_true",
+                    help="serve: solve the ready requests together with the fused batch executor")
     args = ap.parse_args()
     NE = args.ne if args.ne is not None else DEFAULT_NE.get(args.workload, 64)
     rank = int(os.environ.get("RANK", 0))

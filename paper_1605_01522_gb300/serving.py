@@ -1,15 +1,21 @@
 """Continuous-batching solve server over libmfs.
 
 Requests (a coupled block system plus a right-hand side) arrive at any time;
-a request is admitted when a worker is free and its device memory fits the
-HBM budget; admitted requests run concurrently, each on its own handle and
-CUDA stream, so their V-cycles and Krylov kernels overlap on the GPU while
-new requests keep being admitted as slots and memory free up.  A request may
-reuse a resident hierarchy of the same system (a clone: no setup, only a new
-workspace) or bring a new matrix (a full setup).  Resident hierarchies are
-evicted least-recently-used when the budget is short.  Every result is the
-one a solo solve of that request gives (the same kernels and reductions run
-on the request's own stream), which the serving test checks.
+a request is admitted when a slot is free and its device memory fits the HBM
+budget, and new requests keep being admitted as slots and memory free up.  A
+request may reuse a resident hierarchy of the same system (a clone: no
+setup, only a new workspace) or bring a new matrix (a full setup).  Resident
+hierarchies are evicted least-recently-used when the budget is short.
+
+Solves run in one of two modes.  Per request (fused=False): every admitted
+request is solved on its own handle and CUDA stream by its worker thread, so
+the requests' kernels overlap on the GPU.  Fused (fused=True): workers only
+admit and set up; one solver thread takes every request that is ready when
+it is free and solves them together with the fused batch executor
+(mfs_solve_batch, nthreads = 0): the live requests' V-cycles, matvecs and
+Arnoldi passes run as shared multi-system launches, and requests that become
+ready meanwhile join the next batch.  Either way every result is the one a
+solo solve of that request gives, which the serving test checks.
 """
 from __future__ import annotations
 
@@ -49,10 +55,19 @@ class Server:
     """hbm_budget: bytes of device memory the server may hold (resident
     hierarchies + running requests); workers: requests in flight at once."""
 
-    def __init__(self, hbm_budget, workers=8, tol=1e-8, keep_resident=True, max_setups=4, **solver_kw):
+    def __init__(self, hbm_budget, workers=8, tol=1e-8, keep_resident=True, max_setups=4, fused=False,
+                 max_inflight=None, max_batch=64, **solver_kw):
         """max_setups: setups (new matrices) in flight at once, which bounds
-        their transient device memory."""
+        their transient device memory.  fused: solve the ready requests
+        together (see the module docstring); max_inflight: admitted requests
+        at once (default: workers, or 8 x workers when fused); max_batch:
+        requests per fused batch."""
         self.budget = int(hbm_budget)
+        self.fused = fused
+        self.max_inflight = max_inflight or (8 * workers if fused else workers)
+        self.max_batch = max_batch
+        self.ready = collections.deque()  # fused: (request, handle, base) set up and waiting for a batch
+        self.batches = []                 # fused: sizes of the batches solved
         self.tol = tol
         self.kw = solver_kw
         self.keep_resident = keep_resident
@@ -70,6 +85,8 @@ class Server:
         self.setups_running = 0
         self.max_setups = max_setups
         self.threads = [threading.Thread(target=self._work, daemon=True) for _ in range(workers)]
+        if fused:
+            self.threads.append(threading.Thread(target=self._solve_loop, daemon=True))
         for t in self.threads:
             t.start()
 
@@ -117,6 +134,9 @@ class Server:
                 "mean_setup_ms": float(setup.mean() * 1e3) if len(setup) else 0.0,
                 "solves_per_s": ok / (t1 - t0), "peak_hbm_bytes": self.peak_used, "peak_in_flight": self.peak_running,
                 "setups": int(sum(1 for r in self.done if r.setup_done_here)),
+                "solve_mode": "fused batches" if self.fused else "one handle and stream per request",
+                "fused_batches": len(self.batches),
+                "mean_batch": float(np.mean(self.batches)) if self.batches else None,
                 "failed": int(sum(errors.values())), "errors": dict(errors.most_common(3))}
 
     # ------------------------------------------------------------- internals
@@ -148,7 +168,7 @@ class Server:
 
     def _take(self):
         """Admit the oldest pending request that fits (called with the lock held)."""
-        if not self.pending:
+        if not self.pending or self.running >= self.max_inflight:
             return None
         r = self.pending[0]
         if self._needs_setup(r) and self.setups_running >= self.max_setups:
@@ -198,7 +218,7 @@ class Server:
                 if r is None:
                     return
                 base = self.resident[r.key][0] if (r.reuse and r.key in self.resident) else None
-            sv, keep = None, False
+            sv = None
             try:
                 if base is not None:
                     sv = base.clone()
@@ -210,6 +230,11 @@ class Server:
                             self.setups_running -= 1
                             self.cv.notify_all()
                     r.setup_done_here = True
+                if self.fused:
+                    with self.cv:
+                        self.ready.append((r, sv, base))
+                        self.cv.notify_all()
+                    continue
                 r.t_start = time.perf_counter()
                 x = np.zeros(r.system.ndofs)
                 _, r.info, r.rc = sv.solve(r.rhs, x, tol=self.tol)
@@ -217,24 +242,59 @@ class Server:
             except mfs.MfsError as e:
                 r.rc, r.error = e.code, str(e)
             r.t_done = time.perf_counter()
+            self._finish(r, sv, base)
+
+    def _solve_loop(self):
+        """Fused mode: solve every ready request together, batch after batch."""
+        while True:
             with self.cv:
-                self.used -= r.reserved
-                if sv is not None:
-                    shared, own = sv.device_bytes(True), sv.device_bytes(False)
-                    if r.setup_done_here:
-                        self.footprint[r.key] = (shared, own)
-                        if self.keep_resident and r.key not in self.resident and self.used + shared + own <= self.budget:
-                            self.resident[r.key] = [sv, shared, own, 0]
-                            self.used += shared + own
-                            keep = True
-                if base is not None and r.key in self.resident:
-                    self.resident[r.key][3] -= 1
-            # release a handle that is not kept before the request counts as
-            # finished, so that drain() never returns with device work in flight
-            if sv is not None and not keep:
-                sv.close()
-            with self.cv:
-                self.running -= 1
-                self.done.append(r)
-                self.cv.notify_all()
-            r.event.set()
+                while not self.ready and not self.stop:
+                    self.cv.wait(0.05)
+                if not self.ready and self.stop:
+                    return
+                batch = []
+                while self.ready and len(batch) < self.max_batch:
+                    batch.append(self.ready.popleft())
+            t0 = time.perf_counter()
+            for r, _, _ in batch:
+                r.t_start = t0
+            xs = [np.zeros(r.system.ndofs) for r, _, _ in batch]
+            try:
+                _, infos, status = mfs.solve_batch([sv for _, sv, _ in batch], [r.rhs for r, _, _ in batch], xs,
+                                                   tol=self.tol, nthreads=0, check=False)
+                for (r, _, _), x, info, st in zip(batch, xs, infos, status):
+                    r.x, r.info, r.rc = x, info, st
+            except mfs.MfsError as e:
+                for r, _, _ in batch:
+                    r.rc, r.error = e.code, str(e)
+            t1 = time.perf_counter()
+            self.batches.append(len(batch))
+            for r, sv, base in batch:
+                r.t_done = t1
+                self._finish(r, sv, base)
+
+    def _finish(self, r, sv, base):
+        """Release a finished request's reservation, keep a new hierarchy
+        resident when it fits, release the handle otherwise."""
+        keep = False
+        with self.cv:
+            self.used -= r.reserved
+            if sv is not None:
+                shared, own = sv.device_bytes(True), sv.device_bytes(False)
+                if r.setup_done_here:
+                    self.footprint[r.key] = (shared, own)
+                    if self.keep_resident and r.key not in self.resident and self.used + shared + own <= self.budget:
+                        self.resident[r.key] = [sv, shared, own, 0]
+                        self.used += shared + own
+                        keep = True
+            if base is not None and r.key in self.resident:
+                self.resident[r.key][3] -= 1
+        # release a handle that is not kept before the request counts as
+        # finished, so that drain() never returns with device work in flight
+        if sv is not None and not keep:
+            sv.close()
+        with self.cv:
+            self.running -= 1
+            self.done.append(r)
+            self.cv.notify_all()
+        r.event.set()

@@ -1,10 +1,12 @@
 """Serving loop (paper_1605_01522_gb300/serving.py) on the GPU.  Needs a GB300.
 
 Requests of different systems arrive while others run; each is admitted
-when a worker and HBM budget are free, runs on its own handle and stream
-(a clone of a resident hierarchy or a fresh setup), and must return exactly
-the solution a solo solve gives, at a true residual <= 1e-8.  A tight budget
-must cap the device memory held and the requests in flight.
+when a slot and HBM budget are free, gets its own handle (a clone of a
+resident hierarchy or a fresh setup), is solved on its own stream or - in
+the fused mode - together with the other ready requests by the fused batch
+executor, and must return exactly the solution a solo solve gives, at a true
+residual <= 1e-8.  A tight budget must cap the device memory held and the
+requests in flight.
 """
 import numpy as np
 import pytest
@@ -37,7 +39,8 @@ def _requests(pool, n, seed):
     return out
 
 
-def test_each_result_same_alone_and_in_the_mix():
+@pytest.mark.parametrize("fused", [False, True])
+def test_each_result_same_alone_and_in_the_mix(fused):
     pool = _pool()
     reqs = _requests(pool, 24, 1)
     alone = []
@@ -48,7 +51,7 @@ def test_each_result_same_alone_and_in_the_mix():
         alone.append(x)
     for sv in solvers.values():
         sv.close()
-    srv = serving.Server(hbm_budget=8 << 30, workers=6, **KW)
+    srv = serving.Server(hbm_budget=8 << 30, workers=6, fused=fused, **KW)
     try:
         handles = []
         for i, (key, b, reuse) in enumerate(reqs):
@@ -64,6 +67,8 @@ def test_each_result_same_alone_and_in_the_mix():
         st = srv.stats()
         assert st["converged"] == len(reqs) and st["peak_in_flight"] >= 2
         assert st["setups"] < len(reqs)  # some requests reused a resident hierarchy
+        if fused:  # every request went through a fused batch
+            assert st["fused_batches"] >= 1 and round(st["fused_batches"] * st["mean_batch"]) == len(reqs)
     finally:
         srv.close()
 

@@ -101,3 +101,32 @@ def test_failed_setups_are_counted(fake):
         srv.close()
     assert st["requests"] == 3 and st["converged"] == 1 and st["failed"] == 2
     assert "fake setup failure" in next(iter(st["errors"]))
+
+
+def test_fused_mode_solves_ready_requests_together(fake, monkeypatch):
+    """fused=True: workers only admit and set up; ready requests are solved
+    by shared batches (here a fake mfs_solve_batch); every request finishes,
+    each exactly once, the budget and the setup cap hold, and batches hold
+    more than one request."""
+    calls = []
+    lock = threading.Lock()
+
+    def fake_batch(solvers, rhs, xs, tol=1e-8, nthreads=0, check=True):
+        assert nthreads == 0 and len(set(map(id, solvers))) == len(solvers)
+        with lock:
+            calls.append(len(solvers))
+        time.sleep(0.02)
+        for x in xs:
+            x[:] = 1.0
+        return xs, [{"iters": 1}] * len(solvers), [mfs.OK] * len(solvers)
+
+    monkeypatch.setattr(serving.mfs, "solve_batch", fake_batch)
+    srv = serving.Server(hbm_budget=10 ** 7, workers=4, max_setups=2, fused=True, max_batch=16)
+    try:
+        st = _run(srv, [(k % 5, 100 + k % 5, k % 3 == 0) for k in range(80)])
+    finally:
+        srv.close()
+    assert st["requests"] == 80 and st["converged"] == 80 and st["failed"] == 0
+    assert sum(calls) == 80 and max(calls) > 1 and max(calls) <= 16
+    assert st["fused_batches"] == len(calls) and st["peak_hbm_bytes"] <= 10 ** 7
+    assert fake.peak_setups <= 2
