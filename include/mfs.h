@@ -173,10 +173,11 @@ typedef struct {
                                         0 (default) = the fastest of SELL-32 (2, 4 or 8
                                         slots in flight) and one warp per row, each timed
                                         alone (best for one solve at a time: a mid-size
-                                        matrix cannot fill the GPU by itself); 1 = the
-                                        fastest SELL-32 variant only (best when many
-                                        systems run together, mfs_solve_batch, where the
-                                        GPU is full and throughput counts) */
+                                        matrix cannot fill the GPU by itself); 1 = the same,
+                                        but one warp per row only for rows of >= 32 blocks
+                                        (best when many systems run together,
+                                        mfs_solve_batch, where the GPU is full and
+                                        throughput counts) */
   int vcycle_tail;                   /* 1: a single-field V-cycle whose level above the
                                         coarsest is small (<= 48 KB of vectors, one warp per
                                         block row, explicit coarse inverse) runs that level

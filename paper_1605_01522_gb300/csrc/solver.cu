@@ -310,8 +310,12 @@ static int tune_pick(const dev::Sell &a, const dev::Sell &b, bool want32, cudaSt
   float t[4];
   t[0] = want32 ? time_spmv<float>(a, st) : time_spmv<double>(a, st);
   t[1] = want32 ? time_spmv<float>(a4, st) : time_spmv<double>(a4, st);
-  // throughput tuning leaves the one-warp-per-row layout out
-  t[2] = g_layout_tune == 1 ? 1e30f : (want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st));
+  // throughput tuning leaves the one-warp-per-row layout out for short rows
+  // (fewer blocks than lanes: idle lanes; SELL-32 moves more rows per
+  // microsecond when the GPU is full) but keeps it for long rows such as a
+  // restriction's, which one thread per row would walk serially
+  const bool short_rows = a.nnzb < 32 * a.nbr;
+  t[2] = g_layout_tune == 1 && short_rows ? 1e30f : (want32 ? time_spmv<float>(b, st) : time_spmv<double>(b, st));
   t[3] = !small ? 1e30f : (want32 ? time_spmv<float>(a8, st) : time_spmv<double>(a8, st));
   int best = 0;
   for (int c = 1; c < 4; ++c)
