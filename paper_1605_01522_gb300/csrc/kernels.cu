@@ -1448,11 +1448,6 @@ double fp64_rate(cudaStream_t s) {
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
 void set_recorder(Recorder *r) { g_rec = r; }
 
-cudaError_t launch_multi(const RecOp &op, unsigned grid, size_t smem, const void *tab, const MsBlock *map,
-                         const int *active, cudaStream_t s) {
-  void *args[3] = {(void *)&tab, (void *)&map, (void *)&active};
-  return cudaLaunchKernel(op.fn, dim3(grid), dim3(op.threads), args, smem, s);
-}
 HookBypass::HookBypass() { ++g_hook_off; }
 HookBypass::~HookBypass() { --g_hook_off; }
 

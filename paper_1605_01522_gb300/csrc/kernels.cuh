@@ -80,16 +80,13 @@ struct Recorder {
   std::vector<RecOp> ops;
 };
 void set_recorder(Recorder *r);
-// CTA c of a multi-system launch runs block bid (of nb) of table entry t,
-// which belongs to system g
+// CTA c of a multi-system launch of op.fn runs block bid (of nb) of table
+// entry t, which belongs to system g; the kernel takes (tab, map, active):
+// the device array of argument blocks (op.args layout, consecutive), the
+// CTA map and the per-system flags (0: skip) or null
 struct MsBlock {
   int t, bid, nb, g;
 };
-// issue `grid` CTAs of op's multi-system kernel: tab = device array of
-// argument blocks (op.args layout, consecutive), map = grid entries,
-// active = per-system flags (0: skip) or null
-cudaError_t launch_multi(const RecOp &op, unsigned grid, size_t smem, const void *tab, const MsBlock *map,
-                         const int *active, cudaStream_t s);
 
 template <typename T> inline const T *vals(const Sell &A);
 template <> inline const double *vals<double>(const Sell &A) { return A.v64; }
