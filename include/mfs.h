@@ -236,10 +236,11 @@ int mfs_clone(const struct mfs_handle *src, void *stream, struct mfs_handle **ou
  *    tables, and the steps of an iteration are one CUDA graph replayed once
  *    per iteration on a library stream; systems that finish stop taking
  *    part.  The systems are split into -nthreads groups of similar sizes
- *    (0: one group per 32 systems, at most 8) whose launches run
- *    concurrently.  The graph and tables are built on the first call with a
- *    handle list and kept for later calls with the same list and grouping
- *    (until one of its handles is freed).
+ *    (0: one group per 32 systems, at most 8); each group's iterations are
+ *    driven by its own host thread on its own library stream, so the groups
+ *    progress independently.  A group's graph and tables are built on the
+ *    first call with its handle list and kept for later calls with the same
+ *    list (until one of its handles is freed).
  *  nthreads > 0: that many host threads each drive one handle's FGMRES at
  *    a time on the handle's own stream, so the systems' kernels overlap.
  * Either way every result is bit-for-bit the one mfs_solve gives for that

@@ -1357,6 +1357,8 @@ static void merge_sequences(const std::vector<const std::vector<dev::RecOp> *> &
   }
 }
 
+static std::vector<std::vector<int>> size_groups(mfs_handle *const *hs, int nsys, int ngroups);
+
 struct FusedBatch {
   std::vector<mfs_handle *> hs;
   int nsys = 0;
@@ -1476,27 +1478,7 @@ struct FusedBatch {
     }
   }
 
-  // systems in `ngroups` groups of about equal dof totals, each of systems
-  // of similar size (sorted by size, cut into consecutive runs): the
-  // launches of one group are merged; different groups' launches run
-  // concurrently (independent chains of the graph)
-  std::vector<std::vector<int>> make_groups(int ngroups) const {
-    std::vector<int> order(nsys);
-    for (int k = 0; k < nsys; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
-    double total = 0.0;
-    for (int k = 0; k < nsys; ++k) total += (double)hs[k]->n;
-    std::vector<std::vector<int>> g(1);
-    double acc = 0.0;
-    for (int k : order) {
-      if (!g.back().empty() && acc >= total * (double)g.size() / ngroups && (int)g.size() < ngroups)
-        g.emplace_back();
-      g.back().push_back(k);
-      acc += (double)hs[k]->n;
-    }
-    for (auto &m : g) std::sort(m.begin(), m.end());
-    return g;
-  }
+  std::vector<std::vector<int>> make_groups(int ngroups) const { return size_groups(hs.data(), nsys, ngroups); }
 
   int ngroups_used = 1;
 
@@ -1634,6 +1616,26 @@ struct FusedBatch {
   }
 };
 
+// Systems in `ngroups` groups of about equal dof totals, each of systems of
+// similar size (sorted by size, cut into consecutive runs; positions in hs).
+static std::vector<std::vector<int>> size_groups(mfs_handle *const *hs, int nsys, int ngroups) {
+  ngroups = std::max(1, std::min(ngroups, nsys));
+  std::vector<int> order(nsys);
+  for (int k = 0; k < nsys; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->n > hs[b]->n; });
+  double total = 0.0;
+  for (int k = 0; k < nsys; ++k) total += (double)hs[k]->n;
+  std::vector<std::vector<int>> g(1);
+  double acc = 0.0;
+  for (int k : order) {
+    if (!g.back().empty() && acc >= total * (double)g.size() / ngroups && (int)g.size() < ngroups) g.emplace_back();
+    g.back().push_back(k);
+    acc += (double)hs[k]->n;
+  }
+  for (auto &m : g) std::sort(m.begin(), m.end());
+  return g;
+}
+
 // Process-wide cache of fused batches by their handle list (a batch holds
 // the handles' device addresses; mfs_free drops every batch of a handle).
 // (never destroyed itself: at process exit the CUDA runtime may already be
@@ -1664,7 +1666,7 @@ static FusedBatch *fused_for(mfs_handle *const *hv, int n, int ngroups) {
             "mfs fused batch: %d systems in %d groups, %zu + %zu + %zu merged launches per iteration (heads, "
             "preconditioners, Krylov steps), %lld CTAs per replay, %.1f KB patched per iteration, built in %.1f ms\n",
             n, b->ngroups_used, b->nhead, b->npre, b->ntail, (long long)b->ctas, b->patch_bytes / 1024.0, b->build_ms);
-  if (g_fused.size() >= 4) g_fused.erase(g_fused.begin());
+  if (g_fused.size() >= 64) g_fused.erase(g_fused.begin());
   g_fused.push_back(std::move(b));
   return g_fused.back().get();
 }
@@ -2663,20 +2665,52 @@ int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, d
     if (hs[k]->device != hs[0]->device) return fail(MFS_ERR_INVALID, "fused batch: handles on different devices");
   }
   if (nthreads <= 0) {
-    // fused: -nthreads groups, or (0) one group per 32 systems, at most 8
+    // fused: -nthreads groups, or (0) one group per 32 systems, at most 8;
+    // each group (systems of similar size) is one fused plan driven by its
+    // own host thread on its own stream, so the groups progress
+    // independently (one group's float64 Arnoldi passes overlap another's
+    // bandwidth-bound V-cycles, and host work overlaps GPU work)
     const int ngroups = nthreads < 0 ? -nthreads : std::max(1, std::min(8, (nsys + 31) / 32));
+    const std::vector<std::vector<int>> groups = size_groups(hs, nsys, ngroups);
     std::vector<mfs_info> inf(nsys);
     std::vector<int> st(nsys, MFS_OK);
+    std::vector<int> gcode(groups.size(), MFS_OK);
+    std::vector<std::string> gmsg(groups.size());
     const double t0 = now_ms();
-    try {
-      MFS_CUDA(cudaSetDevice(hs[0]->device));
-      FusedBatch *B = fused_for(hs, nsys, ngroups);
-      fused_solve(*B, rhs, x, tol, inf, st);
-    } catch (const CudaError &e) {
-      return fail(e.code, e.what());
-    } catch (const std::bad_alloc &) {
-      return fail(MFS_ERR_OOM, "host allocation failed");
-    }
+    auto run = [&](size_t g) {
+      try {
+        MFS_CUDA(cudaSetDevice(hs[0]->device));
+        const std::vector<int> &m = groups[g];
+        std::vector<mfs_handle *> hv;
+        std::vector<const double *> rv;
+        std::vector<double *> xv;
+        for (int k : m) {
+          hv.push_back(hs[k]);
+          rv.push_back(rhs[k]);
+          xv.push_back(x[k]);
+        }
+        std::vector<mfs_info> ginf(m.size());
+        std::vector<int> gst(m.size(), MFS_OK);
+        FusedBatch *B = fused_for(hv.data(), (int)hv.size(), 1);
+        fused_solve(*B, rv.data(), xv.data(), tol, ginf, gst);
+        for (size_t q = 0; q < m.size(); ++q) {
+          inf[m[q]] = ginf[q];
+          st[m[q]] = gst[q];
+        }
+      } catch (const CudaError &e) {
+        gcode[g] = e.code;
+        gmsg[g] = e.what();
+      } catch (const std::bad_alloc &) {
+        gcode[g] = MFS_ERR_OOM;
+        gmsg[g] = "host allocation failed";
+      }
+    };
+    std::vector<std::thread> pool;
+    for (size_t g = 1; g < groups.size(); ++g) pool.emplace_back(run, g);
+    run(0);
+    for (auto &t : pool) t.join();
+    for (size_t g = 0; g < groups.size(); ++g)
+      if (gcode[g] != MFS_OK) return fail(gcode[g], gmsg[g]);
     const double ms = now_ms() - t0;
     int rc = MFS_OK;
     for (int k = 0; k < nsys; ++k) {
