@@ -1306,19 +1306,21 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
 }
 
 // ---------------------------------------------------------------------------
-// Fused batch: the FGMRES iterations of many independent systems advance in
-// lockstep, each step of an iteration being ONE launch over all systems.
-// Every system's launch sequence (its preconditioner application, recorded
-// once from the same code that issues a solo solve, plus the Krylov steps,
-// re-recorded every iteration with that iteration's vectors) is merged with
-// the others' into multi-system launches: kernel K runs the blocks of every
-// system's launch of K in one grid, each CTA reading its system's argument
-// block from a table (dev::launch_multi).  The merged launches form one CUDA
-// graph per batch, replayed once per iteration; a per-system flag stops the
-// CTAs of systems that have finished.  Each system's kernels, arguments and
-// order are the ones of its solo solve, so its result is the solo result bit
-// for bit.  Restarts and the end of a cycle (x update, true residual) run as
-// ordinary launches for the systems concerned.
+// Fused batch: the FGMRES iterations of a group of independent systems
+// advance in lockstep, each step of an iteration being ONE launch over all of
+// them.  Every system's launch sequence (its preconditioner application,
+// recorded once from the same code that issues a solo solve, plus the Krylov
+// steps, re-recorded every iteration with that iteration's vectors) is merged
+// with the others' into multi-system launches: kernel K runs the blocks of
+// every system's launch of K in one grid, each CTA reading its system's
+// argument block from a table (the k_multi form of K).  The merged launches
+// form one CUDA graph per group, replayed once per iteration; a per-system
+// flag stops the CTAs of systems that have finished.  Each system's kernels,
+// arguments and order are the ones of its solo solve, so its result is the
+// solo result bit for bit.  Restarts and the end of a cycle (x update, true
+// residual) run as ordinary launches for the systems concerned.  A batch is
+// split into groups of similar systems, each driven by its own host thread
+// (mfs_solve_batch).
 // ---------------------------------------------------------------------------
 
 // Merge per-system launch sequences: repeatedly take the kernel (and block
@@ -1356,8 +1358,6 @@ static void merge_sequences(const std::vector<const std::vector<dev::RecOp> *> &
     groups.push_back(std::move(grp));
   }
 }
-
-static std::vector<std::vector<int>> size_groups(mfs_handle *const *hs, int nsys, int ngroups);
 
 struct FusedBatch {
   std::vector<mfs_handle *> hs;
@@ -1434,22 +1434,14 @@ struct FusedBatch {
     dev::set_recorder(nullptr);
   }
 
-  // merge one segment group by group; its launches go to `launches`, its
-  // tables at the current end of the table layout
+  // merge one segment; its launches go to `launches`, its tables at the
+  // current end of the table layout
   void add_segment(std::vector<dev::Recorder> &recs, std::vector<std::vector<std::pair<int, int>>> *at,
-                   std::vector<unsigned char> &tabs, std::vector<dev::MsBlock> &maps,
-                   const std::vector<std::vector<int>> &sysgroups) {
+                   std::vector<unsigned char> &tabs, std::vector<dev::MsBlock> &maps) {
+    std::vector<const std::vector<dev::RecOp> *> seqs;
+    for (auto &r : recs) seqs.push_back(&r.ops);
     std::vector<std::vector<std::pair<int, int>>> groups;
-    for (const auto &members : sysgroups) {
-      std::vector<const std::vector<dev::RecOp> *> seqs;
-      for (int k : members) seqs.push_back(&recs[k].ops);
-      std::vector<std::vector<std::pair<int, int>>> g;
-      merge_sequences(seqs, g);
-      for (auto &grp : g) {
-        for (auto &e : grp) e.first = members[e.first];
-        groups.push_back(std::move(grp));
-      }
-    }
+    merge_sequences(seqs, groups);
     if (at) {
       at->assign(nsys, {});
       for (int k = 0; k < nsys; ++k) (*at)[k].resize(recs[k].ops.size());
@@ -1478,17 +1470,11 @@ struct FusedBatch {
     }
   }
 
-  std::vector<std::vector<int>> make_groups(int ngroups) const { return size_groups(hs.data(), nsys, ngroups); }
-
-  int ngroups_used = 1;
-
   // stream: the stream to run on (a sub-plan takes its parent's), or null
   // for a new library stream
-  void build(mfs_handle *const *hv, int n, int ngroups, cudaStream_t stream = nullptr) {
+  void build(mfs_handle *const *hv, int n, cudaStream_t stream = nullptr) {
     hs.assign(hv, hv + n);
     nsys = n;
-    ngroups_used = std::max(1, std::min(ngroups, n));
-    const std::vector<std::vector<int>> sysgroups = make_groups(ngroups_used);
     MFS_CUDA(cudaSetDevice(hs[0]->device));
     if (stream) {
       s = stream;
@@ -1517,12 +1503,12 @@ struct FusedBatch {
     // tables of the per-iteration launches first (one upload per iteration)
     std::vector<unsigned char> tabs;
     std::vector<dev::MsBlock> maps;
-    add_segment(heads, &head_at, tabs, maps, sysgroups);
+    add_segment(heads, &head_at, tabs, maps);
     const size_t nhead = launches.size();
-    add_segment(tails, &tail_at, tabs, maps, sysgroups);
+    add_segment(tails, &tail_at, tabs, maps);
     patch_bytes = tabs.size();
     const size_t ntail_end = launches.size();
-    add_segment(pre, nullptr, tabs, maps, sysgroups);
+    add_segment(pre, nullptr, tabs, maps);
     tab_bytes = tabs.size();
     // issue order: heads, preconditioners, tails
     std::vector<Launch> order;
@@ -1553,8 +1539,9 @@ struct FusedBatch {
     MFS_CUDA(cudaStreamSynchronize(0));
     // one graph: every merged launch, then the Arnoldi sums to the host.  A
     // launch depends on the previous launches of the systems it serves, so
-    // launches over disjoint sets of systems may run at the same time; each
-    // system's own launches keep their order.
+    // launches over disjoint sets of systems (where the systems' sequences
+    // differ) may run at the same time; each system's own launches keep
+    // their order.
     cudaGraph_t graph = nullptr;
     MFS_CUDA(cudaGraphCreate(&graph, 0));
     struct GraphGuard {
@@ -1600,7 +1587,7 @@ struct FusedBatch {
     std::vector<mfs_handle *> hv;
     for (int p : live) hv.push_back(hs[p]);
     std::unique_ptr<FusedBatch> b(new FusedBatch());
-    b->build(hv.data(), (int)hv.size(), std::max(1, std::min(ngroups_used, ((int)hv.size() + 31) / 32)), s);
+    b->build(hv.data(), (int)hv.size(), s);
     return subs.emplace(live, std::move(b)).first->second.get();
   }
 
@@ -1652,20 +1639,20 @@ static void drop_fused(const mfs_handle *h) {
       ++i;
 }
 
-static FusedBatch *fused_for(mfs_handle *const *hv, int n, int ngroups) {
+static FusedBatch *fused_for(mfs_handle *const *hv, int n) {
   std::lock_guard<std::mutex> lock(g_fused_mu);
   for (auto &b : g_fused)
-    if (b->nsys == n && b->ngroups_used == std::max(1, std::min(ngroups, n)) && std::equal(b->hs.begin(), b->hs.end(), hv))
+    if (b->nsys == n && std::equal(b->hs.begin(), b->hs.end(), hv))
       return b.get();
   std::unique_ptr<FusedBatch> b(new FusedBatch());
   const double t0 = now_ms();
-  b->build(hv, n, ngroups);
+  b->build(hv, n);
   b->build_ms = now_ms() - t0;
   if (hv[0]->prm.verbose)
     fprintf(stderr,
-            "mfs fused batch: %d systems in %d groups, %zu + %zu + %zu merged launches per iteration (heads, "
-            "preconditioners, Krylov steps), %lld CTAs per replay, %.1f KB patched per iteration, built in %.1f ms\n",
-            n, b->ngroups_used, b->nhead, b->npre, b->ntail, (long long)b->ctas, b->patch_bytes / 1024.0, b->build_ms);
+            "mfs fused batch: %d systems, %zu + %zu + %zu merged launches per iteration (heads, preconditioners, "
+            "Krylov steps), %lld CTAs per replay, %.1f KB patched per iteration, built in %.1f ms\n",
+            n, b->nhead, b->npre, b->ntail, (long long)b->ctas, b->patch_bytes / 1024.0, b->build_ms);
   if (g_fused.size() >= 64) g_fused.erase(g_fused.begin());
   g_fused.push_back(std::move(b));
   return g_fused.back().get();
@@ -2691,7 +2678,7 @@ int mfs_solve_batch(mfs_handle *const *hs, int nsys, const double *const *rhs, d
         }
         std::vector<mfs_info> ginf(m.size());
         std::vector<int> gst(m.size(), MFS_OK);
-        FusedBatch *B = fused_for(hv.data(), (int)hv.size(), 1);
+        FusedBatch *B = fused_for(hv.data(), (int)hv.size());
         fused_solve(*B, rv.data(), xv.data(), tol, ginf, gst);
         for (size_t q = 0; q < m.size(); ++q) {
           inf[m[q]] = ginf[q];
