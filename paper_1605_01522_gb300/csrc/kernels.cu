@@ -203,32 +203,7 @@ __device__ __forceinline__ void bsr_warp_row(const int32_t *__restrict__ rp, con
   const int lo = rp[row], hi = rp[row + 1];
 #pragma unroll
   for (int r = 0; r < BR; ++r) acc[r] = T(0);
-  // U of the lane's blocks in flight at once (their loads issued before the
-  // first product): long rows of small blocks were load-latency bound.  The
-  // products are added in the same order as one block at a time.
-  constexpr int U = BR * BC <= 4 ? 4 : (BR * BC <= 9 ? 2 : 1);
-  int k = lo + lane;
-  if constexpr (U > 1)
-  for (; k + 32 * (U - 1) < hi; k += 32 * U) {
-    int64_t c[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) c[u] = __ldg(col + k + 32 * u);
-    T blk[U][BR * BC];
-#pragma unroll
-    for (int u = 0; u < U; ++u) ldg_block<BR * BC, T>(val + (int64_t)(k + 32 * u) * (BR * BC), blk[u]);
-    T xv[U][BC];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int q = 0; q < BC; ++q) xv[u][q] = __ldg(x + c[u] * BC + q);
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-#pragma unroll
-      for (int r = 0; r < BR; ++r)
-#pragma unroll
-        for (int q = 0; q < BC; ++q) acc[r] += blk[u][r * BC + q] * xv[u][q];
-  }
-  for (; k < hi; k += 32) {
+  for (int k = lo + lane; k < hi; k += 32) {
     const int64_t c = __ldg(col + k);
     T xv[BC];
 #pragma unroll
