@@ -34,6 +34,11 @@ WORKLOADS = {
                            dict(max_levels=5, coarse_max=1000),
                            {"simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag"),
                             "simple+sa": dict(simple_group=[0, 0, 0, 1], simple_approx="diag", pg_off=True)}),
+    # config 2 at 64^3 (1,394,250 dofs) and config 0 (the 3,267-dof 2D system, 3 levels)
+    "fsi_box_ne64": (lambda: inputs.fsi_box(ne=64, seed=2), dict(max_levels=5, coarse_max=1000),
+                     {"simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
+    "thermo_elastic_2d_ne32": (lambda: inputs.thermo_elastic_2d(ne=32, seed=0), dict(max_levels=3, coarse_max=0),
+                               {"bgs_amg": {}, "amg_bgs": {}, "simple": {}}),
     "fsi_box_ne48": (lambda: inputs.fsi_box(ne=48, seed=2), dict(max_levels=5, coarse_max=1000),
                      {"bgs_amg": {}, "simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag"),
                       "amg_simple": dict(simple_group=[0, 0, 0, 1], simple_approx="diag")}),
