@@ -189,3 +189,36 @@ def test_fullsize_oseen_petrov_galerkin(prec):
         assert abs(info["iters"] - ref["iters"]) <= max(1, round(0.01 * ref["iters"])), (info["iters"], ref["iters"])
     else:
         assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
+
+
+def test_split_box_64_simple_matches_oracle_count():
+    """Config 2 at 64^3 (1,394,250 dofs), SIMPLE(diag) as benchmarked:
+    FP64 within 1 % (+1) of the oracle's count (a long restarted run),
+    FP32P within 10 % (+1); true residuals <= 1e-8 recomputed on the host."""
+    ref = _counts()["fsi_box_ne64/simple"]
+    s = inputs.fsi_box(ne=64, seed=2)
+    D = precond.assemble(s.scipy_blocks(), 4)
+    for prec in ("fp64", "fp32p"):
+        with mfs.Solver(s, precond="simple", precision=prec, **KW, **FSI_SIMPLE) as lib:
+            x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+            x = x.cpu().numpy()
+        assert rc == mfs.OK
+        assert np.linalg.norm(s.rhs - D @ x) <= 1e-8 * np.linalg.norm(s.rhs)
+        if prec == "fp64":
+            assert abs(info["iters"] - ref["iters"]) <= max(1, round(0.01 * ref["iters"])), (info["iters"], ref["iters"])
+        else:
+            assert info["iters"] <= int(np.ceil(1.10 * ref["iters"])) + 1, (info["iters"], ref["iters"])
+
+
+@pytest.mark.parametrize("pc", ["bgs_amg", "amg_bgs", "simple"])
+def test_thermo_elastic_2d_matches_oracle_count(pc):
+    """Config 0 (3,267 dofs, 3 SA-AMG levels) as benchmarked: iterations
+    within 1 of the oracle's stored count in FP64."""
+    ref = _counts()[f"thermo_elastic_2d_ne32/{pc}"]
+    s = inputs.thermo_elastic_2d(ne=32, seed=0)
+    D = precond.assemble(s.scipy_blocks(), 2)
+    with mfs.Solver(s, precond=pc, max_levels=3, coarse_max=0) as lib:
+        x, info, rc = lib.solve(torch.from_numpy(s.rhs).cuda(), tol=1e-8)
+        x = x.cpu().numpy()
+    assert rc == mfs.OK and np.linalg.norm(s.rhs - D @ x) <= 1e-8 * np.linalg.norm(s.rhs)
+    assert abs(info["iters"] - ref["iters"]) <= 1, (info["iters"], ref["iters"])
