@@ -50,23 +50,51 @@ void set_last_error(const char *msg) { g_last_error = msg; }
                       std::string(#call) + ": " + cudaGetErrorString(e_));                  \
   } while (0)
 
+// Device memory of the library comes from the device's stream-ordered pool
+// (cudaMallocAsync / cudaFreeAsync on the legacy stream): unlike cudaFree, a
+// free does not wait for the whole device, so handles can come and go while
+// other handles' work runs (setups and solves of a server).  Memory is freed
+// only when no stream still uses it (the owner has synchronised its
+// streams).  Freed memory above the pool's release threshold goes back to
+// the system.
+void pool_setup_once() {
+  static std::mutex mu;
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = 4ull << 30;  // keep up to 4 GB of freed memory for reuse
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 struct Arena {
   std::vector<std::pair<void *, int64_t>> ptrs;
   int64_t bytes = 0;
   template <typename T> T *alloc(int64_t count) {
     if (count <= 0) return nullptr;
+    pool_setup_once();
     void *p = nullptr;
-    MFS_CUDA(cudaMalloc(&p, (size_t)count * sizeof(T)));
+    MFS_CUDA(cudaMallocAsync(&p, (size_t)count * sizeof(T), 0));
+    // the allocation is ordered on the legacy stream; once that stream has
+    // passed it, any stream may use the memory
+    MFS_CUDA(cudaStreamSynchronize(0));
     ptrs.push_back({p, count * (int64_t)sizeof(T)});
     // the plain-BSR kernels read blocks with 16-byte loads from the start of
-    // a value array (cudaMalloc aligns to 256 bytes)
+    // a value array (pool allocations are 256-byte aligned)
     if (reinterpret_cast<uintptr_t>(p) & 15) throw CudaError(MFS_ERR_CUDA, "device allocation not 16-byte aligned");
     bytes += count * (int64_t)sizeof(T);
     return (T *)p;
   }
-  // synchronous copy on the legacy stream: a copy from pageable memory may
-  // still be in flight when this returns, so work on other (non-blocking)
-  // streams that reads the result must first synchronise with stream 0
+  // synchronous copy on the legacy stream (after the allocation there): a
+  // copy from pageable memory may still be in flight when this returns, so
+  // work on other (non-blocking) streams that reads the result must first
+  // synchronise with stream 0
   template <typename T> T *upload(const std::vector<T> &h) {
     T *p = alloc<T>((int64_t)h.size());
     if (p) MFS_CUDA(cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
@@ -74,23 +102,60 @@ struct Arena {
   }
   template <typename T> T *zeros(int64_t count) {
     T *p = alloc<T>(count);
-    if (p) MFS_CUDA(cudaMemset(p, 0, (size_t)count * sizeof(T)));
+    if (p) MFS_CUDA(cudaMemsetAsync(p, 0, (size_t)count * sizeof(T), 0));
     return p;
   }
+  // callers free only memory no stream is still using (the owner's streams
+  // have been synchronised)
   void release(const void *p) {
     if (!p) return;
     for (size_t k = 0; k < ptrs.size(); ++k)
       if (ptrs[k].first == p) {
-        cudaFree(ptrs[k].first);
+        cudaFreeAsync(ptrs[k].first, 0);
         bytes -= ptrs[k].second;
         ptrs.erase(ptrs.begin() + (long)k);
         return;
       }
   }
   ~Arena() {
-    for (auto &q : ptrs) cudaFree(q.first);
+    for (auto &q : ptrs) cudaFreeAsync(q.first, 0);
   }
 };
+
+// Pinned host blocks, kept by power-of-two size for reuse (cudaFreeHost
+// would wait for the whole device): a handle's or a fused plan's few small
+// pinned buffers come and go with it.
+struct PinnedCache {
+  std::mutex mu;
+  std::map<size_t, std::vector<void *>> free;
+  static size_t round_up(size_t b) {
+    size_t c = 256;
+    while (c < b) c <<= 1;
+    return c;
+  }
+  void *get(size_t bytes) {
+    const size_t c = round_up(bytes);
+    {
+      std::lock_guard<std::mutex> lock(mu);
+      auto &v = free[c];
+      if (!v.empty()) {
+        void *p = v.back();
+        v.pop_back();
+        return p;
+      }
+    }
+    void *p = nullptr;
+    MFS_CUDA(cudaMallocHost(&p, c));
+    return p;
+  }
+  void put(void *p, size_t bytes) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lock(mu);
+    free[round_up(bytes)].push_back(p);
+  }
+};
+// never destroyed (the CUDA runtime may be gone at process exit)
+static PinnedCache &g_pinned = *new PinnedCache();
 
 // Layout autotuning: matrices with at least kTuneMinRows block rows are built
 // in both layouts (SELL-32, one thread per block row, with 2, 4 or 8 block
@@ -1081,7 +1146,7 @@ struct mfs_handle {
   std::vector<IterGraph> graphs;  // per Krylov index j
   ~mfs_handle() {
     for (auto &g : graphs) g.release();
-    if (hpin) cudaFreeHost(hpin);
+    if (hpin) g_pinned.put(hpin, 256 * sizeof(double));
     if (entry) cudaEventDestroy(entry);
     if (own_stream && s) cudaStreamDestroy(s);
   }
@@ -1396,10 +1461,10 @@ struct FusedBatch {
     subs.clear();
     if (s) cudaStreamSynchronize(s);
     if (exec) cudaGraphExecDestroy(exec);
-    if (htab) cudaFreeHost(htab);
-    if (hactive) cudaFreeHost(hactive);
-    if (hbpin) cudaFreeHost(hbpin);
-    if (ypin) cudaFreeHost(ypin);
+    g_pinned.put(htab, std::max<size_t>(tab_bytes, 16));
+    g_pinned.put(hactive, (size_t)nsys * sizeof(int));
+    g_pinned.put(hbpin, (size_t)136 * nsys * sizeof(double));
+    g_pinned.put(ypin, (size_t)64 * nsys * sizeof(double));
     if (s && own_stream) cudaStreamDestroy(s);
   }
   double *sums(int k) { return hb + (int64_t)k * 136; }
@@ -1491,9 +1556,9 @@ struct FusedBatch {
       }
     hb = ar.zeros<double>((int64_t)136 * nsys);
     dactive = ar.zeros<int>(nsys);
-    MFS_CUDA(cudaMallocHost(&hbpin, (size_t)136 * nsys * sizeof(double)));
-    MFS_CUDA(cudaMallocHost(&ypin, (size_t)64 * nsys * sizeof(double)));
-    MFS_CUDA(cudaMallocHost(&hactive, (size_t)nsys * sizeof(int)));
+    hbpin = (double *)g_pinned.get((size_t)136 * nsys * sizeof(double));
+    ypin = (double *)g_pinned.get((size_t)64 * nsys * sizeof(double));
+    hactive = (int *)g_pinned.get((size_t)nsys * sizeof(int));
     std::vector<dev::Recorder> heads(nsys), pre(nsys), tails(nsys);
     for (int k = 0; k < nsys; ++k) {
       record_head(k, 0, 1.0, heads[k]);
@@ -1529,7 +1594,7 @@ struct FusedBatch {
     this->npre = npre;
     ntail = ntail_end - nhead;
     for (const Launch &L : launches) ctas += L.grid;
-    MFS_CUDA(cudaMallocHost(&htab, std::max<size_t>(tab_bytes, 16)));
+    htab = (unsigned char *)g_pinned.get(std::max<size_t>(tab_bytes, 16));
     std::memcpy(htab, tabs.data(), tab_bytes);
     dtab = ar.alloc<unsigned char>((int64_t)std::max<size_t>(tab_bytes, 16));
     dmap = ar.alloc<dev::MsBlock>((int64_t)std::max<size_t>(maps.size(), 1));
@@ -2297,7 +2362,7 @@ void alloc_solver_work(mfs_handle *h) {
     h->in32 = h->ar.zeros<float>(h->n);
     h->out32 = h->ar.zeros<float>(h->n);
   }
-  MFS_CUDA(cudaMallocHost(&h->hpin, 256 * sizeof(double)));
+  h->hpin = (double *)g_pinned.get(256 * sizeof(double));
 }
 
 int fail(int code, const std::string &msg) {
