@@ -27,8 +27,6 @@
 #include <type_traits>
 #include <vector>
 
-#include <omp.h>
-
 #include "amg_setup.h"
 #include "setup_gpu.h"
 #include "kernels.cuh"
@@ -2367,22 +2365,6 @@ void alloc_solver_work(mfs_handle *h) {
   h->hpin = (double *)g_pinned.get(256 * sizeof(double));
 }
 
-// Setups running at once in this process: each takes an equal share of the
-// host cores for its OpenMP regions (concurrent setups of a server would
-// otherwise each start a team as wide as the machine).
-static std::atomic<int> g_setups_running{0};
-struct HostCoreShare {
-  int saved;
-  HostCoreShare() : saved(omp_get_max_threads()) {
-    const int k = ++g_setups_running;
-    omp_set_num_threads(std::max(1, omp_get_num_procs() / k));
-  }
-  ~HostCoreShare() {
-    --g_setups_running;
-    omp_set_num_threads(saved);
-  }
-};
-
 int fail(int code, const std::string &msg) {
   g_last_error = msg;
   return code;
@@ -2450,7 +2432,6 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
     explicit TuneMode(int m) { g_layout_tune = m; }
     ~TuneMode() { g_layout_tune = 0; }
   } tune_mode(p.layout_tune);
-  HostCoreShare cores;
   try {
     h->prm = p;
     h->nf = nfields;
