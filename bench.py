@@ -294,12 +294,14 @@ def _oracle_worker(core, tasks, results):
         cmd = tasks.get()
         if cmd is None:
             return
-        count, budget = cmd
+        count, budget, xpath = cmd
         out, t_start = [], time.perf_counter()
         while True:
             t0 = time.perf_counter()
             r = krylov.fgmres(lambda v: D @ v, M, rhs, 1e-8, 50)
             out.append((time.perf_counter() - t0, r.iters, float(r.relres)))
+            if xpath and len(out) == 1:  # the oracle's solution, for the GPU arm's error against it
+                np.save(xpath, r.x)
             done = len(out) >= count if count else time.perf_counter() - t_start >= budget
             if done:
                 break
@@ -323,9 +325,10 @@ class OraclePool:
             p.start()
 
     def run(self, cmds):
-        """cmds[i] = (count, budget_s) for worker i, or None to leave it idle;
-        a worker runs `count` solves, or (count 0) solves until budget_s has
-        passed (at least one).  Returns (wall seconds from the first command
+        """cmds[i] = (count, budget_s, xpath) for worker i, or None to leave it
+        idle; a worker runs `count` solves, or (count 0) solves until budget_s
+        has passed (at least one), and saves its first solution to xpath
+        (.npy) unless xpath is None.  Returns (wall seconds from the first command
         to the last result, [(seconds, iters, relres) of every solve])."""
         t0 = time.perf_counter()
         busy = 0
@@ -346,7 +349,8 @@ class OraclePool:
 
 
 def split_steps(total, nproc):
-    return [(total // nproc + (1 if i < total % nproc else 0), 0.0) if i < total else None for i in range(nproc)]
+    return [(total // nproc + (1 if i < total % nproc else 0), 0.0, None) if i < total else None
+            for i in range(nproc)]
 
 
 def run_reference(args, rank, world):
@@ -394,8 +398,8 @@ def run_oracle_baseline(args):
     print("ready", flush=True)
     sys.stdin.readline()
     budget = args.baseline_s
-    w1, r1 = pool.run([(0, budget)] + [None] * (len(cores) - 1))
-    wn, rn = pool.run([(0, budget)] * len(cores))
+    w1, r1 = pool.run([(0, budget, args.oracle_x)] + [None] * (len(cores) - 1))
+    wn, rn = pool.run([(0, budget, None)] * len(cores))
     pool.close()
     print(json.dumps({"single": {"solves": len(r1), "wall_s": w1, "value": len(r1) / w1,
                                  "iters": sorted({r[1] for r in r1}), "relres": max(r[2] for r in r1)},
@@ -410,10 +414,11 @@ class BaselineChild:
     only when release() is called)."""
 
     def __init__(self, args):
+        self.xpath = os.path.join(tempfile.gettempdir(), f"mfs_oracle_x_{os.getpid()}.npy")
         cmd = [sys.executable, os.path.abspath(__file__), "--impl", "reference", "--oracle-baseline",
                "--workload", args.workload, "--ne", str(NE), "--precond", args.precond,
                "--smoother", args.smoother, "--simple-pred", args.simple_pred,
-               "--baseline-s", str(args.baseline_s)] + (["--no-pg"] if args.no_pg else [])
+               "--baseline-s", str(args.baseline_s), "--oracle-x", self.xpath] + (["--no-pg"] if args.no_pg else [])
         self.proc = subprocess.Popen(cmd, stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True)
 
     def result(self):
@@ -426,6 +431,15 @@ class BaselineChild:
                 res = json.loads(line)
         self.proc.wait()
         return res
+
+    def solution(self):
+        """The oracle's solution of the workload (x0 = 0, tol 1e-8), or None."""
+        try:
+            x = np.load(self.xpath)
+            os.remove(self.xpath)
+            return x
+        except OSError:
+            return None
 
 
 def run_mfs(args, rank, world):
@@ -503,6 +517,7 @@ def run_mfs(args, rank, world):
     # true residual, recomputed through the library's FP64 matvec (device)
     r = b - lib.matvec(x)
     relres = float(torch.linalg.norm(r) / torch.linalg.norm(b))
+    x_last = x.cpu().numpy()  # the last timed solve's solution (x0 = 0), compared with the oracle's below
     # end-to-end: host (pinned) vectors, copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -606,8 +621,16 @@ def run_mfs(args, rank, world):
     if rank != 0:
         return
     cpu = None
+    vs_oracle = None
     if child is not None:
         b = child.result()
+        xo = child.solution()
+        if b and xo is not None:
+            vs_oracle = {"x_rel_err": float(np.linalg.norm(x_last - xo) / np.linalg.norm(xo)),
+                         "iters": infos[-1]["iters"], "oracle_iters": b["single"]["iters"],
+                         "true_relres": relres, "oracle_relres": b["single"]["relres"],
+                         "note": "||x - x_oracle|| / ||x_oracle||, same system and right-hand side, x0 = 0; "
+                                 "the FP64 CPU oracle with its own hierarchy"}
         if b:
             one, alln = b["single"], b["all"]
             cpu = {"value": one["value"], "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -631,6 +654,7 @@ def run_mfs(args, rank, world):
         "roofline": roof,
         "roofline_top_f32": secondary,
         "vcycle": vcycle,
+        "vs_oracle": vs_oracle,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches_total),
@@ -810,6 +834,7 @@ def main():
     ap.add_argument("--ne", type=int, default=None,
                     help="mesh edge (default: 64 for box/cons, 48 for fsi/oseen, 32 for te2d)")
     ap.add_argument("--oracle-baseline", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-x", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--baseline-s", type=float, default=10.0,
                     help="CPU baseline: each oracle process runs whole solves for at least this long (one at least)")
     ap.add_argument("--no-graphs", action="store_true")
