@@ -987,6 +987,32 @@ struct KScaleConvert {
   }
 };
 
+// the same with a = 1 / sqrt(nrm2[0]) read from device memory (the norm of
+// the previous Arnoldi vector, so that a captured iteration graph normalises
+// its input itself); out may be null (in-place scaling only)
+template <typename TO>
+__device__ __forceinline__ void d_scale_convert_dev(double *__restrict__ v, const double *__restrict__ nrm2,
+                                                    TO *__restrict__ out, int64_t n, int bid_, int nb_) {
+  const double a = 1.0 / sqrt(nrm2[0]);
+  for (int64_t i = (int64_t)bid_ * blockDim.x + threadIdx.x; i < n; i += (int64_t)nb_ * blockDim.x) {
+    const double t = a * v[i];
+    v[i] = t;
+    if (out) out[i] = (TO)t;
+  }
+}
+template <typename TO>
+struct KScaleConvertDev {
+  static constexpr int kMaxThreads = kThreads;
+  struct Args {
+    double *v;
+    const double *nrm2;
+    TO *out;
+    int64_t n;
+  };
+  static __device__ __forceinline__ void run(const Args &a, int bid, int nb) {
+    d_scale_convert_dev<TO>(a.v, a.nrm2, a.out, a.n, bid, nb);
+  }
+};
 
 __device__ __forceinline__ double block_sum(double v, double *sh) {
 #pragma unroll
@@ -1733,6 +1759,13 @@ void scale_convert(double *v, double a, TO *out, int64_t n, cudaStream_t s) {
 }
 template void scale_convert<float>(double *, double, float *, int64_t, cudaStream_t);
 template void scale_convert<double>(double *, double, double *, int64_t, cudaStream_t);
+template <typename TO>
+void scale_convert_dev(double *v, const double *nrm2, TO *out, int64_t n, cudaStream_t s) {
+  HookScope hs(s, K_VECTOR, (16.0 + (out ? sizeof(TO) : 0)) * n, 8, n, (double)n);
+  if (n) go<KScaleConvertDev<TO>>(ew_grid(n), kThreads, 0, s, {v, nrm2, out, n});
+}
+template void scale_convert_dev<float>(double *, const double *, float *, int64_t, cudaStream_t);
+template void scale_convert_dev<double>(double *, const double *, double *, int64_t, cudaStream_t);
 
 void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s) {
   HookScope hs(s, K_VECTOR, 16.0 * n, 6, n, (double)n);

@@ -197,6 +197,9 @@ template <typename TI, typename TO> void convert(const TI *in, TO *out, int64_t 
 void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s);                      // y = a x
 // v = a v and out = (TO) v in one pass
 template <typename TO> void scale_convert(double *v, double a, TO *out, int64_t n, cudaStream_t s);
+// the same with a = 1 / sqrt(nrm2[0]) taken from device memory; out may be null
+template <typename TO>
+void scale_convert_dev(double *v, const double *nrm2, TO *out, int64_t n, cudaStream_t s);
 
 // Arnoldi (float64).  V holds k row vectors of length n, row q at V + q*ldv.
 int mdot_blocks(int64_t n);

@@ -1116,6 +1116,9 @@ struct HostSide {
 
 using namespace mfs;
 
+constexpr int kHostSlots = 520;  // doubles in hdev / hpin
+constexpr int kDotSlot = 512;
+
 struct mfs_handle {
   mfs_params prm{};
   const std::map<std::pair<int, int>, RawDev> *raw = nullptr;  // input blocks on the device (setup only)
@@ -1137,7 +1140,10 @@ struct mfs_handle {
   double *V = nullptr, *Z = nullptr, *xd = nullptr, *bd = nullptr, *rd = nullptr, *partial = nullptr;
   double *hdev = nullptr, *ydev = nullptr;
   float *in32 = nullptr, *out32 = nullptr;
+  // hdev / hpin: the Arnoldi sums of iterations of even and odd Krylov index
+  // at 0 and 256 (136 each), a dot product at kDotSlot
   double *hpin = nullptr;
+  cudaEvent_t iter_ev[2] = {nullptr, nullptr};  // completion of the last iteration of each parity
   double setup_ms = 0.0;
   std::unique_ptr<EventProf> prof;
   bool own_stream = false;
@@ -1146,7 +1152,9 @@ struct mfs_handle {
   std::vector<IterGraph> graphs;  // per Krylov index j
   ~mfs_handle() {
     for (auto &g : graphs) g.release();
-    if (hpin) g_pinned.put(hpin, 256 * sizeof(double));
+    if (hpin) g_pinned.put(hpin, kHostSlots * sizeof(double));
+    for (auto e : iter_ev)
+      if (e) cudaEventDestroy(e);
     if (entry) cudaEventDestroy(entry);
     if (own_stream && s) cudaStreamDestroy(s);
   }
@@ -1185,11 +1193,11 @@ void matvec(mfs_handle *h, const double *x, double *y) {
   }
 }
 
-void precond_apply(mfs_handle *h, const double *v, double *z) {
+void precond_apply(mfs_handle *h, const double *v, double *z, bool staged = false) {
   if (h->p64) {
     h->p64->apply(v, z);
   } else {
-    dev::convert<double, float>(v, h->in32, h->n, h->s);
+    if (!staged) dev::convert<double, float>(v, h->in32, h->n, h->s);  // staged: in32 holds v already
     h->p32->apply(h->in32, h->out32);
     dev::convert<float, double>(h->out32, z, h->n, h->s);
   }
@@ -1198,10 +1206,10 @@ void precond_apply(mfs_handle *h, const double *v, double *z) {
 // ||x||^2 of n doubles, deterministic, result in host memory
 double dot_host(mfs_handle *h, const double *x, const double *y) {
   dev::mdot(x, 0, 1, y, h->n, h->partial, h->nblk, h->s);
-  dev::reduce_partials(h->partial, 1, h->nblk, h->hdev, h->s);
-  MFS_CUDA(cudaMemcpyAsync(h->hpin, h->hdev, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + kDotSlot, h->s);
+  MFS_CUDA(cudaMemcpyAsync(h->hpin + kDotSlot, h->hdev + kDotSlot, sizeof(double), cudaMemcpyDeviceToHost, h->s));
   MFS_CUDA(cudaStreamSynchronize(h->s));
-  return h->hpin[0];
+  return h->hpin[kDotSlot];
 }
 
 // Capture body() once per Krylov index j into a CUDA graph and replay it:
@@ -1328,28 +1336,59 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
   if (!std::isfinite(r0)) return MFS_ERR_BREAKDOWN;
   KrylovLS ls(m);
   ls.r0 = r0;
-  double *hp = h->hpin;
+  double *hdb[2] = {h->hdev, h->hdev + 256};
+  double *hpb[2] = {h->hpin, h->hpin + 256};
+  // Iteration j of a cycle: for j > 0 v_j = w / |w| (w = V_j as the previous
+  // iteration left it, its norm read on the device), z_j = P^-1 v_j,
+  // w = A z_j and the CGS2 passes, whose sums land in buffer j % 2 (device
+  // and pinned host), then event j % 2.  Nothing in it waits for the host's
+  // Givens step of iteration j - 1, so iteration j + 1 is queued before the
+  // host reads column j unless the residual estimate says iteration j may end
+  // the cycle; the GPU then runs the iterations back to back.  An iteration
+  // queued past the end of a cycle writes only V_{j+2}, Z_{j+1} and its own
+  // buffers, none of which the cycle end reads.
+  auto enqueue = [&](int j) {
+    double *vj = h->V + (int64_t)j * n;
+    double *zj = h->Z + (int64_t)j * n;
+    double *w = h->V + (int64_t)(j + 1) * n;
+    auto body = [&]() {
+      if (j > 0) {
+        const double *nrm2 = hdb[(j - 1) & 1] + 128;
+        if (h->p32) dev::scale_convert_dev<float>(vj, nrm2, h->in32, n, s);
+        else dev::scale_convert_dev<double>(vj, nrm2, nullptr, n, s);
+      }
+      precond_apply(h, vj, zj, j > 0);
+      matvec(h, zj, w);
+      arnoldi(h, j, w, hdb[j & 1], s);
+      MFS_CUDA(cudaMemcpyAsync(hpb[j & 1], hdb[j & 1], 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    };
+    if (h->use_graphs) run_graph(h, j, body, prof);
+    else body();
+    MFS_CUDA(cudaEventRecord(h->iter_ev[j & 1], s));
+  };
+  auto fail_drained = [&](int code) {  // no queued iteration may outlive the call
+    cudaStreamSynchronize(s);
+    return code;
+  };
   while (true) {
-    const double beta = std::sqrt(dot_host(h, r, r));
+    const double beta = restarts == 0 ? r0 : std::sqrt(dot_host(h, r, r));
+    if (prof) h->prof->collect();  // the stream is idle here
     dev::scale(r, 1.0 / beta, h->V, n, s);
     ls.start_cycle(beta);
+    double e_last = beta / r0, rho = 1.0;  // last estimate and its last ratio
+    int queued = 0;
+    enqueue(queued++);
     for (int j = 0; j < m; ++j) {
-      double *vj = h->V + (int64_t)j * n;
-      double *zj = h->Z + (int64_t)j * n;
-      double *w = h->V + (int64_t)(j + 1) * n;
-      auto body = [&]() {
-        precond_apply(h, vj, zj);
-        matvec(h, zj, w);
-        arnoldi(h, j, w, h->hdev, s);
-        MFS_CUDA(cudaMemcpyAsync(hp, h->hdev, 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
-      };
-      if (h->use_graphs) run_graph(h, j, body, prof);
-      else body();
-      MFS_CUDA(cudaStreamSynchronize(s));
-      if (prof) h->prof->collect();
-      if (!ls.column(hp, j)) return MFS_ERR_BREAKDOWN;
+      // queue iteration j + 1 ahead unless iteration j may end the cycle
+      // (predicted estimate: the last one times the last ratio cubed)
+      if (queued == j + 1 && j + 1 < m && ls.iters + 2 <= h->prm.max_iters && e_last * rho * rho * rho > tol)
+        enqueue(queued++);
+      MFS_CUDA(cudaEventSynchronize(h->iter_ev[j & 1]));
+      if (!ls.column(hpb[j & 1], j)) return fail_drained(MFS_ERR_BREAKDOWN);
       if (ls.est <= tol || ls.happy || ls.iters >= h->prm.max_iters) break;
-      dev::scale(w, 1.0 / ls.hn, w, n, s);
+      rho = std::min(1.0, ls.est / e_last);
+      e_last = ls.est;
+      if (queued == j + 1 && j + 1 < m) enqueue(queued++);
     }
     ls.back_substitute();
     MFS_CUDA(cudaMemcpyAsync(h->ydev, ls.y.data(), ls.jend * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1362,6 +1401,7 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     if (relres <= tol || ls.iters >= h->prm.max_iters) break;
     ++restarts;
   }
+  if (prof) h->prof->collect();
   info->iters = ls.iters;
   info->restarts = restarts;
   info->true_relres = relres;
@@ -2356,13 +2396,15 @@ void alloc_solver_work(mfs_handle *h) {
   h->xd = h->ar.zeros<double>(h->n);
   h->bd = h->ar.zeros<double>(h->n);
   h->partial = h->ar.zeros<double>((int64_t)64 * h->nblk);
-  h->hdev = h->ar.zeros<double>(256);
+  h->hdev = h->ar.zeros<double>(kHostSlots);
   h->ydev = h->ar.zeros<double>(64);
   if (h->prm.precision == MFS_FP32P) {
     h->in32 = h->ar.zeros<float>(h->n);
     h->out32 = h->ar.zeros<float>(h->n);
   }
-  h->hpin = (double *)g_pinned.get(256 * sizeof(double));
+  h->hpin = (double *)g_pinned.get(kHostSlots * sizeof(double));
+  for (auto &e : h->iter_ev)
+    if (!e) MFS_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 }
 
 int fail(int code, const std::string &msg) {
@@ -2869,7 +2911,7 @@ int mfs_fp64_rate(double *tflops, void *stream) {
 
 int mfs_apply(mfs_handle *h, const double *v, double *z) {
   if (!h || !v || !z || v == z) return fail(MFS_ERR_INVALID, "bad apply arguments");
-  return with_io(h, v, z, precond_apply);
+  return with_io(h, v, z, [](mfs_handle *hh, const double *vv, double *zz) { precond_apply(hh, vv, zz); });
 }
 
 int mfs_matvec(mfs_handle *h, const double *x, double *y) {
