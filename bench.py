@@ -249,6 +249,8 @@ def precond_extra(args):
         extra["simple_pred"] = args.simple_pred
     if args.smoother == "gs" or args.precond == "bgs_gs":
         extra["smoother"] = "gs"
+    if getattr(args, "vcycle_tail", False):
+        extra["vcycle_tail"] = 1
     return extra
 
 
@@ -257,6 +259,7 @@ def oracle_params(args):
     from oracle import precond
     from oracle.cycles import SmootherParams
     ex = dict(precond_extra(args))
+    ex.pop("vcycle_tail", None)  # a launch form of the library, not a method parameter
     sm = SmootherParams("gs", omega=0.79, sweeps=1) if ex.pop("smoother", None) == "gs" else None
     return precond.Params(args.precond, **solver_kw(args), **ex, smoother=sm)
 
@@ -838,6 +841,8 @@ def main():
     ap.add_argument("--baseline-s", type=float, default=10.0,
                     help="CPU baseline: each oracle process runs whole solves for at least this long (one at least)")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--vcycle-tail", action="store_true",
+                    help="one-CTA V-cycle tails (the level above the coarsest and the coarse solve in one launch)")
     ap.add_argument("--no-pg", action="store_true", help="oseen workload: R = P^T on the velocity field")
     ap.add_argument("--workload", default="box", choices=["box", "fsi", "cons", "oseen", "te2d", "batch", "serve"],
                     help="box: the 64^3 three-field system (headline); fsi: the 48^3 split-box saddle; "

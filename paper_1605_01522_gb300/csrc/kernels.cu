@@ -1772,8 +1772,16 @@ void scale(const double *x, double a, double *y, int64_t n, cudaStream_t s) {
   if (n) go<KScale>(ew_grid(n), kThreads, 0, s, {x, a, y, n});
 }
 
+// CTAs of the CGS2 passes over a length-n basis: one per 2048 entries, up
+// to four per SM; small systems (below 32 k entries) take up to 16, one
+// staged tile of w (kTile entries) each at least, so that their passes do
+// not loop over tiles in one or two CTAs.  (More CTAs for mid-size systems
+// would help a system solved alone but slow down batches, whose merged
+// launches fill the GPU already; the count is per system, so a batch and a
+// solo solve reduce in the same order.)
 int mdot_blocks(int64_t n) {
   int64_t b = n / 2048;
+  b = std::max(b, std::min<int64_t>((n + kTile - 1) / kTile, 16));
   if (b < 1) b = 1;
   if (b > 152 * 4) b = 152 * 4;
   return (int)b;

@@ -1314,7 +1314,17 @@ void arnoldi(mfs_handle *h, int j, double *w, double *hd, cudaStream_t s) {
   dev::reduce_partials(h->partial, 1, h->nblk, hd + 128, s);
 }
 
+// FGMRES solves running in this process (a solve queues iterations ahead
+// only while it runs alone: with other solves on the GPU its host turnaround
+// is covered by their work, and queued-ahead iterations measured slower for
+// 16 concurrent solves)
+static std::atomic<int> g_fgmres_running{0};
+
 int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info, bool prof) {
+  struct Running {
+    Running() { ++g_fgmres_running; }
+    ~Running() { --g_fgmres_running; }
+  } running;
   const int64_t n = h->n;
   const int m = h->m;
   cudaStream_t s = h->s;
@@ -1344,7 +1354,8 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
   // and pinned host), then event j % 2.  Nothing in it waits for the host's
   // Givens step of iteration j - 1, so iteration j + 1 is queued before the
   // host reads column j unless the residual estimate says iteration j may end
-  // the cycle; the GPU then runs the iterations back to back.  An iteration
+  // the cycle (and this solve runs alone in the process); the GPU then runs
+  // the iterations back to back.  An iteration
   // queued past the end of a cycle writes only V_{j+2}, Z_{j+1} and its own
   // buffers, none of which the cycle end reads.
   auto enqueue = [&](int j) {
@@ -1381,7 +1392,8 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     for (int j = 0; j < m; ++j) {
       // queue iteration j + 1 ahead unless iteration j may end the cycle
       // (predicted estimate: the last one times the last ratio cubed)
-      if (queued == j + 1 && j + 1 < m && ls.iters + 2 <= h->prm.max_iters && e_last * rho * rho * rho > tol)
+      if (queued == j + 1 && j + 1 < m && ls.iters + 2 <= h->prm.max_iters && e_last * rho * rho * rho > tol &&
+          g_fgmres_running.load() == 1)
         enqueue(queued++);
       MFS_CUDA(cudaEventSynchronize(h->iter_ev[j & 1]));
       if (!ls.column(hpb[j & 1], j)) return fail_drained(MFS_ERR_BREAKDOWN);
