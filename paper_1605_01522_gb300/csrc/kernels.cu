@@ -1043,9 +1043,9 @@ __device__ __forceinline__ void tile_dots(const double *__restrict__ V, int64_t 
     const int q = warp + 8 * m;
     if (q < k) {
       const double *vq = V + (int64_t)q * ldv + t0;
-      double s = 0.0;
-      for (int t = lane; t < cnt; t += 32) s += vq[t] * ws[t];
-      acc[m] += s;
+      double s = acc[m];  // one FMA chain per row across the tiles (no extra add per tile)
+      for (int t = lane; t < cnt; t += 32) s = fma(vq[t], ws[t], s);
+      acc[m] = s;
     }
   }
 }
@@ -1118,7 +1118,7 @@ __device__ __forceinline__ void d_cgs_fused(const double *__restrict__ V, int64_
     double wn = 0.0;
     if (threadIdx.x < cnt) {
       const int64_t i = t0 + threadIdx.x;
-      double s = 0.0;
+      double s = 0.0;  // (a chain started from w_i would wait for its load)
       for (int q = 0; q < k; ++q) s += V[(int64_t)q * ldv + i] * hs[q];
       wn = w[i] - s;
       w[i] = wn;
@@ -1180,7 +1180,7 @@ __device__ __forceinline__ void d_cgs_update(const double *__restrict__ V, int64
   const int64_t hi = min(n, lo + chunk);
   double nrm = 0.0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    double s = 0.0;
+    double s = 0.0;  // (a chain started from w_i would wait for its load)
     for (int q = 0; q < k; ++q) s += V[(int64_t)q * ldv + i] * hs[q];
     const double wn = w[i] - s;
     w[i] = wn;
