@@ -412,9 +412,10 @@ def run_oracle_baseline(args):
 
 
 class BaselineChild:
-    """The oracle baseline in a separate process (started before any GPU work
-    so that its preparation overlaps the GPU setup; its timed solves start
-    only when release() is called)."""
+    """The oracle baseline in a separate process, started before any GPU work
+    so that its preparation overlaps the GPU setup and warm-ups; the timed GPU
+    solves wait until it is prepared (wait_ready), and its own timed solves
+    start only when result() is called, after the GPU measurements."""
 
     def __init__(self, args):
         self.xpath = os.path.join(tempfile.gettempdir(), f"mfs_oracle_x_{os.getpid()}.npy")
@@ -423,6 +424,13 @@ class BaselineChild:
                "--smoother", args.smoother, "--simple-pred", args.simple_pred,
                "--baseline-s", str(args.baseline_s), "--oracle-x", self.xpath] + (["--no-pg"] if args.no_pg else [])
         self.proc = subprocess.Popen(cmd, stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True)
+
+    def wait_ready(self):
+        """Block until the child has built its hierarchy and forked its
+        processes (so that no oracle work runs beside the timed GPU solves)."""
+        for line in self.proc.stdout:
+            if line.strip() == "ready":
+                return
 
     def result(self):
         self.proc.stdin.write("go\n")
@@ -493,6 +501,8 @@ def run_mfs(args, rank, world):
     # every solve starts from HBM even when its matrices would fit in L2
     flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if child is not None:
+        child.wait_ready()  # the oracle's preparation must not share the host with the timed solves
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
