@@ -251,6 +251,8 @@ def precond_extra(args):
         extra["smoother"] = "gs"
     if getattr(args, "vcycle_tail", False):
         extra["vcycle_tail"] = 1
+    if getattr(args, "pdl", -1) != -1:
+        extra["pdl"] = args.pdl
     return extra
 
 
@@ -259,7 +261,8 @@ def oracle_params(args):
     from oracle import precond
     from oracle.cycles import SmootherParams
     ex = dict(precond_extra(args))
-    ex.pop("vcycle_tail", None)  # a launch form of the library, not a method parameter
+    ex.pop("vcycle_tail", None)  # launch forms of the library, not method parameters
+    ex.pop("pdl", None)
     sm = SmootherParams("gs", omega=0.79, sweeps=1) if ex.pop("smoother", None) == "gs" else None
     return precond.Params(args.precond, **solver_kw(args), **ex, smoother=sm)
 
@@ -699,7 +702,7 @@ def run_batch(args, rank, world):
         kw = solver_kw(args)
     t1 = time.perf_counter()
     # layouts tuned for throughput (many systems on the GPU at once)
-    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, layout_tune=1, **kw)
+    base = {ne: mfs.Solver(sy, precond=args.precond, precision=args.precision, layout_tune=1, pdl=args.pdl, **kw)
             for ne, sy in mats.items()}
     solvers, used = [], set()
     for ne in sizes.tolist():
@@ -851,6 +854,9 @@ def main():
     ap.add_argument("--baseline-s", type=float, default=10.0,
                     help="CPU baseline: each oracle process runs whole solves for at least this long (one at least)")
     ap.add_argument("--no-graphs", action="store_true")
+    ap.add_argument("--pdl", type=int, default=-1, choices=[-1, 0, 1],
+                    help="programmatic dependent launch of the solve-phase kernels: 1 on, 0 off, "
+                         "-1 (default) for systems of at most 65,536 dofs")
     ap.add_argument("--vcycle-tail", action="store_true",
                     help="one-CTA V-cycle tails (the level above the coarsest and the coarse solve in one launch)")
     ap.add_argument("--no-pg", action="store_true", help="oseen workload: R = P^T on the velocity field")

@@ -185,6 +185,13 @@ typedef struct {
                                         arithmetic, bit for bit); 0 (default): one launch per
                                         step (Algorithm 1 as written) - on GB300 the one-SM
                                         tail is no faster than the launches it replaces */
+  int pdl;                           /* solve-phase kernels as programmatic dependent launches
+                                        (each may be scheduled while its predecessor still
+                                        runs and waits on the device for its results; the
+                                        results are the same): 1 on, 0 off, -1 (default) for
+                                        systems of at most 65,536 dofs, whose kernels are
+                                        too short to hide a launch, while no other solve
+                                        runs in the process */
 } mfs_params;
 
 typedef struct {

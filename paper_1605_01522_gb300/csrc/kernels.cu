@@ -33,6 +33,12 @@ thread_local int g_hook_off = 0;
 
 // While set, this thread's launches are appended here instead of issued.
 thread_local Recorder *g_rec = nullptr;
+// While set, this thread's solve-phase launches are programmatic dependent
+// launches where they directly follow another of its kernel launches on the
+// same stream (g_pdl_prev): a kernel after a copy, an event or a graph launch
+// is launched normally.
+thread_local bool g_pdl = false;
+thread_local cudaStream_t g_pdl_prev = nullptr;
 // accounting of the launch being issued (HookScope fills it for the recorder)
 thread_local RecOp g_acct;
 
@@ -55,9 +61,13 @@ struct HookScope {
       return;
     }
     if (g_hook && !g_hook_off) on = g_hook->before(s, cls, sig, rows);
+    if (on) g_pdl_prev = nullptr;  // an event precedes the launch
   }
   ~HookScope() {
-    if (on) g_hook->after(s, cls, bytes, sig, rows, flops);
+    if (on) {
+      g_hook->after(s, cls, bytes, sig, rows, flops);
+      g_pdl_prev = nullptr;
+    }
   }
 };
 
@@ -67,8 +77,14 @@ struct HookScope {
 // independent launches of K (one per system of a batch) as ONE grid: CTA c
 // runs block map[c].bid of the launch whose arguments are tab[map[c].t],
 // unless that launch's system map[c].g is inactive.
+// Launched as a programmatic dependent launch (set_pdl), a kernel may be
+// scheduled while its predecessor in the stream still runs: it first waits
+// until that predecessor has completed and its writes are visible, then lets
+// its own successor start launching.  Launched normally, both are no-ops.
 template <class K>
 __global__ void __launch_bounds__(K::kMaxThreads) k_solo(const __grid_constant__ typename K::Args a) {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   K::run(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
@@ -104,6 +120,22 @@ void go(unsigned grid, unsigned threads, size_t smem, cudaStream_t s, const type
     op.args.assign((const unsigned char *)&a, (const unsigned char *)&a + sizeof(a));
     g_rec->ops.push_back(std::move(op));
     g_acct = RecOp();
+    return;
+  }
+  const bool pdl = g_pdl && g_pdl_prev == s;
+  g_pdl_prev = g_pdl ? s : nullptr;
+  if (pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_solo<K>, a);
     return;
   }
   k_solo<K><<<grid, threads, smem, s>>>(a);
@@ -1473,6 +1505,11 @@ double fp64_rate(cudaStream_t s) {
 
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
 void set_recorder(Recorder *r) { g_rec = r; }
+void set_pdl(bool on) {
+  g_pdl = on;
+  g_pdl_prev = nullptr;
+}
+void pdl_break() { g_pdl_prev = nullptr; }
 
 HookBypass::HookBypass() { ++g_hook_off; }
 HookBypass::~HookBypass() { --g_hook_off; }

@@ -80,6 +80,12 @@ struct Recorder {
   std::vector<RecOp> ops;
 };
 void set_recorder(Recorder *r);
+// this thread's solve-phase launches overlap the end of their predecessor in
+// the stream (programmatic dependent launch) while on
+void set_pdl(bool on);
+// the caller queued something other than a kernel on a stream: the next
+// launch waits for it the ordinary way
+void pdl_break();
 // CTA c of a multi-system launch of op.fn runs block bid (of nb) of table
 // entry t, which belongs to system g; the kernel takes (tab, map, active):
 // the device array of argument blocks (op.args layout, consecutive), the

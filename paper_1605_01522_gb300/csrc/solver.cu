@@ -1208,6 +1208,7 @@ double dot_host(mfs_handle *h, const double *x, const double *y) {
   dev::mdot(x, 0, 1, y, h->n, h->partial, h->nblk, h->s);
   dev::reduce_partials(h->partial, 1, h->nblk, h->hdev + kDotSlot, h->s);
   MFS_CUDA(cudaMemcpyAsync(h->hpin + kDotSlot, h->hdev + kDotSlot, sizeof(double), cudaMemcpyDeviceToHost, h->s));
+  dev::pdl_break();
   MFS_CUDA(cudaStreamSynchronize(h->s));
   return h->hpin[kDotSlot];
 }
@@ -1223,6 +1224,7 @@ template <typename F> void run_graph(mfs_handle *h, int j, F &&body, bool prof) 
     }
     cudaGraph_t graph = nullptr;
     MFS_CUDA(cudaStreamBeginCapture(h->s, cudaStreamCaptureModeThreadLocal));
+    dev::pdl_break();  // the graph's first kernel has no kernel before it
     try {
       body();
     } catch (...) {
@@ -1239,6 +1241,7 @@ template <typename F> void run_graph(mfs_handle *h, int j, F &&body, bool prof) 
     MFS_CUDA(e);
   }
   MFS_CUDA(cudaGraphLaunch(g.exec, h->s));
+  dev::pdl_break();
   if (prof) h->prof->pending.push_back(&g.recs);
 }
 
@@ -1325,6 +1328,13 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     Running() { ++g_fgmres_running; }
     ~Running() { --g_fgmres_running; }
   } running;
+  // programmatic dependent launches for this solve (mfs_params.pdl; the
+  // automatic choice also wants the solve to run alone: 16 concurrent solves
+  // of small systems measured 2 % slower with them)
+  struct Pdl {
+    explicit Pdl(bool on) { dev::set_pdl(on); }
+    ~Pdl() { dev::set_pdl(false); }
+  } pdl(h->prm.pdl == 1 || (h->prm.pdl == -1 && h->n <= 65536 && g_fgmres_running.load() == 1));
   const int64_t n = h->n;
   const int m = h->m;
   cudaStream_t s = h->s;
@@ -1372,10 +1382,12 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
       matvec(h, zj, w);
       arnoldi(h, j, w, hdb[j & 1], s);
       MFS_CUDA(cudaMemcpyAsync(hpb[j & 1], hdb[j & 1], 136 * sizeof(double), cudaMemcpyDeviceToHost, s));
+      dev::pdl_break();
     };
     if (h->use_graphs) run_graph(h, j, body, prof);
     else body();
     MFS_CUDA(cudaEventRecord(h->iter_ev[j & 1], s));
+    dev::pdl_break();
   };
   auto fail_drained = [&](int code) {  // no queued iteration may outlive the call
     cudaStreamSynchronize(s);
@@ -1404,6 +1416,7 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     }
     ls.back_substitute();
     MFS_CUDA(cudaMemcpyAsync(h->ydev, ls.y.data(), ls.jend * sizeof(double), cudaMemcpyHostToDevice, s));
+    dev::pdl_break();
     dev::gemv_add(h->Z, n, ls.jend, h->ydev, x, n, s);
     matvec(h, x, r);
     dev::axpy<double>(r, b, -1.0, n, s);
@@ -2453,6 +2466,7 @@ void mfs_default_params(mfs_params *p) {
   p->verbose = 0;
   p->setup_device = 1;
   p->vcycle_tail = 0;
+  p->pdl = -1;
 }
 
 int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int nfields,
@@ -2472,7 +2486,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
       (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS) ||
       (p.rows_split != 0 && p.rows_split != 1 && p.rows_split != 2 && p.rows_split != 4) ||
-      (p.layout_tune != 0 && p.layout_tune != 1) || (p.vcycle_tail != 0 && p.vcycle_tail != 1))
+      (p.layout_tune != 0 && p.layout_tune != 1) || (p.vcycle_tail != 0 && p.vcycle_tail != 1) || p.pdl < -1 || p.pdl > 1)
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;

@@ -75,7 +75,8 @@ class Params(C.Structure):
                 ("cuda_stream", C.c_void_p), ("verbose", C.c_int), ("setup_only", C.c_int),
                 ("profile", C.c_int), ("no_graphs", C.c_int), ("setup_device", C.c_int),
                 ("simple_pred", C.c_int), ("gs_sweeps", C.c_int), ("gs_omega", C.c_double),
-                ("rows_split", C.c_int), ("layout_tune", C.c_int), ("vcycle_tail", C.c_int)]
+                ("rows_split", C.c_int), ("layout_tune", C.c_int), ("vcycle_tail", C.c_int),
+                ("pdl", C.c_int)]
 
 
 class Info(C.Structure):
