@@ -854,9 +854,9 @@ def main():
     ap.add_argument("--baseline-s", type=float, default=10.0,
                     help="CPU baseline: each oracle process runs whole solves for at least this long (one at least)")
     ap.add_argument("--no-graphs", action="store_true")
-    ap.add_argument("--pdl", type=int, default=-1, choices=[-1, 0, 1],
+    ap.add_argument("--pdl", type=int, default=-1,
                     help="programmatic dependent launch of the solve-phase kernels: 1 on, 0 off, "
-                         "-1 (default) for systems of at most 65,536 dofs")
+                         "N > 1 for launches of at most N CTAs, -1 (default) automatic")
     ap.add_argument("--vcycle-tail", action="store_true",
                     help="one-CTA V-cycle tails (the level above the coarsest and the coarse solve in one launch)")
     ap.add_argument("--no-pg", action="store_true", help="oseen workload: R = P^T on the velocity field")

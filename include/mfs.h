@@ -188,10 +188,12 @@ typedef struct {
   int pdl;                           /* solve-phase kernels as programmatic dependent launches
                                         (each may be scheduled while its predecessor still
                                         runs and waits on the device for its results; the
-                                        results are the same): 1 on, 0 off, -1 (default) for
-                                        systems of at most 65,536 dofs, whose kernels are
-                                        too short to hide a launch, while no other solve
-                                        runs in the process */
+                                        results are the same): 1 every launch, 0 none,
+                                        N > 1 launches of at most N CTAs, -1 (default)
+                                        while no other solve runs in the process: every
+                                        launch of a system of at most 65,536 dofs (its
+                                        kernels are too short to hide a launch), the
+                                        launches of at most 160 CTAs of a larger one */
 } mfs_params;
 
 typedef struct {

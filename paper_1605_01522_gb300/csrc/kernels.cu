@@ -37,7 +37,7 @@ thread_local Recorder *g_rec = nullptr;
 // launches where they directly follow another of its kernel launches on the
 // same stream (g_pdl_prev): a kernel after a copy, an event or a graph launch
 // is launched normally.
-thread_local bool g_pdl = false;
+thread_local unsigned g_pdl = 0;  // largest grid (CTAs) launched this way; 0: none
 thread_local cudaStream_t g_pdl_prev = nullptr;
 // accounting of the launch being issued (HookScope fills it for the recorder)
 thread_local RecOp g_acct;
@@ -122,7 +122,7 @@ void go(unsigned grid, unsigned threads, size_t smem, cudaStream_t s, const type
     g_acct = RecOp();
     return;
   }
-  const bool pdl = g_pdl && g_pdl_prev == s;
+  const bool pdl = grid <= g_pdl && g_pdl_prev == s;
   g_pdl_prev = g_pdl ? s : nullptr;
   if (pdl) {
     cudaLaunchConfig_t cfg = {};
@@ -1505,8 +1505,8 @@ double fp64_rate(cudaStream_t s) {
 
 void set_launch_hook(LaunchHook *h) { g_hook = h; }
 void set_recorder(Recorder *r) { g_rec = r; }
-void set_pdl(bool on) {
-  g_pdl = on;
+void set_pdl(unsigned max_grid) {
+  g_pdl = max_grid;
   g_pdl_prev = nullptr;
 }
 void pdl_break() { g_pdl_prev = nullptr; }

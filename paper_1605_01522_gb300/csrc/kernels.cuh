@@ -80,9 +80,9 @@ struct Recorder {
   std::vector<RecOp> ops;
 };
 void set_recorder(Recorder *r);
-// this thread's solve-phase launches overlap the end of their predecessor in
-// the stream (programmatic dependent launch) while on
-void set_pdl(bool on);
+// this thread's solve-phase launches of at most max_grid CTAs overlap the end
+// of their predecessor in the stream (programmatic dependent launch); 0: none
+void set_pdl(unsigned max_grid);
 // the caller queued something other than a kernel on a stream: the next
 // launch waits for it the ordinary way
 void pdl_break();

@@ -1328,13 +1328,18 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
     Running() { ++g_fgmres_running; }
     ~Running() { --g_fgmres_running; }
   } running;
-  // programmatic dependent launches for this solve (mfs_params.pdl; the
-  // automatic choice also wants the solve to run alone: 16 concurrent solves
-  // of small systems measured 2 % slower with them)
+  // programmatic dependent launches for this solve (mfs_params.pdl).  The
+  // automatic choice: every launch of a small system, the launches of at
+  // most 160 CTAs (coarse levels, reductions) of a larger one - its big
+  // launches measured slower that way - and only while the solve runs alone
+  // (16 concurrent solves of small systems measured 2 % slower with them)
+  const bool alone = g_fgmres_running.load() == 1;
   struct Pdl {
-    explicit Pdl(bool on) { dev::set_pdl(on); }
-    ~Pdl() { dev::set_pdl(false); }
-  } pdl(h->prm.pdl == 1 || (h->prm.pdl == -1 && h->n <= 65536 && g_fgmres_running.load() == 1));
+    explicit Pdl(unsigned max_grid) { dev::set_pdl(max_grid); }
+    ~Pdl() { dev::set_pdl(0); }
+  } pdl(h->prm.pdl == 1 ? ~0u
+        : h->prm.pdl > 1 ? (unsigned)h->prm.pdl
+        : (h->prm.pdl == -1 && alone) ? (h->n <= 65536 ? ~0u : 160u) : 0u);
   const int64_t n = h->n;
   const int m = h->m;
   cudaStream_t s = h->s;
@@ -2486,7 +2491,7 @@ int mfs_setup(const mfs_block *blocks, int nblocks, const mfs_field *fields, int
       (p.precision != MFS_FP64 && p.precision != MFS_FP32P) || p.setup_device < 0 || p.setup_device > 1 ||
       (p.simple_pred != MFS_PRED_BGS_AMG && p.simple_pred != MFS_PRED_AMG_BGS) ||
       (p.rows_split != 0 && p.rows_split != 1 && p.rows_split != 2 && p.rows_split != 4) ||
-      (p.layout_tune != 0 && p.layout_tune != 1) || (p.vcycle_tail != 0 && p.vcycle_tail != 1) || p.pdl < -1 || p.pdl > 1)
+      (p.layout_tune != 0 && p.layout_tune != 1) || (p.vcycle_tail != 0 && p.vcycle_tail != 1) || p.pdl < -1)
     return fail(MFS_ERR_INVALID, "bad parameters");
   const bool host_only = p.setup_only != 0;
   int ndev = 0;
