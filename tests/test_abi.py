@@ -36,6 +36,7 @@ def test_status_strings_and_defaults():
     assert (p.precond, p.bgs_order, p.bgs_sweeps, p.restart, p.cheb_degree) == (0, 0, 1, 50, 2)
     assert abs(p.cheb_ratio - 30.0) < 1e-15 and abs(p.cheb_boost - 1.1) < 1e-15
     assert p.rows_split == 0  # threads per row of the float64 matvec: timed at setup
+    assert (p.layout_tune, p.vcycle_tail, p.pdl) == (0, 0, -1)  # layouts for one solve, stepwise V-cycle, automatic PDL
 
 
 @pytest.mark.parametrize("split", [3, -1, 8])
@@ -45,4 +46,13 @@ def test_bad_rows_split_is_refused(split):
     s = inputs.thermo_elastic_2d(ne=4)
     with pytest.raises(mfs.MfsError) as e:
         mfs.Solver(s, setup_only=1, rows_split=split)
+    assert e.value.code == mfs.ERR_INVALID
+
+
+@pytest.mark.parametrize("field,value", [("pdl", -2), ("vcycle_tail", 2), ("layout_tune", -1)])
+def test_bad_launch_options_are_refused(field, value):
+    """Out-of-range launch options are refused before anything is built."""
+    s = inputs.thermo_elastic_2d(ne=4)
+    with pytest.raises(mfs.MfsError) as e:
+        mfs.Solver(s, setup_only=1, **{field: value})
     assert e.value.code == mfs.ERR_INVALID
