@@ -1317,29 +1317,32 @@ void arnoldi(mfs_handle *h, int j, double *w, double *hd, cudaStream_t s) {
   dev::reduce_partials(h->partial, 1, h->nblk, hd + 128, s);
 }
 
-// FGMRES solves running in this process (a solve queues iterations ahead
-// only while it runs alone: with other solves on the GPU its host turnaround
-// is covered by their work, and queued-ahead iterations measured slower for
-// 16 concurrent solves)
-static std::atomic<int> g_fgmres_running{0};
+// Solves and other solve-phase calls (apply, matvec) running in this process.
+// A solve queues iterations ahead only while it runs alone: with other solves
+// on the GPU its host turnaround is covered by their work, and queued-ahead
+// iterations measured slower for 16 concurrent solves.
+static std::atomic<int> g_solves_running{0};
+
+// One solve-phase call: counted in g_solves_running, and its launches made
+// programmatic dependent launches as mfs_params.pdl says.  The automatic
+// choice: every launch of a small system, the launches of at most 160 CTAs
+// (coarse levels, reductions) of a larger one - its big launches measured
+// slower that way - and only while the call runs alone (16 concurrent solves
+// of small systems measured 2 % slower with them).
+struct SolvePhase {
+  explicit SolvePhase(const mfs_handle *h) {
+    const bool alone = ++g_solves_running == 1;
+    const int p = h->prm.pdl;
+    dev::set_pdl(p == 1 ? ~0u : p > 1 ? (unsigned)p : (p == -1 && alone) ? (h->n <= 65536 ? ~0u : 160u) : 0u);
+  }
+  ~SolvePhase() {
+    dev::set_pdl(0);
+    --g_solves_running;
+  }
+};
 
 int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info, bool prof) {
-  struct Running {
-    Running() { ++g_fgmres_running; }
-    ~Running() { --g_fgmres_running; }
-  } running;
-  // programmatic dependent launches for this solve (mfs_params.pdl).  The
-  // automatic choice: every launch of a small system, the launches of at
-  // most 160 CTAs (coarse levels, reductions) of a larger one - its big
-  // launches measured slower that way - and only while the solve runs alone
-  // (16 concurrent solves of small systems measured 2 % slower with them)
-  const bool alone = g_fgmres_running.load() == 1;
-  struct Pdl {
-    explicit Pdl(unsigned max_grid) { dev::set_pdl(max_grid); }
-    ~Pdl() { dev::set_pdl(0); }
-  } pdl(h->prm.pdl == 1 ? ~0u
-        : h->prm.pdl > 1 ? (unsigned)h->prm.pdl
-        : (h->prm.pdl == -1 && alone) ? (h->n <= 65536 ? ~0u : 160u) : 0u);
+  SolvePhase phase(h);
   const int64_t n = h->n;
   const int m = h->m;
   cudaStream_t s = h->s;
@@ -1410,7 +1413,7 @@ int fgmres(mfs_handle *h, const double *b, double *x, double tol, mfs_info *info
       // queue iteration j + 1 ahead unless iteration j may end the cycle
       // (predicted estimate: the last one times the last ratio cubed)
       if (queued == j + 1 && j + 1 < m && ls.iters + 2 <= h->prm.max_iters && e_last * rho * rho * rho > tol &&
-          g_fgmres_running.load() == 1)
+          g_solves_running.load() == 1)
         enqueue(queued++);
       MFS_CUDA(cudaEventSynchronize(h->iter_ev[j & 1]));
       if (!ls.column(hpb[j & 1], j)) return fail_drained(MFS_ERR_BREAKDOWN);
@@ -2901,7 +2904,10 @@ static int with_io(mfs_handle *h, const double *in, double *out, void (*fn)(mfs_
       a = h->bd;
     }
     if (!dout) b = h->xd;
-    fn(h, a, b);
+    {
+      SolvePhase phase(h);
+      fn(h, a, b);
+    }
     if (!dout) MFS_CUDA(cudaMemcpyAsync(out, h->xd, h->n * sizeof(double), cudaMemcpyDeviceToHost, h->s));
     MFS_CUDA(cudaStreamSynchronize(h->s));
     MFS_CUDA(cudaGetLastError());

@@ -274,3 +274,7 @@ def test_programmatic_dependent_launch_same_result_bit_for_bit(name, pc, prec):
             assert ia["iters"] == ib["iters"] and torch.equal(xa, xb)
         xh, ih, _ = b.solve(s.rhs.copy(), np.zeros(s.ndofs), tol=1e-8)
         assert ih["iters"] == ia["iters"] and np.array_equal(xh, xa.cpu().numpy())
+        v = _cuda(np.random.default_rng(6).standard_normal(s.ndofs))
+        za = a.apply(v)
+        for sv in (b, e):  # preconditioner applications and matvecs take the same launches
+            assert torch.equal(za, sv.apply(v)) and torch.equal(a.matvec(v), sv.matvec(v))
