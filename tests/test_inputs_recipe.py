@@ -8,8 +8,8 @@ blocks A_01 = alpha * int B^T m N and A_10 = beta * int N m^T B (so A_10 =
 Checked from the mathematics, not by re-running the assembly: dof counts,
 symmetry, the coupling ratio, rigid-body modes in the kernel of the elasticity
 rows away from the boundary, constants in the kernel of the Laplacians, the
-Q1 mass row sum h^d, identity rows and zero couplings on the boundary, and
-the log-uniform batch sizes."""
+Q1 mass row sum h^d, identity rows and zero couplings on the boundary, the
+log-uniform batch sizes, and the structure of the split-box saddle system."""
 import numpy as np
 import pytest
 
@@ -115,3 +115,32 @@ def test_batch_sizes_are_log_uniform_in_range():
     s256, mats, rhs = inputs.batch_workload(8, 12, 16, seed=3)
     assert len(rhs) == 8 and all(len(r) == mats[int(n)].ndofs for r, n in zip(rhs, s256))
     assert all(mats[int(n)].fields[0].nnodes == (n + 1) ** 3 for n in s256)
+
+
+def test_split_box_saddle_system_structure():
+    """The split-box saddle stand-in: four fields on the two halves of the cube
+    (structure above z = 0.5; mesh motion, Stokes velocity and PSPG pressure
+    below), 600,250 dofs at n_e = 48 by the node counts, a symmetric
+    gradient / divergence pair, a negative semi-definite stabilised pressure
+    block on the free dofs, an S-Fu interface penalty pair, and a symmetric
+    velocity block that becomes non-symmetric (and Petrov-Galerkin) with wind."""
+    ne = 8
+    s = inputs.fsi_box(ne=ne)
+    up, lo = (ne + 1) ** 2 * (ne - ne // 2 + 1), (ne + 1) ** 2 * (ne // 2 + 1)
+    assert [f.ndofs for f in s.fields] == [3 * up, 3 * lo, 3 * lo, lo]
+    assert 3 * 49 ** 2 * 25 * 3 + 49 ** 2 * 25 == 600250  # the n_e = 48 form
+    A = _blocks(s)
+    assert abs(A[(3, 2)] - A[(2, 3)].T).max() == 0.0
+    assert abs(A[(0, 2)] - A[(2, 0)].T).max() == 0.0 and abs(A[(0, 2)]).max() > 0
+    assert not any(k in A for k in [(0, 1), (1, 0), (0, 3), (3, 0), (1, 3), (3, 1)])
+    fu = A[(2, 2)]
+    assert abs(fu - fu.T).max() <= 1e-14 * abs(fu).max()
+    fp = s.fields[3]
+    free = np.setdiff1d(np.arange(fp.ndofs), fp.dirichlet_nodes)
+    P = A[(3, 3)].toarray()[np.ix_(free, free)]
+    assert np.linalg.eigvalsh(P).max() <= 1e-12 * abs(P).max()
+    assert np.all(np.diag(P) < 0)
+    assert not s.fields[2].petrov_galerkin
+    o = inputs.fsi_box(ne=ne, wind=(0.2, 0.1, 0.0))
+    fo = _blocks(o)[(2, 2)]
+    assert abs(fo - fo.T).max() > 1e-6 * abs(fo).max() and o.fields[2].petrov_galerkin
