@@ -383,6 +383,7 @@ def run_reference(args, rank, world):
     cfg = workload_config(args, s, {"oracle_iters": iters, "oracle_setup_s": round(setup_s, 1),
                                     "solve_s_mean": statistics.mean(r[0] for r in res)})
     cfg["precision"] = "fp64"
+    cfg["l2"] = "host cores (no GPU L2 involved); the oracle's matrices are read from host memory"
     cfg["workload"] = cfg["workload"].replace(f"in {args.precision.upper()}", "in FP64 (the CPU oracle)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
